@@ -1,0 +1,360 @@
+"""FP64 CPU oracle for the far-field ptychography projection cycle.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+module.  The product path (``paper_2008_11511_gb300``) never calls it and has
+no CPU fallback.  It shares no code with the CUDA path; the only common input
+source is the seeded generator in ``synthetic/``.
+
+Everything is plain NumPy/SciPy in float64 / complex128, written to be checked
+against the paper by eye.  The paper (PyNX, Favre-Nicolin et al. 2020) gives
+the operators by name and definition; the algorithms it cites (DM: Elser 2007
+and its ptychographic form by Thibault et al. 2008/2009; AP: Marchesini et al.
+2013; ML: Thibault & Guizar-Sicairos 2012; incoherent modes: Thibault & Menzel
+2013) are restated here from their mathematics.
+
+Notation (paper, Section 4 and the ptychography operator table in the
+appendix): J positions r_j, K probe modes P_k (N x N), object O (Ho x Wo),
+exit waves Psi_jk.  ``FT`` is the orthonormal 2D DFT over the last two axes,
+arrays in FFT order (zero frequency at [0, 0]).  A position (row, col) is the
+top-left corner of the frame's object patch.
+
+Readings of points the paper leaves open (each is listed in the design doc):
+* FT normalisation: orthonormal, so IFT = FT^H and Parseval holds exactly.
+* ObjProbe2Psi: Phi_jk(x) = P_k(x) O(r_j + x) (the paper writes
+  Psi_j(r) = O(r) P(r - r_j); with integer top-left positions this is the same
+  product on the patch).
+* ApplyAmplitude with modes: one common factor sqrt(I_obs) / sqrt(sum_k |Psi_k|^2)
+  for all modes; masked pixels left unchanged; I_obs clamped at 0; a zero
+  calculated amplitude stays zero (denominator floored at 1e-20).
+* LLK (Poisson): the deviance form sum over unmasked pixels of
+  I_c - I_o + I_o ln(I_o / I_c) (= I_c where I_o = 0), I_c floored at 1e-30 in
+  the log.  It is 0 on exact data and >= 0.
+* DM: beta = 1 difference map, Psi <- Psi + P_F(2 P_O Psi - Psi) - P_O Psi, with
+  P_O Psi = Phi formed from the current O, P; Psi starts at Phi.
+* Psi2ObjProbe: one Jacobi step (object and probe both from the same pre-update
+  O, P) with inertia: O <- (N_O + d_O O) / (D_O + d_O), d_O = alpha_O max D_O,
+  and likewise for P with d_P = alpha_P max D_P.
+* The per-cycle LLK is that of the wave being projected (Phi for AP, 2 Phi - Psi
+  for DM); ``llk`` gives the exact L(O, P).
+"""
+from __future__ import annotations
+
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.fft
+
+ICALC_FLOOR = 1e-30   # floor of the calculated intensity inside log and ratio
+AMP_FLOOR = 1e-20     # floor of the calculated amplitude in the projection
+STACK = 64            # frames per stack (the paper processes Psi in stacks of 16-128 frames)
+
+
+def _workers():
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+@dataclass
+class Data:
+    """PtychoData (paper Section 4): observed intensities, positions, mask."""
+
+    iobs: np.ndarray       # float64 (J, N, N), FFT order
+    positions: np.ndarray  # int64 (J, 2) top-left (row, col)
+    mask: np.ndarray       # bool (N, N), True = bad pixel (free)
+
+    @staticmethod
+    def make(iobs, positions, mask=None):
+        iobs = np.asarray(iobs, dtype=np.float64)
+        N = iobs.shape[-1]
+        if mask is None:
+            mask = np.zeros((N, N), dtype=bool)
+        return Data(iobs=iobs, positions=np.asarray(positions, dtype=np.int64),
+                    mask=np.asarray(mask).astype(bool))
+
+    @property
+    def J(self):
+        return self.iobs.shape[0]
+
+    @property
+    def N(self):
+        return self.iobs.shape[-1]
+
+
+# --------------------------------------------------------------------------
+# Operators (paper appendix, "Ptychography operators")
+# --------------------------------------------------------------------------
+
+def ft(x):
+    """FT: orthonormal 2D discrete Fourier transform over the last two axes."""
+    return scipy.fft.fft2(x, axes=(-2, -1), norm="ortho", workers=_workers())
+
+
+def ift(x):
+    """IFT: inverse of ``ft`` (its adjoint, as ``ft`` is unitary)."""
+    return scipy.fft.ifft2(x, axes=(-2, -1), norm="ortho", workers=_workers())
+
+
+def obj_probe_to_psi(obj, probe, positions):
+    """ObjProbe2Psi: Phi[j, k] = P_k * O[r_j : r_j + N, c_j : c_j + N]."""
+    K, N, _ = probe.shape
+    out = np.empty((len(positions), K, N, N), dtype=np.complex128)
+    for j, (r, c) in enumerate(positions):
+        out[j] = probe * obj[r:r + N, c:c + N][None]
+    return out
+
+
+def calc_intensity(psi_hat):
+    """Incoherent sum over probe modes: I_c = sum_k |Psi_hat_k|^2 (modes on axis -3)."""
+    return (psi_hat.real ** 2 + psi_hat.imag ** 2).sum(axis=-3)
+
+
+def apply_amplitude(psi_hat, iobs, mask):
+    """ApplyAmplitude: in Fourier space replace the modulus by the observed
+    amplitude, with one common factor for all modes; masked pixels unchanged.
+
+    psi_hat: (..., K, N, N); iobs: (..., N, N); mask: (N, N) bool.
+    """
+    ic = calc_intensity(psi_hat)
+    s = np.sqrt(np.maximum(iobs, 0.0)) / np.maximum(np.sqrt(ic), AMP_FLOOR)
+    s = np.where(mask, 1.0, s)
+    return psi_hat * s[..., None, :, :]
+
+
+def llk_terms(icalc, iobs, mask):
+    """Poisson log-likelihood per pixel (deviance form), 0 on masked pixels:
+    I_c - I_o + I_o ln(I_o / I_c), which is I_c where I_o = 0."""
+    io = np.maximum(iobs, 0.0)
+    ic = icalc
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = ic - io + np.where(io > 0, io * np.log(np.where(io > 0, io, 1.0) / np.maximum(ic, ICALC_FLOOR)), 0.0)
+    return np.where(mask, 0.0, t)
+
+
+def llk_poisson(icalc, iobs, mask):
+    """LLK operator: total Poisson log-likelihood (sum of ``llk_terms``)."""
+    return float(llk_terms(icalc, iobs, mask).sum())
+
+
+def psi_to_obj_probe_sums(psi, obj, probe, positions, shape_obj):
+    """Psi2ObjProbe accumulation (numerators and denominators), all from the
+    same O, P (Jacobi):
+
+      N_O(r_j + x) += sum_k conj(P_k(x)) Psi_jk(x)     D_O(r_j + x) += sum_k |P_k(x)|^2
+      N_Pk(x)      += conj(O(r_j + x)) Psi_jk(x)        D_P(x)       += |O(r_j + x)|^2
+    """
+    K, N, _ = probe.shape
+    n_o = np.zeros(shape_obj, dtype=np.complex128)
+    d_o = np.zeros(shape_obj, dtype=np.float64)
+    n_p = np.zeros((K, N, N), dtype=np.complex128)
+    d_p = np.zeros((N, N), dtype=np.float64)
+    p_conj = np.conj(probe)
+    p_pow = (probe.real ** 2 + probe.imag ** 2).sum(0)
+    for j, (r, c) in enumerate(positions):
+        patch = obj[r:r + N, c:c + N]
+        n_o[r:r + N, c:c + N] += (p_conj * psi[j]).sum(0)
+        d_o[r:r + N, c:c + N] += p_pow
+        n_p += np.conj(patch)[None] * psi[j]
+        d_p += patch.real ** 2 + patch.imag ** 2
+    return n_o, d_o, n_p, d_p
+
+
+def normalise(obj, probe, sums, alpha_obj=1e-2, alpha_probe=1e-2,
+              update_obj=True, update_probe=True):
+    """Psi2ObjProbe normalisation with inertia:
+    O <- (N_O + d_O O) / (D_O + d_O), d_O = alpha_O max D_O; same for P."""
+    n_o, d_o, n_p, d_p = sums
+    if update_obj:
+        delta = alpha_obj * d_o.max()
+        obj = (n_o + delta * obj) / (d_o + delta)
+    if update_probe:
+        delta = alpha_probe * d_p.max()
+        probe = (n_p + delta * probe) / (d_p + delta)[None]
+    return obj, probe
+
+
+def _stacks(J, stack=STACK):
+    for lo in range(0, J, stack):
+        yield lo, min(J, lo + stack)
+
+
+def _add_sums(acc, part):
+    if acc is None:
+        return [a.copy() for a in part]
+    for a, b in zip(acc, part):
+        a += b
+    return acc
+
+
+# --------------------------------------------------------------------------
+# Algorithms
+# --------------------------------------------------------------------------
+
+def ap_cycle(obj, probe, data: Data, alpha_obj=1e-2, alpha_probe=1e-2,
+             update_obj=True, update_probe=True):
+    """One Alternating Projections cycle (AP, Marchesini et al. 2013):
+    Psi_j = IFT(ApplyAmplitude(FT(Phi_j))), Phi = ObjProbe2Psi(O, P), then
+    Psi2ObjProbe.  Returns (obj, probe, llk of FT(Phi))."""
+    obj = np.asarray(obj, dtype=np.complex128)
+    probe = np.asarray(probe, dtype=np.complex128)
+    sums = None
+    llk = 0.0
+    for lo, hi in _stacks(data.J):
+        pos = data.positions[lo:hi]
+        phi = obj_probe_to_psi(obj, probe, pos)
+        phi_hat = ft(phi)
+        llk += llk_poisson(calc_intensity(phi_hat), data.iobs[lo:hi], data.mask)
+        psi = ift(apply_amplitude(phi_hat, data.iobs[lo:hi], data.mask))
+        sums = _add_sums(sums, psi_to_obj_probe_sums(psi, obj, probe, pos, obj.shape))
+    obj, probe = normalise(obj, probe, sums, alpha_obj, alpha_probe, update_obj, update_probe)
+    return obj, probe, llk
+
+
+def dm_cycle(obj, probe, psi, data: Data, alpha_obj=1e-2, alpha_probe=1e-2,
+             update_obj=True, update_probe=True, init_psi=False):
+    """One Difference Map cycle (beta = 1; Elser 2007, Thibault et al. 2008):
+    Phi = ObjProbe2Psi(O, P); X = 2 Phi - Psi;
+    Psi <- Psi + IFT(ApplyAmplitude(FT(X))) - Phi; then Psi2ObjProbe from the new Psi.
+    ``init_psi`` sets Psi = Phi first.  Returns (obj, probe, psi, llk of FT(X))."""
+    obj = np.asarray(obj, dtype=np.complex128)
+    probe = np.asarray(probe, dtype=np.complex128)
+    psi = np.array(psi, dtype=np.complex128, copy=True) if psi is not None else None
+    J = data.J
+    if init_psi or psi is None:
+        psi = np.empty((J,) + probe.shape, dtype=np.complex128)
+        init_psi = True
+    sums = None
+    llk = 0.0
+    for lo, hi in _stacks(J):
+        pos = data.positions[lo:hi]
+        phi = obj_probe_to_psi(obj, probe, pos)
+        if init_psi:
+            psi[lo:hi] = phi
+        x = 2.0 * phi - psi[lo:hi]
+        x_hat = ft(x)
+        llk += llk_poisson(calc_intensity(x_hat), data.iobs[lo:hi], data.mask)
+        x_proj = ift(apply_amplitude(x_hat, data.iobs[lo:hi], data.mask))
+        psi[lo:hi] = psi[lo:hi] + x_proj - phi
+        sums = _add_sums(sums, psi_to_obj_probe_sums(psi[lo:hi], obj, probe, pos, obj.shape))
+    obj, probe = normalise(obj, probe, sums, alpha_obj, alpha_probe, update_obj, update_probe)
+    return obj, probe, psi, llk
+
+
+def llk(obj, probe, data: Data):
+    """Exact Poisson LLK of (O, P): LLK operator applied to FT(ObjProbe2Psi(O, P))."""
+    obj = np.asarray(obj, dtype=np.complex128)
+    probe = np.asarray(probe, dtype=np.complex128)
+    total = 0.0
+    for lo, hi in _stacks(data.J):
+        phi_hat = ft(obj_probe_to_psi(obj, probe, data.positions[lo:hi]))
+        total += llk_poisson(calc_intensity(phi_hat), data.iobs[lo:hi], data.mask)
+    return total
+
+
+def ml_grad(obj, probe, data: Data):
+    """Gradient of the Poisson LLK (ML, Thibault & Guizar-Sicairos 2012).
+
+    L(O, P) = sum_j sum_unmasked [I_c - I_o ln I_c] (+ a constant; same gradient
+    as the deviance returned by ``llk``), I_c = sum_k |FT(Phi_jk)|^2.
+    With z complex, the returned gradient is dL/dRe z + i dL/dIm z:
+
+      G_O(r_j + x) = sum_jk conj(P_k(x)) IFT[w_j FT(Phi_jk)](x)
+      G_Pk(x)      = sum_j  conj(O(r_j + x)) IFT[w_j FT(Phi_jk)](x)
+      w_j = 2 (1 - I_o / I_c) on unmasked pixels, 0 on masked ones.
+
+    Returns (llk deviance, G_O, G_P)."""
+    obj = np.asarray(obj, dtype=np.complex128)
+    probe = np.asarray(probe, dtype=np.complex128)
+    K, N, _ = probe.shape
+    g_o = np.zeros(obj.shape, dtype=np.complex128)
+    g_p = np.zeros(probe.shape, dtype=np.complex128)
+    total = 0.0
+    for lo, hi in _stacks(data.J):
+        pos = data.positions[lo:hi]
+        phi_hat = ft(obj_probe_to_psi(obj, probe, pos))
+        ic = calc_intensity(phi_hat)
+        io = np.maximum(data.iobs[lo:hi], 0.0)
+        total += llk_poisson(ic, data.iobs[lo:hi], data.mask)
+        w = np.where(data.mask, 0.0, 2.0 * (1.0 - io / np.maximum(ic, ICALC_FLOOR)))
+        back = ift(phi_hat * w[:, None])
+        for i, (r, c) in enumerate(pos):
+            patch = obj[r:r + N, c:c + N]
+            g_o[r:r + N, c:c + N] += (np.conj(probe) * back[i]).sum(0)
+            g_p += np.conj(patch)[None] * back[i]
+    return total, g_o, g_p
+
+
+def cycles(algorithm, obj, probe, data: Data, n, psi=None, init_psi=True, **kw):
+    """Run ``n`` AP or DM cycles; returns (obj, probe, psi, [llk per cycle])."""
+    llks = []
+    for i in range(n):
+        if algorithm == "AP":
+            obj, probe, l = ap_cycle(obj, probe, data, **kw)
+        elif algorithm == "DM":
+            obj, probe, psi, l = dm_cycle(obj, probe, psi, data, init_psi=(init_psi and i == 0), **kw)
+        else:
+            raise ValueError(algorithm)
+        llks.append(l)
+    return obj, probe, psi, llks
+
+
+# --------------------------------------------------------------------------
+# Sampled outputs for full-size checks: values the oracle can compute one frame
+# or one object pixel at a time.
+# --------------------------------------------------------------------------
+
+def dm_frame_update(obj, probe, psi_j, iobs_j, pos_j, mask, init_psi=False):
+    """New Psi_j and the LLK of frame j for one DM step (the frame's part of
+    ``dm_cycle``).  Returns (psi_new_j, llk_j)."""
+    obj = np.asarray(obj, dtype=np.complex128)
+    probe = np.asarray(probe, dtype=np.complex128)
+    phi = obj_probe_to_psi(obj, probe, np.asarray([pos_j]))[0]
+    psi_j = phi if init_psi else np.asarray(psi_j, dtype=np.complex128)
+    x_hat = ft(2.0 * phi - psi_j)
+    l = llk_poisson(calc_intensity(x_hat), np.asarray(iobs_j, np.float64), mask)
+    return psi_j + ift(apply_amplitude(x_hat, np.asarray(iobs_j, np.float64), mask)) - phi, l
+
+
+def frames_llk(obj, probe, data: Data, frames):
+    """Exact LLK of a subset of frames."""
+    obj = np.asarray(obj, dtype=np.complex128)
+    probe = np.asarray(probe, dtype=np.complex128)
+    frames = np.asarray(frames)
+    phi_hat = ft(obj_probe_to_psi(obj, probe, data.positions[frames]))
+    return llk_poisson(calc_intensity(phi_hat), data.iobs[frames], data.mask)
+
+
+def object_denominator(probe, positions, shape_obj):
+    """D_O = sum_j sum_k |P_k(x)|^2 placed at r_j + x (needs no transforms)."""
+    K, N, _ = probe.shape
+    p_pow = (np.abs(np.asarray(probe, np.complex128)) ** 2).sum(0)
+    d_o = np.zeros(shape_obj, dtype=np.float64)
+    for r, c in positions:
+        d_o[r:r + N, c:c + N] += p_pow
+    return d_o
+
+
+def frames_covering(positions, N, pixel):
+    """Indices j whose N x N patch contains object pixel (row, col)."""
+    y, x = pixel
+    p = np.asarray(positions)
+    sel = (p[:, 0] <= y) & (y < p[:, 0] + N) & (p[:, 1] <= x) & (x < p[:, 1] + N)
+    return np.nonzero(sel)[0]
+
+
+__all__ = [
+    "Data", "ft", "ift", "obj_probe_to_psi", "calc_intensity", "apply_amplitude", "llk_terms",
+    "llk_poisson", "psi_to_obj_probe_sums", "normalise", "ap_cycle", "dm_cycle", "llk", "ml_grad",
+    "cycles", "dm_frame_update", "frames_llk", "object_denominator", "frames_covering",
+    "ICALC_FLOOR", "AMP_FLOOR", "STACK",
+]
+
+
+def unit_count(data: Data) -> int:
+    """Number of unmasked detector pixels over all frames (the LLK normaliser)."""
+    return int((~data.mask).sum()) * data.J
+
