@@ -1,0 +1,361 @@
+"""Benchmark: difference-map cycle throughput on 256x256 frames (frames/s) and
+its fraction of the HBM roof, on one GB300 per process.
+
+Workload (one "step" = one full DM cycle over every frame): 4000 frames of
+256 x 256 on a Fermat spiral over a 2048 x 2048 object, one probe mode, 1e6
+photons per frame, a 2 % detector-gap mask; the synthetic stand-in for the
+paper's far-field ptychography workloads (Table 1: 1000 x 256^2 frames).
+
+Arms:
+  default          libptycho CUDA path (CUDA graph replay of the cycle)
+  --impl reference the FP64 CPU oracle (the only reference there is for this
+                   method), timed on a bounded sample of the same workload
+
+Output: one JSON line on rank 0.  Multi-GPU (torchrun): every rank runs an
+independent replica of the workload (the DM cycle over one object has no
+independent partition without a per-cycle all-reduce); value = frames of all
+ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DM-cycle frames/s at 256² (plain FP32 vs chosen form, same GB300); % HBM roof"
+UNIT = "frames/s"
+WORKLOAD = "dm256"
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def workload_desc(s):
+    return (f"DM cycle, {s.J} frames {s.N}x{s.N}, object {s.Ho}x{s.Wo}, K={s.K}, "
+            f"{s.photons:.0e} photons/frame, {100 * s.mask.mean():.1f}% mask, spiral step {s.step_px:.1f} px")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured", "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0))}
+    return {"hbm_gbs": 6800.0, "src": "fallback", "sm_max_mhz": 2070.0}
+
+
+def alg_bytes_per_cycle(s, algo="DM"):
+    """Bytes the method must move per cycle: Psi read + write (DM), I read, O and P read + write."""
+    px = s.N * s.N
+    b = s.J * px * 4 + s.Ho * s.Wo * 16 + s.K * px * 16
+    if algo == "DM":
+        b += s.J * s.K * px * 16
+    return b
+
+
+# per-kernel algorithmic HBM bytes per frame (DM) and nominal flops per frame
+def kernel_models(s):
+    import math
+    px = s.N * s.N
+    K = s.K
+    fft1d = 5.0 * px * math.log2(s.N)  # one 1D pass over all rows (or columns) of a frame
+    return {
+        "row_fwd": {"bytes": K * px * 8, "flops": K * (fft1d + 10.0 * px)},
+        "col": {"bytes": px * 4, "flops": K * (2 * fft1d + 12.0 * px) + 30.0 * px},
+        "row_bwd": {"bytes": K * px * 8, "flops": K * (fft1d + 24.0 * px) + 4.0 * px},
+    }
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2008_11511_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    p = os.path.join(PROFILES, "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    ent = d.get(kernel)
+    if not ent or ent.get("source_hash") != source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch_full")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        med = statistics.median(sms) if sms else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def dist_init():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample_rate(s, seconds=15.0, min_frames=32):
+    """FP64 oracle DM-cycle throughput (frames/s) on a bounded sample of the
+    workload's frames (same object, probe, mask and intensities)."""
+    import oracle
+    J = min_frames
+    while True:
+        idx = np.linspace(0, s.J - 1, J).astype(np.int64)
+        data = oracle.Data.make(s.iobs[idx], s.positions[idx], s.mask)
+        t0 = time.perf_counter()
+        oracle.dm_cycle(s.obj0, s.probe0, None, data, init_psi=True)
+        dt = time.perf_counter() - t0
+        if dt >= seconds / 4 or J >= s.J:
+            return J / dt, J, dt
+        J = min(s.J, int(J * max(2.0, seconds / 4 / max(dt, 1e-3))))
+
+
+def run_reference(args):
+    """The oracle as the reference arm (rank 0 only)."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from synthetic import make_config
+    s = make_config(WORKLOAD)
+    cores = len(os.sched_getaffinity(0))
+    # size one step so that warmup + steps stay within a few minutes
+    rate, J, dt = oracle_sample_rate(s, seconds=8.0)
+    idx = np.linspace(0, s.J - 1, J).astype(np.int64)
+    data = oracle.Data.make(s.iobs[idx], s.positions[idx], s.mask)
+    obj, probe, psi = s.obj0, s.probe0, None
+    for w in range(args.warmup):
+        obj, probe, psi, _ = oracle.dm_cycle(obj, probe, psi, data, init_psi=(w == 0))
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        obj, probe, psi, _ = oracle.dm_cycle(obj, probe, psi, data, init_psi=(psi is None))
+    el = time.perf_counter() - t0
+    value = J * args.steps / el
+    sample = f"{J} of {s.J} frames per step (evenly spaced), full 2048^2 object, FP64 NumPy/SciPy"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "desc": workload_desc(s), "form": "fp64 oracle",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_init()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2008_11511_gb300 import Ptycho, _lib
+    from synthetic import make_config
+    s = make_config(WORKLOAD)
+    obj = torch.tensor(s.obj0, device=dev)
+    probe = torch.tensor(s.probe0, device=dev)
+    iobs = torch.tensor(s.iobs, device=dev)
+    pb = Ptycho(obj, probe, iobs, s.positions, s.mask, with_psi=True)
+    stream = torch.cuda.current_stream(dev)
+    llk_buf = torch.empty(max(args.steps, args.warmup, 1), dtype=torch.float64, device=dev)
+
+    # warm-up (the first cycle initialises Psi and captures the CUDA graphs)
+    pb.dm(args.warmup, init_psi=True, llk=llk_buf)
+    pb.dm(1, llk=llk_buf)
+    torch.cuda.synchronize(dev)
+
+    # timed region: K DM cycles (inputs ~3 GB >> 129 MB L2, so no flush is needed)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pb.dm(args.steps, llk=llk_buf)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, ws)
+    value = s.J * args.steps * ws / (ms_max / 1e3)
+    ms_per_step = ms_max / args.steps
+
+    # per-kernel durations, live, with events on the launch stream (direct launches)
+    _lib.call("ptx_profile_enable", pb._handle(), 1)
+    pb.dm(args.steps, llk=llk_buf)
+    torch.cuda.synchronize(dev)
+    import ctypes
+    nk = len(_lib.KERNEL_KINDS)
+    launches = (ctypes.c_int64 * nk)()
+    tot = (ctypes.c_double * nk)()
+    _lib.call("ptx_profile_read", pb._handle(), nk, launches, tot)
+    _lib.call("ptx_profile_enable", pb._handle(), 0)
+    kstats = {name: {"launches": int(launches[i]), "total_ms": float(tot[i]),
+                     "avg_us": (1e3 * tot[i] / launches[i]) if launches[i] else None}
+              for i, name in enumerate(_lib.KERNEL_KINDS)}
+    tot_ms = sum(v["total_ms"] for v in kstats.values()) or 1.0
+    for v in kstats.values():
+        v["share"] = v["total_ms"] / tot_ms
+
+    # end to end through the public API with host buffers: every step copies the
+    # intensity stack in from pinned host memory and reads the cycle's LLK back
+    host_iobs = torch.from_numpy(s.iobs).pin_memory()
+    host_llk = torch.empty(1, dtype=torch.float64).pin_memory()
+    e_steps = max(1, min(args.steps, 10))
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        iobs.copy_(host_iobs, non_blocking=True)
+        l = pb.dm(1, llk=llk_buf)
+        host_llk.copy_(l[:1], non_blocking=True)
+        stream.synchronize()
+    el = time.perf_counter() - t0
+    barrier(ws)
+    el = max_over_ranks(el, ws)
+    e2e_value = s.J * e_steps * ws / el
+
+    # roofline: the dominant kernel by time share
+    pk = peaks()
+    models = kernel_models(s)
+    dom = max(("row_fwd", "col", "row_bwd"), key=lambda k: kstats[k]["total_ms"])
+    ks = kstats[dom]
+    nframes_per_launch = s.J * args.steps / ks["launches"]
+    flops = models[dom]["flops"] * nframes_per_launch
+    alu_peak_tflops = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    achieved_tflops = flops / (ks["avg_us"] * 1e-6) / 1e12
+    traffic = ncu_traffic(dom)
+    roof = {"kernel": dom, "bound": "alu", "achieved": achieved_tflops, "peak": alu_peak_tflops,
+            "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak_tflops,
+            "peak_src": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived)",
+            "flops_per_launch": flops, "alg_bytes_per_launch": models[dom]["bytes"] * nframes_per_launch,
+            "traffic": traffic}
+    cyc_bytes = alg_bytes_per_cycle(s, "DM")
+    cyc_gbs = cyc_bytes / (ms_per_step * 1e-3) / 1e9
+    roof_cycle = {"bound": "hbm", "achieved": cyc_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                  "frac": cyc_gbs / pk["hbm_gbs"], "peak_src": pk["src"], "alg_bytes_per_cycle": cyc_bytes}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, J, dt = oracle_sample_rate(s, seconds=args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+               "sample": f"one FP64 DM cycle on {J} of {s.J} frames (evenly spaced), full object; {dt:.1f} s"}
+
+    per_cycle_launches = kstats["row_fwd"]["launches"] + kstats["col"]["launches"] + kstats["row_bwd"]["launches"] \
+        + kstats["den_max"]["launches"] + kstats["normalise"]["launches"] + kstats["cycle_end"]["launches"]
+    gpu_launches = per_cycle_launches + 1  # + the per-call control kernel
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "desc": workload_desc(s), "form": "fp32 (plain)",
+                           "parallelism": f"replicas x{ws}",
+                           "l2": "inputs larger than L2 (Psi 2.1 GB + I 1.05 GB per replica); no flush"},
+                "roofline": roof, "roofline_cycle": roof_cycle, "kernels": kstats,
+                "clocks": clk, "gpu_launches": gpu_launches,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(s.iobs.nbytes),
+                        "d2h_bytes_per_step": 8, "steps": e_steps},
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    pb.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

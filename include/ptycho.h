@@ -1,0 +1,181 @@
+/*
+ * libptycho - far-field ptychography projection cycle on one NVIDIA GB300 (sm_103a).
+ *
+ * The operations follow the ptychography operators of Favre-Nicolin et al.,
+ * "PyNX: high performance computing toolkit for coherent X-ray imaging based on
+ * operators" (2020): ObjProbe2Psi, FT / IFT, ApplyAmplitude, Psi2ObjProbe, AP,
+ * DM, LLK and ML (appendix operator table; feature list of Section 4).
+ *
+ * Conventions for every entry point:
+ *   - Complex arrays are complex64 (interleaved float re, im), C-contiguous.
+ *   - A position (row, col) is the top-left corner of the frame's N x N object
+ *     patch: the exit wave of frame j, mode k is Phi_jk(y, x) = P_k(y, x) O(row_j + y, col_j + x)
+ *     (the paper's Psi_j(r) = O(r) P(r - r_j), Section 4 / operator table).
+ *   - The 2D Fourier transform is orthonormal (forward and inverse both scaled
+ *     by 1/N); intensities and the mask are in FFT order (zero frequency at [0][0]).
+ *   - "device" pointers are CUDA global-memory pointers on the current device;
+ *     "host" pointers are ordinary process memory.  The caller owns every array it
+ *     passes; the library never frees caller memory.
+ *   - A stream argument is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on that stream: arguments are checked on
+ *     the host before anything is enqueued, results are valid once the stream
+ *     has reached the call.  No entry point except ptx_create allocates device
+ *     memory, and none synchronises the host with the device after ptx_create.
+ *   - Errors come back as a ptx_status; ptx_last_error() gives the text of the
+ *     last failure on the calling thread.  Nothing is enqueued when a call fails
+ *     its argument checks.
+ */
+#ifndef LIBPTYCHO_PTYCHO_H
+#define LIBPTYCHO_PTYCHO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ptx_handle ptx_handle; /* opaque, owned by the library */
+
+typedef enum {
+    PTX_OK = 0,
+    PTX_ERR_INVALID_ARG = 1,   /* null pointer, non-positive size, bad flag or name */
+    PTX_ERR_UNSUPPORTED = 2,   /* frame size N not in the supported set, K > PTX_MAX_MODES */
+    PTX_ERR_OUT_OF_BOUNDS = 3, /* a position puts its patch outside the object */
+    PTX_ERR_CUDA = 4,          /* a CUDA runtime call failed (text in ptx_last_error) */
+    PTX_ERR_TIMEOUT = 5,       /* reserved: a bounded device-side wait gave up */
+    PTX_ERR_NOT_READY = 6      /* scratch too small or handle in an unusable state */
+} ptx_status;
+
+/* Flags of the cycle calls (bitwise OR). */
+#define PTX_UPDATE_OBJ   0x1u  /* update the object (Psi2ObjProbe numerator N_O / denominator D_O) */
+#define PTX_UPDATE_PROBE 0x2u  /* update the probe modes (N_P / D_P) */
+#define PTX_DM_INIT_PSI  0x4u  /* DM only: set Psi = P . O[r_j] before the first cycle */
+#define PTX_NO_NORMALISE 0x8u  /* accumulate N_O, D_O, N_P, D_P but do not normalise (data-parallel split) */
+#define PTX_NO_GRAPH     0x10u /* enqueue kernels directly instead of replaying a captured CUDA graph */
+
+#define PTX_MAX_MODES 8
+
+/* Supported frame sizes N (N x N frames): products of 2 and 3 that the
+ * kernels are built for. */
+#define PTX_SUPPORTED_SIZES {8, 12, 16, 32, 64, 128, 192, 256, 384, 512}
+
+/* One ptychography problem (the paper's PtychoData plus the current Ptycho
+ * object and probe, Section 4). */
+typedef struct {
+    int32_t N;              /* frame size: N x N detector pixels */
+    int32_t K;              /* number of incoherent probe modes, 1..PTX_MAX_MODES */
+    int32_t J;              /* number of scan positions (frames), >= 1 */
+    int32_t Ho, Wo;         /* object height and width, each >= N */
+    void* obj;              /* device complex64 [Ho][Wo]; updated in place by the cycles */
+    void* probe;            /* device complex64 [K][N][N]; updated in place by the cycles */
+    const int32_t* positions; /* host int32 [J][2] (row, col) top-left corners; copied at create;
+                                 each must satisfy 0 <= row <= Ho-N, 0 <= col <= Wo-N */
+    const float* iobs;      /* device float32 [J][N][N] observed intensities, FFT order; borrowed,
+                               read-only, must stay valid for the handle's lifetime; negative
+                               values are treated as 0 */
+    const uint8_t* mask;    /* host uint8 [N][N], nonzero = bad pixel (left free by the projection,
+                               excluded from the LLK and its gradient); NULL = no mask; copied */
+    void* psi;              /* device complex64 [J][K][N][N] exit-wave stack Psi, needed by DM
+                               (the Ptycho object's Psi array); may be NULL for AP, LLK and ML */
+} ptx_problem;
+
+/* Device scratch needed by ptx_create for these problems, in bytes.  The caller
+ * allocates it (e.g. with torch.empty) and keeps it alive until ptx_destroy.  It
+ * holds the copied positions and mask, the Fourier-space work stack of one
+ * batch of frames, the object / probe numerator-denominator accumulators and
+ * the FP64 log-likelihood partial sums. */
+ptx_status ptx_workspace_bytes(const ptx_problem* probs, int32_t nprob, size_t* scratch_bytes);
+
+/* Create a handle for nprob problems (nprob = 1 for a single scan).  `probs` is
+ * copied; the device arrays it points to are borrowed.  `scratch` is a device
+ * buffer of at least ptx_workspace_bytes() bytes, 256-byte aligned.  Copies the
+ * positions and the mask into scratch on `stream`, zeroes the accumulators and
+ * waits for these copies (the only host synchronisation of the library).  Returns PTX_ERR_OUT_OF_BOUNDS for a position outside the
+ * object, PTX_ERR_UNSUPPORTED for an unsupported N or K. */
+ptx_status ptx_create(ptx_handle** out, const ptx_problem* probs, int32_t nprob,
+                      void* scratch, size_t scratch_bytes, void* stream);
+
+/* Alternating-projection cycles (the AP operator; Marchesini et al. 2013 as cited
+ * in Section 4): per cycle, Phi = ObjProbe2Psi(O, P); Psi = IFT(ApplyAmplitude(FT(Phi)));
+ * Psi2ObjProbe (numerators and denominators from the same O, P), then the
+ * normalisation O <- (N_O + d_O O) / (D_O + d_O), d_O = alpha_obj max D_O, and the same
+ * for P.  llk_dev: device double [ncycles * nprob]; entry [c * nprob + p] receives the
+ * Poisson LLK (deviance form) of FT(Phi) in cycle c of problem p.  Psi is not stored. */
+ptx_status ptx_ap_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, double* llk_dev, void* stream);
+
+/* Difference-map cycles (the DM operator, beta = 1; Elser 2007 as cited in
+ * Section 4): Phi = ObjProbe2Psi(O, P); X = 2 Phi - Psi;
+ * Psi <- Psi + IFT(ApplyAmplitude(FT(X))) - Phi; then Psi2ObjProbe from the new Psi and
+ * the normalisation as for AP.  Needs probs[p].psi.  With PTX_DM_INIT_PSI, Psi = Phi is
+ * set at the first cycle.  llk_dev as for AP, with the LLK of FT(X). */
+ptx_status ptx_dm_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, double* llk_dev, void* stream);
+
+/* Exact Poisson log-likelihood of the current (O, P) (the LLK operator):
+ * sum over frames and unmasked pixels of I_c - I_o + I_o ln(I_o / I_c) (I_c where
+ * I_o = 0), I_c = sum_k |FT(Phi_jk)|^2.  Writes nprob doubles to llk_dev. */
+ptx_status ptx_llk(ptx_handle* h, double* llk_dev, void* stream);
+
+/* Gradient of the Poisson LLK with respect to the object and the probe (the
+ * ML operator's gradient; Thibault & Guizar-Sicairos 2012 as cited in Section 4):
+ * G = dL/dRe z + i dL/dIm z, i.e.
+ *   G_O(r_j + x) = sum_jk conj(P_k(x)) IFT[w_j FT(Phi_jk)](x),
+ *   G_Pk(x)      = sum_j conj(O(r_j + x)) IFT[w_j FT(Phi_jk)](x),
+ *   w_j = 2 (1 - I_o / I_c) on unmasked pixels, 0 on masked ones.
+ * grad_obj: device complex64 [Ho][Wo], grad_probe: device complex64 [K][N][N]
+ * (problem 0; nprob must be 1), both overwritten.  Either may be NULL to skip it.
+ * llk_dev (may be NULL) receives the LLK.  Psi is recomputed, never stored. */
+ptx_status ptx_ml_grad(ptx_handle* h, void* grad_obj, void* grad_probe, double* llk_dev, void* stream);
+
+/* Normalise O and P from the accumulated numerators / denominators and clear
+ * them (the second half of Psi2ObjProbe); used after cycles run with
+ * PTX_NO_NORMALISE once the accumulators of several GPUs have been summed. */
+ptx_status ptx_normalise(ptx_handle* h, uint32_t flags, void* stream);
+
+/* Device addresses of problem p's accumulators (for an all-reduce across GPUs):
+ * obj_acc = float32 [Ho][Wo][4] {Re N_O, Im N_O, D_O, 0}; probe_acc = float32
+ * [K][N][N][4] {Re N_Pk, Im N_Pk, D_P, 0}. */
+ptx_status ptx_accumulators(ptx_handle* h, int32_t p, void** obj_acc, size_t* obj_acc_bytes,
+                            void** probe_acc, size_t* probe_acc_bytes);
+
+/* Set a scalar parameter: "alpha_obj" or "alpha_probe" (inertia factors of the
+ * normalisation, default 0.01 each, must be >= 0). */
+ptx_status ptx_set_param(ptx_handle* h, const char* name, double value);
+
+/* In-place orthonormal 2D FFT of `nframes` N x N complex64 frames (the FT
+ * operator for direction = -1, IFT for direction = +1): X[ky][kx] =
+ * (1/N) sum_{y,x} x[y][x] exp(direction * 2 pi i (ky y + kx x) / N).
+ * data: device complex64 [nframes][N][N]. */
+ptx_status ptx_fft2(void* data, int32_t nframes, int32_t N, int32_t direction, void* stream);
+
+/* Kernel kinds reported by ptx_profile_read. */
+#define PTX_KERNEL_ROW_FWD   0 /* gather x probe, (2 Phi - Psi), forward row FFT */
+#define PTX_KERNEL_COL       1 /* column FFT, amplitude projection + LLK, inverse column FFT */
+#define PTX_KERNEL_ROW_BWD   2 /* inverse row FFT, Psi update, Psi2ObjProbe scatter */
+#define PTX_KERNEL_DEN_MAX   3 /* max of the denominators */
+#define PTX_KERNEL_NORMALISE 4 /* normalisation of O and P */
+#define PTX_KERNEL_CYCLE_END 5 /* FP64 LLK reduction of the cycle */
+#define PTX_KERNEL_KINDS     6
+
+/* Per-kernel timing for measurement.  While enabled, the cycle calls launch
+ * their kernels directly (no CUDA graph) and bracket every launch with CUDA
+ * events recorded on the launch stream.  Enabling resets the counters. */
+ptx_status ptx_profile_enable(ptx_handle* h, int32_t enable);
+
+/* Wait for the recorded events and return, for each of the first `nkinds`
+ * kernel kinds, the number of launches (host int64 array) and their summed
+ * duration in milliseconds (host double array) since profiling was enabled. */
+ptx_status ptx_profile_read(ptx_handle* h, int32_t nkinds, int64_t* launches, double* total_ms);
+
+/* Text of the last failure on the calling thread ("" if none). */
+const char* ptx_last_error(void);
+
+/* Destroy a handle (waits for nothing; the caller must make sure no call on it is
+ * still running on the GPU before freeing the scratch).  NULL is ignored. */
+void ptx_destroy(ptx_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBPTYCHO_PTYCHO_H */

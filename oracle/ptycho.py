@@ -166,14 +166,20 @@ def psi_to_obj_probe_sums(psi, obj, probe, positions, shape_obj):
 def normalise(obj, probe, sums, alpha_obj=1e-2, alpha_probe=1e-2,
               update_obj=True, update_probe=True):
     """Psi2ObjProbe normalisation with inertia:
-    O <- (N_O + d_O O) / (D_O + d_O), d_O = alpha_O max D_O; same for P."""
+    O <- (N_O + d_O O) / (D_O + d_O), d_O = alpha_O max D_O; same for P.
+    A pixel whose denominator D + d is zero (alpha = 0 and never illuminated)
+    keeps its value (the paper is silent on this case)."""
     n_o, d_o, n_p, d_p = sums
     if update_obj:
         delta = alpha_obj * d_o.max()
-        obj = (n_o + delta * obj) / (d_o + delta)
+        den = d_o + delta
+        with np.errstate(divide="ignore", invalid="ignore"):
+            obj = np.where(den > 0, (n_o + delta * obj) / den, obj)
     if update_probe:
         delta = alpha_probe * d_p.max()
-        probe = (n_p + delta * probe) / (d_p + delta)[None]
+        den = (d_p + delta)[None]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            probe = np.where(den > 0, (n_p + delta * probe) / den, probe)
     return obj, probe
 
 

@@ -1,0 +1,635 @@
+// libptycho C ABI: argument checks, scratch layout, batch scheduling and
+// CUDA-graph replay of the cycle.  The operations themselves are the kernels of
+// kernels.cuh; this file only validates, lays out memory and enqueues.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ptycho.h"
+#include "kernels.cuh"
+
+namespace ptx {
+const KernelSet* kernel_set_8();
+const KernelSet* kernel_set_12();
+const KernelSet* kernel_set_16();
+const KernelSet* kernel_set_32();
+const KernelSet* kernel_set_64();
+const KernelSet* kernel_set_128();
+const KernelSet* kernel_set_192();
+const KernelSet* kernel_set_256();
+const KernelSet* kernel_set_384();
+const KernelSet* kernel_set_512();
+cudaError_t set_attrs_8();
+cudaError_t set_attrs_12();
+cudaError_t set_attrs_16();
+cudaError_t set_attrs_32();
+cudaError_t set_attrs_64();
+cudaError_t set_attrs_128();
+cudaError_t set_attrs_192();
+cudaError_t set_attrs_256();
+cudaError_t set_attrs_384();
+cudaError_t set_attrs_512();
+
+const KernelSet* kernel_set(int N) {
+    switch (N) {
+        case 8: return kernel_set_8();
+        case 12: return kernel_set_12();
+        case 16: return kernel_set_16();
+        case 32: return kernel_set_32();
+        case 64: return kernel_set_64();
+        case 128: return kernel_set_128();
+        case 192: return kernel_set_192();
+        case 256: return kernel_set_256();
+        case 384: return kernel_set_384();
+        case 512: return kernel_set_512();
+        default: return nullptr;
+    }
+}
+
+// Raise the dynamic shared-memory limit of every kernel once per device.
+static cudaError_t ensure_attributes() {
+    static int done_mask = 0;  // bit per device ordinal < 32
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 32 && (done_mask >> dev) & 1) return cudaSuccess;
+    cudaError_t (*fns[])() = {set_attrs_8,   set_attrs_12,  set_attrs_16,  set_attrs_32,  set_attrs_64,
+                              set_attrs_128, set_attrs_192, set_attrs_256, set_attrs_384, set_attrs_512};
+    for (auto f : fns)
+        if ((e = f()) != cudaSuccess) return e;
+    if (dev < 32) done_mask |= 1 << dev;
+    return cudaSuccess;
+}
+}  // namespace ptx
+
+using namespace ptx;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ptx_status fail(ptx_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+ptx_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(PTX_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Default size of the Fourier-space batch work stack: small enough to stay
+// resident in the 129 MB L2 together with the streamed exit waves.
+constexpr size_t kSpecBudget = (size_t)64 << 20;
+
+struct Layout {
+    size_t pos, mask, acc_obj, acc_probe, llk_part, maxbits;
+    size_t end;
+};
+
+struct ProbHost {
+    ptx_problem p;
+    const KernelSet* ks = nullptr;
+    int L1 = 1, C2 = 1, L3 = 1;
+    int B = 1;   // frames per batch
+    int G3 = 1;  // frame groups of row_bwd
+    Layout lay{};
+    ProbArgs args{};
+};
+
+int choose_lines(int N, int K, int maxl) {
+    int L = 1;
+    while (K * L * 2 <= maxl && N % (L * 2) == 0) L *= 2;
+    return L;
+}
+
+bool supported_N(int N) {
+    static const int sizes[] = PTX_SUPPORTED_SIZES;
+    for (int s : sizes)
+        if (s == N) return true;
+    return false;
+}
+
+ptx_status check_problem(const ptx_problem& p, int idx) {
+    if (!supported_N(p.N)) return fail(PTX_ERR_UNSUPPORTED, "problem %d: frame size N=%d is not supported", idx, p.N);
+    if (p.K < 1 || p.K > PTX_MAX_MODES)
+        return fail(p.K < 1 ? PTX_ERR_INVALID_ARG : PTX_ERR_UNSUPPORTED, "problem %d: K=%d modes (1..%d)", idx, p.K,
+                    PTX_MAX_MODES);
+    if (p.J < 1) return fail(PTX_ERR_INVALID_ARG, "problem %d: J=%d must be >= 1", idx, p.J);
+    if (p.Ho < p.N || p.Wo < p.N)
+        return fail(PTX_ERR_INVALID_ARG, "problem %d: object %dx%d smaller than the frame %d", idx, p.Ho, p.Wo, p.N);
+    if (!p.obj || !p.probe || !p.positions || !p.iobs)
+        return fail(PTX_ERR_INVALID_ARG, "problem %d: obj, probe, positions and iobs must be non-null", idx);
+    for (int j = 0; j < p.J; ++j) {
+        const int r = p.positions[2 * j], c = p.positions[2 * j + 1];
+        if (r < 0 || c < 0 || r > p.Ho - p.N || c > p.Wo - p.N)
+            return fail(PTX_ERR_OUT_OF_BOUNDS, "problem %d: position %d = (%d, %d) puts the %dx%d patch outside the %dx%d object",
+                        idx, j, r, c, p.N, p.N, p.Ho, p.Wo);
+    }
+    return PTX_OK;
+}
+
+void plan_problem(ProbHost& h) {
+    const ptx_problem& p = h.p;
+    h.ks = kernel_set(p.N);
+    const int maxl = h.ks->max_lines;
+    h.L1 = choose_lines(p.N, p.K, maxl);
+    h.C2 = choose_lines(p.N, p.K, maxl);
+    h.L3 = choose_lines(p.N, p.K, maxl);
+    const size_t frame_bytes = (size_t)p.K * p.N * p.N * sizeof(float2);
+    size_t B = kSpecBudget / frame_bytes;
+    if (B < 1) B = 1;
+    if (B > (size_t)p.J) B = p.J;
+    if (B > 32768) B = 32768;  // grid.y limit of the batch kernels
+    h.B = (int)B;
+    const int rowblk = p.N / h.L3;
+    int G = (2 * 152 + rowblk - 1) / rowblk;
+    if (G > h.B) G = h.B;
+    if (G < 1) G = 1;
+    h.G3 = G;
+}
+
+// Per-problem regions (offsets relative to the problem's base).
+size_t layout_problem(ProbHost& h) {
+    const ptx_problem& p = h.p;
+    size_t o = 0;
+    h.lay.pos = o;
+    o = align_up(o + sizeof(int2) * (size_t)p.J);
+    h.lay.mask = o;
+    o = align_up(o + (size_t)p.N * p.N);
+    h.lay.acc_obj = o;
+    o = align_up(o + sizeof(float4) * (size_t)p.Ho * p.Wo);
+    h.lay.acc_probe = o;
+    o = align_up(o + sizeof(float4) * (size_t)p.K * p.N * p.N);
+    h.lay.llk_part = o;
+    o = align_up(o + sizeof(double) * (size_t)p.J * (p.N / h.C2));
+    h.lay.maxbits = o;
+    o = align_up(o + 2 * sizeof(unsigned));
+    h.lay.end = o;
+    return o;
+}
+
+struct GraphKey {
+    int algo;
+    uint32_t flags;
+    bool operator<(const GraphKey& o) const { return algo != o.algo ? algo < o.algo : flags < o.flags; }
+};
+
+}  // namespace
+
+struct ptx_handle {
+    std::vector<ProbHost> probs;
+    char* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    size_t spec_off = 0, ctl_off = 0;
+    Ctl* ctl = nullptr;
+    double alpha_obj = 1e-2, alpha_probe = 1e-2;
+    int device = 0;
+    cudaStream_t cap_stream = nullptr;
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    // per-kernel timing (ptx_profile_enable)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_used;  // (kind, index of the start event in ev_pool)
+};
+
+namespace {
+
+ptx_status compute_layout(std::vector<ProbHost>& probs, size_t* spec_off, size_t* ctl_off, size_t* total) {
+    size_t o = 0;
+    size_t spec = 0;
+    for (auto& h : probs) {
+        plan_problem(h);
+        size_t sz = layout_problem(h);
+        // shift this problem's regions to its base
+        h.lay.pos += o;
+        h.lay.mask += o;
+        h.lay.acc_obj += o;
+        h.lay.acc_probe += o;
+        h.lay.llk_part += o;
+        h.lay.maxbits += o;
+        h.lay.end += o;
+        o += sz;
+        size_t s = (size_t)h.B * h.p.K * h.p.N * h.p.N * sizeof(float2);
+        if (s > spec) spec = s;
+    }
+    *ctl_off = o;
+    o = align_up(o + sizeof(Ctl));
+    *spec_off = o;
+    o = align_up(o + spec);
+    *total = o;
+    return PTX_OK;
+}
+
+void fill_args(ptx_handle* h, ProbHost& ph) {
+    ProbArgs& a = ph.args;
+    const ptx_problem& p = ph.p;
+    a.N = p.N;
+    a.K = p.K;
+    a.J = p.J;
+    a.Ho = p.Ho;
+    a.Wo = p.Wo;
+    a.obj = (float2*)p.obj;
+    a.probe = (float2*)p.probe;
+    a.iobs = p.iobs;
+    a.psi = (float2*)p.psi;
+    a.pos = (const int2*)(h->scratch + ph.lay.pos);
+    a.mask = (const uint8_t*)(h->scratch + ph.lay.mask);
+    a.acc_obj = (float4*)(h->scratch + ph.lay.acc_obj);
+    a.acc_probe = (float4*)(h->scratch + ph.lay.acc_probe);
+    a.spec = (float2*)(h->scratch + h->spec_off);
+    a.llk_part = (double*)(h->scratch + ph.lay.llk_part);
+    a.maxbits = (unsigned*)(h->scratch + ph.lay.maxbits);
+    a.grad_obj = nullptr;
+    a.grad_probe = nullptr;
+    a.L1 = ph.L1;
+    a.C2 = ph.C2;
+    a.L3 = ph.L3;
+}
+
+enum Algo { ALGO_AP = 0, ALGO_DM = 1 };
+
+// Bracket one launch with profiling events when profiling is on.
+struct ProfScope {
+    ptx_handle* h;
+    int kind;
+    cudaStream_t s;
+    int idx = -1;
+    ProfScope(ptx_handle* h_, int kind_, cudaStream_t s_) : h(h_), kind(kind_), s(s_) {
+        if (!h->profiling) return;
+        idx = (int)h->ev_used.size() * 2;
+        while ((int)h->ev_pool.size() < idx + 2) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                idx = -1;
+                return;
+            }
+            h->ev_pool.push_back(e);
+        }
+        cudaEventRecord(h->ev_pool[idx], s);
+    }
+    ~ProfScope() {
+        if (idx < 0) return;
+        cudaEventRecord(h->ev_pool[idx + 1], s);
+        h->ev_used.push_back({kind, idx});
+    }
+};
+
+// One cycle of every problem, enqueued on `s`.
+ptx_status enqueue_cycle(ptx_handle* h, int algo, uint32_t flags, cudaStream_t s) {
+    const bool upd_o = flags & PTX_UPDATE_OBJ;
+    const bool upd_p = flags & PTX_UPDATE_PROBE;
+    const bool init = flags & PTX_DM_INIT_PSI;
+    const int np = (int)h->probs.size();
+    for (int pi = 0; pi < np; ++pi) {
+        ProbHost& ph = h->probs[pi];
+        const ProbArgs& a = ph.args;
+        const KernelSet* ks = ph.ks;
+        const int fwd_mode = (algo == ALGO_DM && !init) ? X_DM : X_PHI;
+        const int bwd_mode = (algo == ALGO_DM) ? BWD_DM : BWD_AP;
+        for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
+            const int nb = std::min(ph.B, ph.p.J - j0);
+            const int G = std::min(ph.G3, nb);
+            {
+                ProfScope ps(h, PTX_KERNEL_ROW_FWD, s);
+                ks->row_fwd(a, j0, nb, fwd_mode, s);
+            }
+            {
+                ProfScope ps(h, PTX_KERNEL_COL, s);
+                ks->col(a, j0, nb, COL_PROJECT, s);
+            }
+            {
+                ProfScope ps(h, PTX_KERNEL_ROW_BWD, s);
+                ks->row_bwd(a, j0, nb, G, bwd_mode, upd_o, upd_p, s);
+            }
+        }
+        if (!(flags & PTX_NO_NORMALISE) && (upd_o || upd_p)) {
+            {
+                ProfScope ps(h, PTX_KERNEL_DEN_MAX, s);
+                k_den_max<<<2 * 152, 256, 0, s>>>(a, upd_o, upd_p);
+            }
+            ProfScope ps(h, PTX_KERNEL_NORMALISE, s);
+            k_normalise<<<4 * 152, 256, 0, s>>>(a, (float)h->alpha_obj, (float)h->alpha_probe, upd_o, upd_p);
+        }
+        ProfScope ps(h, PTX_KERNEL_CYCLE_END, s);
+        k_cycle_end<<<1, 1024, 0, s>>>(h->ctl, a, pi, a.N / a.C2, pi == np - 1);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return PTX_OK;
+}
+
+ptx_status get_graph(ptx_handle* h, int algo, uint32_t flags, cudaGraphExec_t* out) {
+    GraphKey key{algo, flags};
+    auto it = h->graphs.find(key);
+    if (it != h->graphs.end()) {
+        *out = it->second;
+        return PTX_OK;
+    }
+    cudaError_t e;
+    if (!h->cap_stream) {
+        if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    ptx_status st = enqueue_cycle(h, algo, flags, h->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (st != PTX_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    h->graphs[key] = ex;
+    *out = ex;
+    return PTX_OK;
+}
+
+void drop_graphs(ptx_handle* h) {
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+}
+
+ptx_status check_device(ptx_handle* h) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != h->device)
+        return fail(PTX_ERR_INVALID_ARG, "handle was created on device %d but device %d is current", h->device, dev);
+    return PTX_OK;
+}
+
+ptx_status run_cycles(ptx_handle* h, int algo, int ncycles, uint32_t flags, double* llk_dev, void* stream) {
+    if (!h) return fail(PTX_ERR_INVALID_ARG, "null handle");
+    if (ncycles < 0) return fail(PTX_ERR_INVALID_ARG, "ncycles=%d must be >= 0", ncycles);
+    const uint32_t known = PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_DM_INIT_PSI | PTX_NO_NORMALISE | PTX_NO_GRAPH;
+    if (flags & ~known) return fail(PTX_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags & ~known);
+    if (algo == ALGO_AP && (flags & PTX_DM_INIT_PSI))
+        return fail(PTX_ERR_INVALID_ARG, "PTX_DM_INIT_PSI is a DM flag");
+    if (algo == ALGO_DM)
+        for (size_t i = 0; i < h->probs.size(); ++i)
+            if (!h->probs[i].p.psi)
+                return fail(PTX_ERR_INVALID_ARG, "problem %zu: DM needs the psi array", i);
+    ptx_status st = check_device(h);
+    if (st != PTX_OK) return st;
+    if (ncycles == 0) return PTX_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_set_ctl<<<1, 1, 0, s>>>(h->ctl, llk_dev, (int)h->probs.size());
+    const bool graph = !(flags & PTX_NO_GRAPH) && !h->profiling;
+    const uint32_t base = flags & (PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_NO_NORMALISE);
+    for (int c = 0; c < ncycles; ++c) {
+        uint32_t f = base;
+        if (c == 0 && (flags & PTX_DM_INIT_PSI)) f |= PTX_DM_INIT_PSI;
+        if (graph) {
+            cudaGraphExec_t ex;
+            if ((st = get_graph(h, algo, f, &ex)) != PTX_OK) return st;
+            cudaError_t e = cudaGraphLaunch(ex, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+        } else {
+            if ((st = enqueue_cycle(h, algo, f, s)) != PTX_OK) return st;
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "cycle launch");
+    return PTX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ptx_status ptx_workspace_bytes(const ptx_problem* probs, int32_t nprob, size_t* scratch_bytes) {
+    if (!probs || nprob < 1 || !scratch_bytes) return fail(PTX_ERR_INVALID_ARG, "null argument or nprob < 1");
+    std::vector<ProbHost> v(nprob);
+    for (int i = 0; i < nprob; ++i) {
+        ptx_status st = check_problem(probs[i], i);
+        if (st != PTX_OK) return st;
+        v[i].p = probs[i];
+    }
+    size_t so, co, tot;
+    compute_layout(v, &so, &co, &tot);
+    *scratch_bytes = tot;
+    return PTX_OK;
+}
+
+ptx_status ptx_create(ptx_handle** out, const ptx_problem* probs, int32_t nprob, void* scratch, size_t scratch_bytes,
+                      void* stream) {
+    if (!out) return fail(PTX_ERR_INVALID_ARG, "out is null");
+    *out = nullptr;
+    if (!probs || nprob < 1) return fail(PTX_ERR_INVALID_ARG, "no problems");
+    if (!scratch) return fail(PTX_ERR_INVALID_ARG, "scratch is null");
+    if ((uintptr_t)scratch % kAlign) return fail(PTX_ERR_INVALID_ARG, "scratch must be %zu-byte aligned", kAlign);
+    std::vector<ProbHost> v(nprob);
+    for (int i = 0; i < nprob; ++i) {
+        ptx_status st = check_problem(probs[i], i);
+        if (st != PTX_OK) return st;
+        v[i].p = probs[i];
+    }
+    size_t spec_off, ctl_off, total;
+    compute_layout(v, &spec_off, &ctl_off, &total);
+    if (scratch_bytes < total)
+        return fail(PTX_ERR_NOT_READY, "scratch of %zu bytes is smaller than the %zu needed", scratch_bytes, total);
+    cudaError_t e = ensure_attributes();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    ptx_handle* h = new ptx_handle();
+    h->probs = std::move(v);
+    h->scratch = (char*)scratch;
+    h->scratch_bytes = scratch_bytes;
+    h->spec_off = spec_off;
+    h->ctl_off = ctl_off;
+    h->ctl = (Ctl*)(h->scratch + ctl_off);
+    cudaGetDevice(&h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // zero everything the library owns, then copy positions and mask
+    e = cudaMemsetAsync(h->scratch, 0, spec_off, s);
+    for (size_t i = 0; e == cudaSuccess && i < h->probs.size(); ++i) {
+        ProbHost& ph = h->probs[i];
+        // positions: the (row, col) int32 pairs are already laid out as int2
+        std::vector<int32_t> pos(ph.p.positions, ph.p.positions + 2 * (size_t)ph.p.J);
+        e = cudaMemcpyAsync(h->scratch + ph.lay.pos, pos.data(), pos.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) break;
+        if (ph.p.mask) {
+            e = cudaMemcpyAsync(h->scratch + ph.lay.mask, ph.p.mask, (size_t)ph.p.N * ph.p.N, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) break;
+        }
+        ph.p.positions = nullptr;  // borrowed host arrays are not kept
+        ph.p.mask = nullptr;
+        fill_args(h, ph);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host staging vectors die here
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "ptx_create copy");
+    }
+    *out = h;
+    return PTX_OK;
+}
+
+ptx_status ptx_ap_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, double* llk_dev, void* stream) {
+    return run_cycles(h, ALGO_AP, ncycles, flags, llk_dev, stream);
+}
+
+ptx_status ptx_dm_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, double* llk_dev, void* stream) {
+    return run_cycles(h, ALGO_DM, ncycles, flags, llk_dev, stream);
+}
+
+ptx_status ptx_llk(ptx_handle* h, double* llk_dev, void* stream) {
+    if (!h || !llk_dev) return fail(PTX_ERR_INVALID_ARG, "null handle or llk_dev");
+    ptx_status st = check_device(h);
+    if (st != PTX_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (size_t pi = 0; pi < h->probs.size(); ++pi) {
+        ProbHost& ph = h->probs[pi];
+        for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
+            const int nb = std::min(ph.B, ph.p.J - j0);
+            ph.ks->row_fwd(ph.args, j0, nb, X_PHI, s);
+            ph.ks->col(ph.args, j0, nb, COL_LLK, s);
+        }
+        k_llk_reduce<<<1, 1024, 0, s>>>(ph.args, ph.p.N / ph.C2, llk_dev + pi);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ptx_llk launch");
+    return PTX_OK;
+}
+
+ptx_status ptx_ml_grad(ptx_handle* h, void* grad_obj, void* grad_probe, double* llk_dev, void* stream) {
+    if (!h) return fail(PTX_ERR_INVALID_ARG, "null handle");
+    if (h->probs.size() != 1) return fail(PTX_ERR_INVALID_ARG, "ptx_ml_grad needs a single-problem handle");
+    ptx_status st = check_device(h);
+    if (st != PTX_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    ProbHost& ph = h->probs[0];
+    ProbArgs a = ph.args;
+    a.grad_obj = (float2*)grad_obj;
+    a.grad_probe = (float2*)grad_probe;
+    cudaError_t e = cudaSuccess;
+    if (grad_obj) e = cudaMemsetAsync(grad_obj, 0, sizeof(float2) * (size_t)a.Ho * a.Wo, s);
+    if (e == cudaSuccess && grad_probe) e = cudaMemsetAsync(grad_probe, 0, sizeof(float2) * (size_t)a.K * a.N * a.N, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ptx_ml_grad memset");
+    for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
+        const int nb = std::min(ph.B, ph.p.J - j0);
+        ph.ks->row_fwd(a, j0, nb, X_PHI, s);
+        ph.ks->col(a, j0, nb, COL_GRAD, s);
+        if (grad_obj || grad_probe)
+            ph.ks->row_bwd(a, j0, nb, std::min(ph.G3, nb), BWD_GRAD, grad_obj != nullptr, grad_probe != nullptr, s);
+    }
+    if (llk_dev) k_llk_reduce<<<1, 1024, 0, s>>>(a, a.N / a.C2, llk_dev);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ptx_ml_grad launch");
+    return PTX_OK;
+}
+
+ptx_status ptx_normalise(ptx_handle* h, uint32_t flags, void* stream) {
+    if (!h) return fail(PTX_ERR_INVALID_ARG, "null handle");
+    if (flags & ~(PTX_UPDATE_OBJ | PTX_UPDATE_PROBE)) return fail(PTX_ERR_INVALID_ARG, "flags: only update bits");
+    ptx_status st = check_device(h);
+    if (st != PTX_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int uo = (flags & PTX_UPDATE_OBJ) != 0, up = (flags & PTX_UPDATE_PROBE) != 0;
+    for (auto& ph : h->probs) {
+        k_den_max<<<2 * 152, 256, 0, s>>>(ph.args, uo, up);
+        k_normalise<<<4 * 152, 256, 0, s>>>(ph.args, (float)h->alpha_obj, (float)h->alpha_probe, uo, up);
+        cudaError_t e = cudaMemsetAsync(ph.args.maxbits, 0, 2 * sizeof(unsigned), s);
+        if (e != cudaSuccess) return cuda_fail(e, "ptx_normalise memset");
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ptx_normalise launch");
+    return PTX_OK;
+}
+
+ptx_status ptx_accumulators(ptx_handle* h, int32_t p, void** obj_acc, size_t* obj_acc_bytes, void** probe_acc,
+                            size_t* probe_acc_bytes) {
+    if (!h || p < 0 || p >= (int)h->probs.size()) return fail(PTX_ERR_INVALID_ARG, "bad handle or problem index");
+    const ProbHost& ph = h->probs[p];
+    if (obj_acc) *obj_acc = ph.args.acc_obj;
+    if (obj_acc_bytes) *obj_acc_bytes = sizeof(float4) * (size_t)ph.p.Ho * ph.p.Wo;
+    if (probe_acc) *probe_acc = ph.args.acc_probe;
+    if (probe_acc_bytes) *probe_acc_bytes = sizeof(float4) * (size_t)ph.p.K * ph.p.N * ph.p.N;
+    return PTX_OK;
+}
+
+ptx_status ptx_set_param(ptx_handle* h, const char* name, double value) {
+    if (!h || !name) return fail(PTX_ERR_INVALID_ARG, "null handle or name");
+    if (!(value >= 0.0) || !std::isfinite(value)) return fail(PTX_ERR_INVALID_ARG, "%s must be finite and >= 0", name);
+    if (!strcmp(name, "alpha_obj")) {
+        h->alpha_obj = value;
+    } else if (!strcmp(name, "alpha_probe")) {
+        h->alpha_probe = value;
+    } else {
+        return fail(PTX_ERR_INVALID_ARG, "unknown parameter '%s'", name);
+    }
+    drop_graphs(h);  // the captured graphs hold the old value
+    return PTX_OK;
+}
+
+ptx_status ptx_fft2(void* data, int32_t nframes, int32_t N, int32_t direction, void* stream) {
+    if (!data || nframes < 0) return fail(PTX_ERR_INVALID_ARG, "null data or negative nframes");
+    if (direction != -1 && direction != 1) return fail(PTX_ERR_INVALID_ARG, "direction must be -1 or +1");
+    if (!supported_N(N)) return fail(PTX_ERR_UNSUPPORTED, "frame size N=%d is not supported", N);
+    if (nframes == 0) return PTX_OK;
+    if (nframes > 65535) return fail(PTX_ERR_INVALID_ARG, "nframes=%d exceeds 65535 per call", nframes);
+    cudaError_t e = ensure_attributes();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    kernel_set(N)->fft2((float2*)data, nframes, direction, (cudaStream_t)stream);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ptx_fft2 launch");
+    return PTX_OK;
+}
+
+ptx_status ptx_profile_enable(ptx_handle* h, int32_t enable) {
+    if (!h) return fail(PTX_ERR_INVALID_ARG, "null handle");
+    h->profiling = enable != 0;
+    h->ev_used.clear();
+    return PTX_OK;
+}
+
+ptx_status ptx_profile_read(ptx_handle* h, int32_t nkinds, int64_t* launches, double* total_ms) {
+    if (!h || nkinds < 0 || (nkinds > 0 && (!launches || !total_ms)))
+        return fail(PTX_ERR_INVALID_ARG, "null handle or output arrays");
+    for (int k = 0; k < nkinds; ++k) {
+        launches[k] = 0;
+        total_ms[k] = 0.0;
+    }
+    for (const auto& u : h->ev_used) {
+        cudaError_t e = cudaEventSynchronize(h->ev_pool[u.second + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, h->ev_pool[u.second], h->ev_pool[u.second + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        if (u.first < nkinds) {
+            launches[u.first] += 1;
+            total_ms[u.first] += ms;
+        }
+    }
+    return PTX_OK;
+}
+
+const char* ptx_last_error(void) { return g_last_error.c_str(); }
+
+void ptx_destroy(ptx_handle* h) {
+    if (!h) return;
+    drop_graphs(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Normalisation, denominator maxima and FP64 log-likelihood reductions
+// (second half of Psi2ObjProbe and the LLK operator's final sum).
+#include "kernels.cuh"
+
+namespace ptx {
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// max D_O and max D_P over the accumulators (both >= 0, so their bit patterns
+// order like unsigned integers).
+__global__ void k_den_max(ProbArgs a, int upd_obj, int upd_probe) {
+    float mo = 0.f, mp = 0.f;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (upd_obj) {
+        const size_t n = (size_t)a.Ho * a.Wo;
+        for (size_t i = i0; i < n; i += stride) mo = fmaxf(mo, a.acc_obj[i].z);
+    }
+    if (upd_probe) {
+        const size_t n = (size_t)a.N * a.N;
+        for (size_t i = i0; i < n; i += stride) mp = fmaxf(mp, a.acc_probe[i].z);
+    }
+    mo = warp_max(mo);
+    mp = warp_max(mp);
+    if ((threadIdx.x & 31) == 0) {
+        if (mo > 0.f) atomicMax(&a.maxbits[0], __float_as_uint(mo));
+        if (mp > 0.f) atomicMax(&a.maxbits[1], __float_as_uint(mp));
+    }
+}
+
+// O <- (N_O + d_O O) / (D_O + d_O), d_O = alpha_obj max D_O (unchanged where the
+// denominator is 0); the same for each probe mode with D_P; accumulators cleared.
+__global__ void k_normalise(ProbArgs a, float alpha_obj, float alpha_probe, int upd_obj, int upd_probe) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (upd_obj) {
+        const float d = alpha_obj * __uint_as_float(a.maxbits[0]);
+        const size_t n = (size_t)a.Ho * a.Wo;
+        for (size_t i = i0; i < n; i += stride) {
+            const float4 v = a.acc_obj[i];
+            const float den = v.z + d;
+            if (den > 0.f) {
+                const float2 o = a.obj[i];
+                a.obj[i] = make_float2((v.x + d * o.x) / den, (v.y + d * o.y) / den);
+            }
+            a.acc_obj[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    if (upd_probe) {
+        const float d = alpha_probe * __uint_as_float(a.maxbits[1]);
+        const size_t n = (size_t)a.K * a.N * a.N;
+        for (size_t i = i0; i < n; i += stride) {
+            const float4 v = a.acc_probe[i];
+            const float den = v.z + d;
+            if (den > 0.f) {
+                const float2 o = a.probe[i];
+                a.probe[i] = make_float2((v.x + d * o.x) / den, (v.y + d * o.y) / den);
+            }
+            a.acc_probe[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
+__device__ double block_reduce_llk(const double* part, size_t n) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < 32) {
+        r = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    return r;
+}
+
+__global__ void k_llk_reduce(ProbArgs a, int nparts_per_frame, double* out) {
+    double r = block_reduce_llk(a.llk_part, (size_t)a.J * nparts_per_frame);
+    if (threadIdx.x == 0) *out = r;
+}
+
+__global__ void k_cycle_end(Ctl* ctl, ProbArgs a, int p, int nparts_per_frame, int last_problem) {
+    double r = block_reduce_llk(a.llk_part, (size_t)a.J * nparts_per_frame);
+    if (threadIdx.x == 0) {
+        if (ctl->llk_out) ctl->llk_out[(size_t)ctl->cycle * ctl->nprob + p] = r;
+        a.maxbits[0] = 0u;
+        a.maxbits[1] = 0u;
+        if (last_problem) ctl->cycle += 1;
+    }
+}
+
+__global__ void k_set_ctl(Ctl* ctl, double* llk_out, int nprob) {
+    ctl->llk_out = llk_out;
+    ctl->cycle = 0;
+    ctl->nprob = nprob;
+    ctl->err = 0;
+}
+
+}  // namespace ptx

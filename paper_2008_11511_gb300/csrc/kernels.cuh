@@ -1,0 +1,465 @@
+// Kernels of the far-field ptychography cycle.  One cycle over a batch of
+// frames is three passes through a Fourier-space work stack `spec` that is
+// sized to stay resident in L2:
+//
+//   row_fwd   : Phi = P_k . O[r_j] (ObjProbe2Psi), X = Phi (AP) or 2 Phi - Psi (DM),
+//               forward FFT of each row                        -> spec
+//   col       : forward FFT of each column, then per pixel the amplitude
+//               projection (ApplyAmplitude, common factor over modes) and the
+//               Poisson LLK, then the inverse column FFT of the correction
+//               D^ = P_M(X^) - X^                               -> spec
+//   row_bwd   : inverse row FFT -> D = IFT(P_M(FT X)) - X; the new exit wave
+//               is Psi' = Phi + D (equal to Psi + P_F(X) - Phi for DM and to
+//               P_F(Phi) for AP), scattered into the Psi2ObjProbe numerators
+//               and denominators.
+//
+// After all batches: max of the denominators, normalisation with inertia,
+// and the FP64 reduction of the per-block LLK partial sums.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft.cuh"
+
+namespace ptx {
+
+constexpr int kThreads = 256;
+
+enum RowFwdMode : int { X_PHI = 0, X_DM = 1 };
+enum ColMode : int { COL_PROJECT = 0, COL_LLK = 1, COL_GRAD = 2 };
+enum RowBwdMode : int { BWD_AP = 0, BWD_DM = 1, BWD_GRAD = 2 };
+
+// Device view of one problem (all pointers device, fixed for a handle).
+struct ProbArgs {
+    int N, K, J, Ho, Wo;
+    float2* obj;            // [Ho][Wo]
+    float2* probe;          // [K][N][N]
+    const float* iobs;      // [J][N][N]
+    float2* psi;            // [J][K][N][N] or null
+    const int2* pos;        // [J] {row, col}
+    const uint8_t* mask;    // [N][N]
+    float4* acc_obj;        // [Ho][Wo] {Re N_O, Im N_O, D_O, 0}
+    float4* acc_probe;      // [K][N][N] {Re N_P, Im N_P, D_P, 0}
+    float2* spec;           // [B][K][N][N] batch work stack
+    double* llk_part;       // [J][ncolblk] per-block LLK partial sums
+    unsigned* maxbits;      // [2] max D_O, max D_P (float bits; values >= 0)
+    float2* grad_obj;       // [Ho][Wo] (ML gradient) or null
+    float2* grad_probe;     // [K][N][N] or null
+    int L1, C2, L3;         // rows per row_fwd block, columns per col block, rows per row_bwd block
+};
+
+struct Ctl {
+    double* llk_out;  // destination of per-cycle LLK values
+    int cycle;        // cycle index within the current call
+    int nprob;
+    int err;
+    int pad;
+};
+
+__device__ __forceinline__ void red_add_v4(float4* addr, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+__device__ __forceinline__ void red_add_v2(float2* addr, float a, float b) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
+}
+
+// Poisson LLK of one pixel (deviance form): I_c - I_o + I_o ln(I_o / I_c), = I_c for I_o <= 0,
+// I_c floored at 1e-30.  With u = I_c / I_o - 1 the term is I_o (u - ln(1 + u)); for
+// -1/2 < u < 1 it is evaluated without cancellation from ln(1+u) = 2 atanh(t),
+// t = u / (2 + u):  u - ln(1 + u) = u t - 2 t^3 (1/3 + t^2/5 + t^4/7 + ...), |t| <= 1/3.
+__device__ __forceinline__ float llk_term(float ic, float io) {
+    if (!(io > 0.f)) return ic;
+    float icf = fmaxf(ic, 1e-30f);
+    float u = (icf - io) / io;
+    float f;
+    if (u > -0.5f && u < 1.0f) {
+        float t = u / (2.0f + u);
+        float t2 = t * t;
+        float poly = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, 1.f / 15.f, 1.f / 13.f), 1.f / 11.f),
+                                                     1.f / 9.f), 1.f / 7.f), 1.f / 5.f), 1.f / 3.f);
+        f = fmaf(u, t, -2.0f * t * t2 * poly);
+    } else {
+        f = u - logf(icf / io);
+    }
+    return io * f;
+}
+
+// Kahan-compensated float accumulation (per thread), reduced in FP64 across the block.
+struct KahanF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        float y = v - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+template <int T>
+__device__ __forceinline__ double block_sum_double(double v, double* red_smem) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red_smem[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < 32) {
+        r = (threadIdx.x < T / 32) ? red_smem[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    return r;  // valid in thread 0
+}
+
+// Inter-pass twiddles of the line FFT, tw_s[k2 * M + n1] = exp(-2 pi i n1 k2 / N),
+// computed per block with sincospif on the exactly reduced integer n1 k2 mod N.
+template <int N>
+__device__ __forceinline__ void load_twiddles(float2* tw_s) {
+    constexpr int M = Plan<N>::M;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int k2 = i / M, n1 = i - k2 * M;
+        const int m = (n1 * k2) % N;
+        float s, c;
+        sincospif(-2.0f * (float)m / (float)N, &s, &c);
+        tw_s[i] = make_float2(c, s);
+    }
+}
+
+// Max lines (of N elements) held by one block.
+template <int N>
+__host__ __device__ constexpr int max_lines() {
+    return (4096 / N) < 1 ? 1 : ((4096 / N) > 256 ? 256 : (4096 / N));
+}
+
+// ---------------------------------------------------------------------------
+// row_fwd: grid (N / L1, frames in batch); block handles rows [y0, y0 + L1) of
+// all K modes of frame j0 + blockIdx.y.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_row_fwd(ProbArgs a, int j0, int mode) {
+    constexpr int P = line_pitch<N>();
+    extern __shared__ __align__(16) float2 sm[];
+    float2* tw = sm;
+    float2* buf = sm + N;
+    const int K = a.K, L = a.L1;
+    const int y0 = blockIdx.x * L;
+    const int b = blockIdx.y;
+    const int j = j0 + b;
+    load_twiddles<N>(tw);
+    const int2 p = a.pos[j];
+    const int nel = K * L * N;
+    for (int e = threadIdx.x; e < nel; e += kThreads) {
+        const int x = e % N;
+        const int line = e / N;
+        const int k = line / L, r = line - k * L;
+        const int y = y0 + r;
+        float2 pr = a.probe[((size_t)k * N + y) * N + x];
+        float2 ob = a.obj[(size_t)(p.x + y) * a.Wo + (p.y + x)];
+        float2 X = cmul(pr, ob);
+        if (mode == X_DM) {
+            float2 ps = a.psi[(((size_t)j * K + k) * N + y) * N + x];
+            X = make_float2(2.f * X.x - ps.x, 2.f * X.y - ps.y);
+        }
+        buf[line * P + x] = X;
+    }
+    __syncthreads();
+    fft_lines<N, -1, kThreads, max_lines<N>()>(buf, K * L, tw);
+    for (int e = threadIdx.x; e < nel; e += kThreads) {
+        const int x = e % N;
+        const int line = e / N;
+        const int k = line / L, r = line - k * L;
+        a.spec[(((size_t)b * K + k) * N + y0 + r) * N + x] = buf[line * P + x];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// col: grid (N / C2, frames in batch); block handles columns [x0, x0 + C2) of
+// all K modes of one frame.  Lines in shared memory are columns.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_col(ProbArgs a, int j0, int mode) {
+    constexpr int P = line_pitch<N>();
+    extern __shared__ __align__(16) float2 sm[];
+    __shared__ double red_s[kThreads / 32];
+    float2* tw = sm;
+    float2* buf = sm + N;
+    const int K = a.K, C = a.C2;
+    const int x0 = blockIdx.x * C;
+    const int b = blockIdx.y;
+    const int j = j0 + b;
+    load_twiddles<N>(tw);
+    const int nel = K * N * C;
+    for (int e = threadIdx.x; e < nel; e += kThreads) {
+        const int c = e % C;
+        const int t = e / C;
+        const int n = t % N, k = t / N;
+        buf[(k * C + c) * P + n] = a.spec[(((size_t)b * K + k) * N + n) * N + x0 + c];
+    }
+    __syncthreads();
+    fft_lines<N, -1, kThreads, max_lines<N>()>(buf, K * C, tw);
+    constexpr float invN2 = 1.0f / float(N * N);
+    KahanF llk;
+    const float* io_row = a.iobs + (size_t)j * N * N;
+    for (int e = threadIdx.x; e < N * C; e += kThreads) {
+        const int c = e % C, n = e / C;
+        float icr = 0.f;
+        for (int k = 0; k < K; ++k) icr += cnorm(buf[(k * C + c) * P + n]);
+        const float ic = icr * invN2;
+        const float io = io_row[n * N + x0 + c];
+        const bool masked = a.mask[n * N + x0 + c] != 0;
+        if (!masked) llk.add(llk_term(ic, io));
+        if (mode != COL_LLK) {
+            float f;
+            if (masked) {
+                f = 0.f;
+            } else if (mode == COL_PROJECT) {
+                f = (sqrtf(fmaxf(io, 0.f)) / fmaxf(sqrtf(ic), 1e-20f) - 1.0f) * invN2;
+            } else {
+                f = 2.0f * (1.0f - fmaxf(io, 0.f) / fmaxf(ic, 1e-30f)) * invN2;
+            }
+            for (int k = 0; k < K; ++k) {
+                float2& v = buf[(k * C + c) * P + n];
+                v = cscale(v, f);
+            }
+        }
+    }
+    double tot = block_sum_double<kThreads>(llk.value(), red_s);
+    if (threadIdx.x == 0) a.llk_part[(size_t)j * gridDim.x + blockIdx.x] = tot;
+    if (mode == COL_LLK) return;
+    __syncthreads();
+    fft_lines<N, +1, kThreads, max_lines<N>()>(buf, K * C, tw);
+    for (int e = threadIdx.x; e < nel; e += kThreads) {
+        const int c = e % C;
+        const int t = e / C;
+        const int n = t % N, k = t / N;
+        a.spec[(((size_t)b * K + k) * N + n) * N + x0 + c] = buf[(k * C + c) * P + n];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// row_bwd: grid (N / L3, G); block handles rows [y0, y0 + L3) of frames
+// b = blockIdx.y, blockIdx.y + G, ... of the batch, keeping its share of the
+// probe numerator / denominator in shared memory across those frames.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_row_bwd(ProbArgs a, int j0, int nb, int mode, int upd_obj,
+                                                      int upd_probe) {
+    constexpr int P = line_pitch<N>();
+    extern __shared__ __align__(16) float2 sm[];
+    const int K = a.K, L = a.L3;
+    float2* tw = sm;
+    float2* buf = sm + N;
+    float2* np_s = buf + K * L * P;        // [K][L][N]
+    float* dp_s = (float*)(np_s + K * L * N);  // [L][N]
+    const int y0 = blockIdx.x * L;
+    load_twiddles<N>(tw);
+    const bool acc_p = upd_probe != 0;
+    const bool acc_o = upd_obj != 0;
+    if (acc_p) {
+        for (int e = threadIdx.x; e < K * L * N; e += kThreads) np_s[e] = make_float2(0.f, 0.f);
+        for (int e = threadIdx.x; e < L * N; e += kThreads) dp_s[e] = 0.f;
+    }
+    const int nel = K * L * N;
+    for (int b = blockIdx.y; b < nb; b += gridDim.y) {
+        const int j = j0 + b;
+        const int2 p = a.pos[j];
+        for (int e = threadIdx.x; e < nel; e += kThreads) {
+            const int x = e % N;
+            const int line = e / N;
+            const int k = line / L, r = line - k * L;
+            buf[line * P + x] = a.spec[(((size_t)b * K + k) * N + y0 + r) * N + x];
+        }
+        __syncthreads();
+        fft_lines<N, +1, kThreads, max_lines<N>()>(buf, K * L, tw);
+        for (int e = threadIdx.x; e < L * N; e += kThreads) {
+            const int x = e % N, r = e / N;
+            const int y = y0 + r;
+            const size_t oidx = (size_t)(p.x + y) * a.Wo + (p.y + x);
+            const float2 ob = a.obj[oidx];
+            float2 no = make_float2(0.f, 0.f);
+            float dn = 0.f;
+            for (int k = 0; k < K; ++k) {
+                const float2 d = buf[(k * L + r) * P + x];
+                const float2 pr = a.probe[((size_t)k * N + y) * N + x];
+                float2 w;
+                if (mode == BWD_GRAD) {
+                    w = d;
+                } else {
+                    w = cadd(cmul(pr, ob), d);
+                    if (mode == BWD_DM) a.psi[(((size_t)j * K + k) * N + y) * N + x] = w;
+                }
+                if (acc_o) {
+                    const float2 t = cconjmul(pr, w);
+                    no.x += t.x;
+                    no.y += t.y;
+                    dn = fmaf(pr.x, pr.x, fmaf(pr.y, pr.y, dn));
+                }
+                if (acc_p) {
+                    const float2 t = cconjmul(ob, w);
+                    float2& q = np_s[(k * L + r) * N + x];
+                    q.x += t.x;
+                    q.y += t.y;
+                }
+            }
+            if (acc_p) dp_s[r * N + x] += cnorm(ob);
+            if (acc_o) {
+                if (mode == BWD_GRAD)
+                    red_add_v2(a.grad_obj + oidx, no.x, no.y);
+                else
+                    red_add_v4(a.acc_obj + oidx, no.x, no.y, dn, 0.f);
+            }
+        }
+        __syncthreads();
+    }
+    if (acc_p) {
+        for (int e = threadIdx.x; e < K * L * N; e += kThreads) {
+            const int x = e % N;
+            const int line = e / N;
+            const int k = line / L, r = line - k * L;
+            const size_t pidx = ((size_t)k * N + y0 + r) * N + x;
+            const float2 q = np_s[e];
+            if (mode == BWD_GRAD)
+                red_add_v2(a.grad_probe + pidx, q.x, q.y);
+            else
+                red_add_v4(a.acc_probe + pidx, q.x, q.y, dp_s[r * N + x], 0.f);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Normalisation (Psi2ObjProbe second half) and reductions.
+// ---------------------------------------------------------------------------
+__global__ void k_den_max(ProbArgs a, int upd_obj, int upd_probe);
+__global__ void k_normalise(ProbArgs a, float alpha_obj, float alpha_probe, int upd_obj, int upd_probe);
+__global__ void k_llk_reduce(ProbArgs a, int nparts_per_frame, double* out);
+__global__ void k_cycle_end(Ctl* ctl, ProbArgs a, int p, int nparts_per_frame, int last_problem);
+__global__ void k_set_ctl(Ctl* ctl, double* llk_out, int nprob);
+
+// ---------------------------------------------------------------------------
+// Plain orthonormal 2D FFT of frames in place (FT / IFT operators).
+// ---------------------------------------------------------------------------
+template <int N, int DIR>
+__global__ void __launch_bounds__(kThreads) k_fft_rows(float2* data, int L) {
+    constexpr int P = line_pitch<N>();
+    extern __shared__ __align__(16) float2 sm[];
+    float2* tw = sm;
+    float2* buf = sm + N;
+    load_twiddles<N>(tw);
+    float2* base = data + ((size_t)blockIdx.y * N + blockIdx.x * L) * N;
+    for (int e = threadIdx.x; e < L * N; e += kThreads) buf[(e / N) * P + (e % N)] = base[e];
+    __syncthreads();
+    fft_lines<N, DIR, kThreads, max_lines<N>()>(buf, L, tw);
+    for (int e = threadIdx.x; e < L * N; e += kThreads) base[e] = buf[(e / N) * P + (e % N)];
+}
+
+template <int N, int DIR>
+__global__ void __launch_bounds__(kThreads) k_fft_cols(float2* data, int C) {
+    constexpr int P = line_pitch<N>();
+    extern __shared__ __align__(16) float2 sm[];
+    float2* tw = sm;
+    float2* buf = sm + N;
+    load_twiddles<N>(tw);
+    float2* base = data + (size_t)blockIdx.y * N * N + blockIdx.x * C;
+    for (int e = threadIdx.x; e < N * C; e += kThreads) {
+        const int c = e % C, n = e / C;
+        buf[c * P + n] = base[(size_t)n * N + c];
+    }
+    __syncthreads();
+    fft_lines<N, DIR, kThreads, max_lines<N>()>(buf, C, tw);
+    constexpr float invN = 1.0f / float(N);
+    for (int e = threadIdx.x; e < N * C; e += kThreads) {
+        const int c = e % C, n = e / C;
+        base[(size_t)n * N + c] = cscale(buf[c * P + n], invN);
+    }
+}
+
+// Launch table for one frame size.
+struct KernelSet {
+    int N;
+    void (*row_fwd)(const ProbArgs&, int j0, int nb, int mode, cudaStream_t);
+    void (*col)(const ProbArgs&, int j0, int nb, int mode, cudaStream_t);
+    void (*row_bwd)(const ProbArgs&, int j0, int nb, int G, int mode, int upd_obj, int upd_probe, cudaStream_t);
+    void (*fft2)(float2* data, int nframes, int dir, cudaStream_t);
+    size_t (*smem_row_fwd)(int K, int L);
+    size_t (*smem_col)(int K, int C);
+    size_t (*smem_row_bwd)(int K, int L);
+    int max_lines;
+    int R, M;
+};
+
+const KernelSet* kernel_set(int N);
+cudaError_t set_kernel_attributes();
+
+template <int N>
+size_t smem_row_fwd_t(int K, int L) { return sizeof(float2) * (N + (size_t)K * L * line_pitch<N>()); }
+template <int N>
+size_t smem_col_t(int K, int C) { return sizeof(float2) * (N + (size_t)K * C * line_pitch<N>()); }
+template <int N>
+size_t smem_row_bwd_t(int K, int L) {
+    return sizeof(float2) * (N + (size_t)K * L * line_pitch<N>() + (size_t)K * L * N) + sizeof(float) * (size_t)L * N;
+}
+
+template <int N>
+void launch_row_fwd(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s) {
+    dim3 grid(N / a.L1, nb);
+    k_row_fwd<N><<<grid, kThreads, smem_row_fwd_t<N>(a.K, a.L1), s>>>(a, j0, mode);
+}
+template <int N>
+void launch_col(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s) {
+    dim3 grid(N / a.C2, nb);
+    k_col<N><<<grid, kThreads, smem_col_t<N>(a.K, a.C2), s>>>(a, j0, mode);
+}
+template <int N>
+void launch_row_bwd(const ProbArgs& a, int j0, int nb, int G, int mode, int upd_obj, int upd_probe, cudaStream_t s) {
+    dim3 grid(N / a.L3, G);
+    k_row_bwd<N><<<grid, kThreads, smem_row_bwd_t<N>(a.K, a.L3), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
+}
+template <int N>
+void launch_fft2(float2* data, int nframes, int dir, cudaStream_t s) {
+    constexpr int ml = max_lines<N>();
+    int L = 1;
+    while (L * 2 <= ml && N % (L * 2) == 0) L *= 2;
+    size_t sm = sizeof(float2) * (N + (size_t)L * line_pitch<N>());
+    dim3 grid(N / L, nframes);
+    if (dir < 0) {
+        k_fft_rows<N, -1><<<grid, kThreads, sm, s>>>(data, L);
+        k_fft_cols<N, -1><<<grid, kThreads, sm, s>>>(data, L);
+    } else {
+        k_fft_rows<N, +1><<<grid, kThreads, sm, s>>>(data, L);
+        k_fft_cols<N, +1><<<grid, kThreads, sm, s>>>(data, L);
+    }
+}
+
+template <int N>
+cudaError_t set_attrs_t() {
+    cudaError_t e;
+    const int mx = 200 * 1024;
+    if ((e = cudaFuncSetAttribute(k_row_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_col<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_bwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_fft_rows<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_fft_rows<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_fft_cols<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_fft_cols<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    return cudaSuccess;
+}
+
+template <int N>
+const KernelSet* make_kernel_set() {
+    static const KernelSet ks = {N,
+                                 &launch_row_fwd<N>,
+                                 &launch_col<N>,
+                                 &launch_row_bwd<N>,
+                                 &launch_fft2<N>,
+                                 &smem_row_fwd_t<N>,
+                                 &smem_col_t<N>,
+                                 &smem_row_bwd_t<N>,
+                                 max_lines<N>(),
+                                 Plan<N>::R,
+                                 Plan<N>::M};
+    return &ks;
+}
+
+}  // namespace ptx

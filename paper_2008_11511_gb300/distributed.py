@@ -1,0 +1,59 @@
+"""Data-parallel split of one ptychography problem over several GPUs.
+
+Frames are independent within a cycle, so the positions can be sharded across
+ranks; the only exchange per cycle is the sum of the Psi2ObjProbe numerators
+and denominators (object: Ho x Wo x {Re N_O, Im N_O, D_O, 0}; probe:
+K x N x N x {Re N_P, Im N_P, D_P, 0}) and of the log-likelihood.  Every rank
+then normalises the same sums, so O and P stay identical on all ranks.
+
+The paper's own multi-GPU mode (PtychoSplit, Section 4) instead runs the parts
+asynchronously and stitches them at the end; this module provides the
+synchronous form, whose result equals the single-GPU cycle.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+import torch.distributed as dist
+
+
+def split_positions(positions, world: int, rank: int) -> np.ndarray:
+    """Indices of the frames owned by ``rank``: positions sorted by (row, col) and
+    cut into ``world`` contiguous, nearly equal spatial blocks."""
+    pos = np.asarray(positions)
+    order = np.lexsort((pos[:, 1], pos[:, 0]))
+    return np.sort(np.array_split(order, world)[rank])
+
+
+def allreduce_accumulators(acc_obj: torch.Tensor, acc_probe: torch.Tensor, llk: torch.Tensor | None = None,
+                           group=None):
+    """Sum the packed accumulators (and the LLK) over all ranks in place."""
+    dist.all_reduce(acc_obj, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(acc_probe, op=dist.ReduceOp.SUM, group=group)
+    if llk is not None:
+        dist.all_reduce(llk, op=dist.ReduceOp.SUM, group=group)
+
+
+def dm_cycles_data_parallel(pb, ncycles: int, update_obj=True, update_probe=True, init_psi=False, group=None):
+    """DM cycles of a Ptycho that holds this rank's frames only: accumulate
+    without normalising, all-reduce the accumulators, normalise.  Returns the
+    global per-cycle LLK (device float64)."""
+    out = torch.empty(max(ncycles, 1), dtype=torch.float64, device=pb.device)
+    acc_o, acc_p = pb.accumulators()
+    for c in range(ncycles):
+        llk = pb.dm(1, update_obj=update_obj, update_probe=update_probe, init_psi=(init_psi and c == 0),
+                    normalise=False, llk=out[c:c + 1])
+        allreduce_accumulators(acc_o, acc_p, llk, group=group)
+        pb.normalise(update_obj=update_obj, update_probe=update_probe)
+    return out[:ncycles]
+
+
+def ap_cycles_data_parallel(pb, ncycles: int, update_obj=True, update_probe=True, group=None):
+    """AP cycles with the same split as ``dm_cycles_data_parallel``."""
+    out = torch.empty(max(ncycles, 1), dtype=torch.float64, device=pb.device)
+    acc_o, acc_p = pb.accumulators()
+    for c in range(ncycles):
+        llk = pb.ap(1, update_obj=update_obj, update_probe=update_probe, normalise=False, llk=out[c:c + 1])
+        allreduce_accumulators(acc_o, acc_p, llk, group=group)
+        pb.normalise(update_obj=update_obj, update_probe=update_probe)
+    return out[:ncycles]

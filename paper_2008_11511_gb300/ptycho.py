@@ -1,0 +1,226 @@
+"""PyTorch-facing API of libptycho.
+
+PyTorch provides the device memory (object, probe, intensities, exit-wave
+stack, scratch) and the stream; every step of the ptychography cycle runs in
+libptycho's CUDA kernels.  Names follow the paper's operators (Section 4 and
+the appendix operator table): AP, DM, LLK, ML, FT / IFT.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (PTX_DM_INIT_PSI, PTX_NO_GRAPH, PTX_NO_NORMALISE, PTX_UPDATE_OBJ, PTX_UPDATE_PROBE,
+                   SUPPORTED_SIZES, Problem, PtychoError)
+
+
+def _stream_ptr(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _require_cuda(t: torch.Tensor, name: str, dtype):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Ptycho:
+    """One far-field ptychography problem resident on the GPU (the paper's
+    ``Ptycho`` object: data, object, probe modes and the exit-wave stack).
+
+    obj:       complex64 (Ho, Wo) CUDA tensor, updated in place by the cycles
+    probe:     complex64 (K, N, N) CUDA tensor, updated in place
+    iobs:      float32 (J, N, N) CUDA tensor, FFT order (zero frequency at [0, 0])
+    positions: int (J, 2) array of (row, col) top-left patch corners
+    mask:      optional uint8/bool (N, N) array, nonzero = bad pixel
+    psi:       complex64 (J, K, N, N) CUDA tensor for DM; allocated when
+               ``with_psi`` is set and none is given
+    """
+
+    def __init__(self, obj: torch.Tensor, probe: torch.Tensor, iobs: torch.Tensor, positions, mask=None,
+                 psi: torch.Tensor | None = None, with_psi: bool = False):
+        _require_cuda(obj, "obj", torch.complex64)
+        _require_cuda(probe, "probe", torch.complex64)
+        _require_cuda(iobs, "iobs", torch.float32)
+        if probe.dim() != 3 or obj.dim() != 2 or iobs.dim() != 3:
+            raise ValueError("shapes: obj (Ho, Wo), probe (K, N, N), iobs (J, N, N)")
+        K, N, N2 = probe.shape
+        J = iobs.shape[0]
+        if N2 != N or tuple(iobs.shape[1:]) != (N, N):
+            raise ValueError("probe and iobs frames must be N x N")
+        self.device = obj.device
+        pos = np.ascontiguousarray(np.asarray(positions, dtype=np.int32).reshape(J, 2))
+        if psi is None and with_psi:
+            psi = torch.empty((J, K, N, N), dtype=torch.complex64, device=self.device)
+        if psi is not None:
+            _require_cuda(psi, "psi", torch.complex64)
+            if tuple(psi.shape) != (J, K, N, N):
+                raise ValueError("psi must be (J, K, N, N)")
+        m = None
+        if mask is not None:
+            m = np.ascontiguousarray(np.asarray(mask).astype(np.uint8).reshape(N, N))
+        self.obj, self.probe, self.iobs, self.psi = obj, probe, iobs, psi
+        self.N, self.K, self.J = N, K, J
+        self.Ho, self.Wo = obj.shape
+        self._prob = Problem(N=N, K=K, J=J, Ho=self.Ho, Wo=self.Wo, obj=obj.data_ptr(), probe=probe.data_ptr(),
+                             positions=pos.ctypes.data, iobs=iobs.data_ptr(),
+                             mask=(m.ctypes.data if m is not None else None),
+                             psi=(psi.data_ptr() if psi is not None else None))
+        nbytes = ctypes.c_size_t(0)
+        _lib.call("ptx_workspace_bytes", ctypes.byref(self._prob), 1, ctypes.byref(nbytes))
+        with torch.cuda.device(self.device):
+            self.scratch = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+            h = ctypes.c_void_p()
+            _lib.call("ptx_create", ctypes.byref(h), ctypes.byref(self._prob), 1,
+                      ctypes.c_void_p(self.scratch.data_ptr()), nbytes, _stream_ptr(self.device))
+        self._h = h
+        self._prob.positions = None
+        self._prob.mask = None
+        self.positions = pos
+        self.mask = m
+
+    # -- lifecycle -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            torch.cuda.current_stream(self.device).synchronize()
+            _lib.load().ptx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _handle(self):
+        if not self._h:
+            raise RuntimeError("Ptycho handle is closed")
+        return self._h
+
+    # -- algorithms ------------------------------------------------------------
+    @staticmethod
+    def _flags(update_obj, update_probe, graph, normalise=True):
+        f = 0
+        if update_obj:
+            f |= PTX_UPDATE_OBJ
+        if update_probe:
+            f |= PTX_UPDATE_PROBE
+        if not graph:
+            f |= PTX_NO_GRAPH
+        if not normalise:
+            f |= PTX_NO_NORMALISE
+        return f
+
+    def ap(self, ncycles: int, update_obj: bool = True, update_probe: bool = True, graph: bool = True,
+           normalise: bool = True, llk: torch.Tensor | None = None) -> torch.Tensor:
+        """``ncycles`` alternating-projection cycles; returns the per-cycle LLK
+        (float64 CUDA tensor of length ncycles)."""
+        out = llk if llk is not None else torch.empty(max(ncycles, 1), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            _lib.call("ptx_ap_cycles", self._handle(), int(ncycles),
+                      self._flags(update_obj, update_probe, graph, normalise),
+                      ctypes.c_void_p(out.data_ptr()), _stream_ptr(self.device))
+        return out[:ncycles]
+
+    def dm(self, ncycles: int, update_obj: bool = True, update_probe: bool = True, init_psi: bool = False,
+           graph: bool = True, normalise: bool = True, llk: torch.Tensor | None = None) -> torch.Tensor:
+        """``ncycles`` difference-map cycles; ``init_psi`` sets Psi = P O first."""
+        if self.psi is None:
+            raise ValueError("DM needs the exit-wave stack: create Ptycho with with_psi=True")
+        f = self._flags(update_obj, update_probe, graph, normalise)
+        if init_psi:
+            f |= PTX_DM_INIT_PSI
+        out = llk if llk is not None else torch.empty(max(ncycles, 1), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            _lib.call("ptx_dm_cycles", self._handle(), int(ncycles), f, ctypes.c_void_p(out.data_ptr()),
+                      _stream_ptr(self.device))
+        return out[:ncycles]
+
+    def llk(self) -> torch.Tensor:
+        """Exact Poisson LLK of the current object and probe (float64 CUDA scalar tensor)."""
+        out = torch.empty(1, dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            _lib.call("ptx_llk", self._handle(), ctypes.c_void_p(out.data_ptr()), _stream_ptr(self.device))
+        return out[0]
+
+    def ml_grad(self, grad_obj: bool = True, grad_probe: bool = True):
+        """Poisson-LLK gradient: returns (llk, G_O or None, G_P or None) with
+        G = dL/dRe z + i dL/dIm z (the PyTorch convention for real losses)."""
+        go = torch.empty_like(self.obj) if grad_obj else None
+        gp = torch.empty_like(self.probe) if grad_probe else None
+        out = torch.empty(1, dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            _lib.call("ptx_ml_grad", self._handle(), ctypes.c_void_p(go.data_ptr() if go is not None else None),
+                      ctypes.c_void_p(gp.data_ptr() if gp is not None else None), ctypes.c_void_p(out.data_ptr()),
+                      _stream_ptr(self.device))
+        return out[0], go, gp
+
+    def normalise(self, update_obj: bool = True, update_probe: bool = True):
+        """Normalise O, P from the accumulated numerators/denominators (after
+        cycles run with ``normalise=False`` and an all-reduce of ``accumulators()``)."""
+        with torch.cuda.device(self.device):
+            _lib.call("ptx_normalise", self._handle(), self._flags(update_obj, update_probe, True),
+                      _stream_ptr(self.device))
+
+    def accumulators(self):
+        """Views of the object and probe accumulators: float32 (Ho, Wo, 4) and
+        (K, N, N, 4) with {Re N, Im N, D, 0} per pixel."""
+        po, so, pp, sp = ctypes.c_void_p(), ctypes.c_size_t(), ctypes.c_void_p(), ctypes.c_size_t()
+        _lib.call("ptx_accumulators", self._handle(), 0, ctypes.byref(po), ctypes.byref(so), ctypes.byref(pp),
+                  ctypes.byref(sp))
+        base = self.scratch.data_ptr()
+        oo = po.value - base
+        op = pp.value - base
+        acc_o = self.scratch[oo:oo + so.value].view(torch.float32).view(self.Ho, self.Wo, 4)
+        acc_p = self.scratch[op:op + sp.value].view(torch.float32).view(self.K, self.N, self.N, 4)
+        return acc_o, acc_p
+
+    def set_param(self, name: str, value: float):
+        """``alpha_obj`` / ``alpha_probe``: inertia factors of the normalisation."""
+        _lib.call("ptx_set_param", self._handle(), name.encode(), float(value))
+
+
+def fft2(x: torch.Tensor, direction: int = -1) -> torch.Tensor:
+    """In-place orthonormal 2D FFT of complex64 frames (..., N, N) on the GPU
+    (the FT operator; ``direction=+1`` is IFT).  Returns ``x``."""
+    _require_cuda(x, "x", torch.complex64)
+    N = x.shape[-1]
+    if x.shape[-2] != N:
+        raise ValueError("frames must be square")
+    nframes = x.numel() // (N * N)
+    with torch.cuda.device(x.device):
+        _lib.call("ptx_fft2", ctypes.c_void_p(x.data_ptr()), int(nframes), int(N), int(direction),
+                  _stream_ptr(x.device))
+    return x
+
+
+class PtychoLLK(torch.autograd.Function):
+    """L(O, P) = Poisson LLK as a differentiable function of the object and the
+    probe.  ``forward`` copies (obj, probe) into the problem's buffers and calls
+    ptx_llk; ``backward`` calls ptx_ml_grad, which recomputes the exit waves
+    rather than storing them (the ML operator's gradient)."""
+
+    @staticmethod
+    def forward(ctx, obj: torch.Tensor, probe: torch.Tensor, problem: Ptycho):
+        with torch.no_grad():
+            problem.obj.copy_(obj)
+            problem.probe.copy_(probe)
+        ctx.problem = problem
+        ctx.needs = (obj.requires_grad, probe.requires_grad)
+        return problem.llk().clone()
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        pb = ctx.problem
+        _, go, gp = pb.ml_grad(grad_obj=ctx.needs[0], grad_probe=ctx.needs[1])
+        g = grad_out.to(torch.float32)
+        return (go * g if go is not None else None, gp * g if gp is not None else None, None)
+
+
+__all__ = ["Ptycho", "PtychoLLK", "PtychoError", "fft2", "SUPPORTED_SIZES"]

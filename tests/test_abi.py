@@ -1,0 +1,114 @@
+"""The C-ABI library loads, exports every symbol include/ptycho.h declares, and
+rejects bad arguments on the host (no device work: these run without a GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ptycho.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2008_11511_gb300 import build as b
+    b.build()
+    from paper_2008_11511_gb300 import _lib
+    return _lib.load()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ptx_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("ptx_create", "ptx_ap_cycles", "ptx_dm_cycles", "ptx_llk", "ptx_ml_grad", "ptx_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2008_11511_gb300._lib import EXPORTS
+    names = declared_functions()
+    assert sorted(EXPORTS) == names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _problem(N=64, K=1, J=3, Ho=128, Wo=100, positions=None):
+    from paper_2008_11511_gb300._lib import Problem
+    pos = np.array(positions if positions is not None else [[0, 0], [10, 20], [Ho - N, Wo - N]],
+                   dtype=np.int32)
+    p = Problem(N=N, K=K, J=len(pos), Ho=Ho, Wo=Wo, obj=0x1000, probe=0x2000, positions=pos.ctypes.data,
+                iobs=0x3000, mask=None, psi=None)
+    return p, pos
+
+
+def _ws(lib, p):
+    n = ctypes.c_size_t(0)
+    st = lib.ptx_workspace_bytes(ctypes.byref(p), 1, ctypes.byref(n))
+    return st, n.value
+
+
+def test_workspace_bytes_and_argument_checks(lib):
+    from paper_2008_11511_gb300._lib import STATUS_NAMES
+    p, pos = _problem()
+    st, n = _ws(lib, p)
+    assert st == 0 and n > 128 * 100 * 16
+    # unsupported frame size
+    p2, pos2 = _problem(N=100, Ho=200, Wo=200, positions=[[0, 0]])
+    st, _ = _ws(lib, p2)
+    assert STATUS_NAMES[st] == "PTX_ERR_UNSUPPORTED"
+    assert b"not supported" in lib.ptx_last_error()
+    # out-of-bounds position (one past the last valid row)
+    p3, pos3 = _problem(positions=[[0, 0], [128 - 64 + 1, 0]])
+    st, _ = _ws(lib, p3)
+    assert STATUS_NAMES[st] == "PTX_ERR_OUT_OF_BOUNDS"
+    p4, pos4 = _problem(positions=[[0, -1]])
+    st, _ = _ws(lib, p4)
+    assert STATUS_NAMES[st] == "PTX_ERR_OUT_OF_BOUNDS"
+    # too many modes, zero modes, object smaller than the frame
+    p5, pos5 = _problem(K=9)
+    assert STATUS_NAMES[_ws(lib, p5)[0]] == "PTX_ERR_UNSUPPORTED"
+    p6, pos6 = _problem(K=0)
+    assert STATUS_NAMES[_ws(lib, p6)[0]] == "PTX_ERR_INVALID_ARG"
+    p7, pos7 = _problem(Ho=32, Wo=32, positions=[[0, 0]])
+    assert STATUS_NAMES[_ws(lib, p7)[0]] == "PTX_ERR_INVALID_ARG"
+    # null arguments
+    n = ctypes.c_size_t()
+    assert STATUS_NAMES[lib.ptx_workspace_bytes(None, 1, ctypes.byref(n))] == "PTX_ERR_INVALID_ARG"
+    p8, pos8 = _problem()
+    p8.iobs = None
+    assert STATUS_NAMES[_ws(lib, p8)[0]] == "PTX_ERR_INVALID_ARG"
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    from paper_2008_11511_gb300._lib import STATUS_NAMES
+    assert STATUS_NAMES[lib.ptx_ap_cycles(None, 1, 3, None, None)] == "PTX_ERR_INVALID_ARG"
+    assert STATUS_NAMES[lib.ptx_dm_cycles(None, 1, 3, None, None)] == "PTX_ERR_INVALID_ARG"
+    assert STATUS_NAMES[lib.ptx_llk(None, None, None)] == "PTX_ERR_INVALID_ARG"
+    assert STATUS_NAMES[lib.ptx_ml_grad(None, None, None, None, None)] == "PTX_ERR_INVALID_ARG"
+    assert STATUS_NAMES[lib.ptx_set_param(None, b"alpha_obj", 0.1)] == "PTX_ERR_INVALID_ARG"
+    assert STATUS_NAMES[lib.ptx_fft2(None, 1, 64, -1, None)] == "PTX_ERR_INVALID_ARG"
+    assert STATUS_NAMES[lib.ptx_fft2(ctypes.c_void_p(0x1000), 1, 100, -1, None)] == "PTX_ERR_UNSUPPORTED"
+    assert STATUS_NAMES[lib.ptx_fft2(ctypes.c_void_p(0x1000), 1, 64, 2, None)] == "PTX_ERR_INVALID_ARG"
+    lib.ptx_destroy(None)
+
+
+def test_product_package_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2008_11511_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_python_api_imports_without_a_gpu():
+    from paper_2008_11511_gb300 import Ptycho, PtychoError, PtychoLLK, fft2  # noqa: F401
+    import paper_2008_11511_gb300.ptycho as m
+    assert m.Ptycho is Ptycho

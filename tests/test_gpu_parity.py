@@ -1,0 +1,447 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative L2 norm ||x - x_ref|| / ||x_ref||, float32 path vs float64
+oracle): 1e-5 for one cycle (object, probe, exit waves, log-likelihood), 1e-4
+after 20 or 100 cycles.  The object error is also measured on the illuminated
+region (D_O > 1e-3 max D_O) where the update acts.
+
+Both sides start from the same complex64 state.  The configured start points
+(flat object, Gaussian-blurred probe) put up to half of the detector pixels
+below the float32 FFT resolution (model amplitude < 1e-7 of the peak), where
+any single-precision transform returns rounding noise and the amplitude
+projection gives the observed photons that noise's phase.  Cycle parity is
+therefore checked from "warm" states (the oracle's state after one or more AP
+cycles, where the spectrum is filled), and the configured start itself is
+checked against an independent single-precision evaluation of the same cycle
+(test_configured_start_is_at_the_float32_floor).
+"""
+import copy
+import functools
+
+import scipy.fft
+import numpy as np
+import pytest
+
+import oracle
+from synthetic import make_config, make_scan
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL1 = 1e-5     # one float32 cycle
+TOL20 = 1e-4    # many cycles
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2008_11511_gb300 import build as b
+    b.build()
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def to_dev(x):
+    return torch.tensor(np.ascontiguousarray(x), device="cuda")
+
+
+def gpu_problem(s, with_psi=True, obj=None, probe=None):
+    from paper_2008_11511_gb300 import Ptycho
+    o = to_dev((s.obj0 if obj is None else obj).astype(np.complex64))
+    p = to_dev((s.probe0 if probe is None else probe).astype(np.complex64))
+    return Ptycho(o, p, to_dev(s.iobs), s.positions, s.mask, with_psi=with_psi)
+
+
+def data_of(s):
+    return oracle.Data.make(s.iobs, s.positions, s.mask)
+
+
+def illuminated(s, probe):
+    d = oracle.object_denominator(probe, s.positions, (s.Ho, s.Wo))
+    return d > 1e-3 * d.max()
+
+
+def check_close(name, got, ref, tol):
+    e = rel(got, ref)
+    assert e < tol, f"{name}: rel err {e:.3e} >= {tol:.0e}"
+    return e
+
+
+@functools.lru_cache(maxsize=None)
+def _warm_cached(cfg, J, n_ap, over):
+    s = make_config(cfg, J=J, **dict(over))
+    o, p = s.obj0.astype(complex), s.probe0.astype(complex)
+    data = data_of(s)
+    for _ in range(n_ap):
+        o, p, _ = oracle.ap_cycle(o, p, data)
+    return s, o.astype(np.complex64), p.astype(np.complex64)
+
+
+def warm(cfg, J=None, n_ap=1, **over):
+    """(scan, obj, probe): the oracle's state after n_ap AP cycles from the
+    configured start, rounded to complex64 (the common start of both sides)."""
+    s, o, p = _warm_cached(cfg, J, n_ap, tuple(sorted(over.items())))
+    return copy.copy(s), o.copy(), p.copy()
+
+
+# ------------------------------------------------------------------ FT / IFT
+
+@pytest.mark.parametrize("N", [8, 12, 16, 32, 64, 128, 192, 256, 384, 512])
+def test_fft2_matches_oracle(N):
+    from paper_2008_11511_gb300 import fft2
+    rng = np.random.default_rng(N)
+    nf = 5
+    x = (rng.standard_normal((nf, N, N)) + 1j * rng.standard_normal((nf, N, N))).astype(np.complex64)
+    X = to_dev(x)
+    fft2(X, -1)
+    ref = oracle.ft(x.astype(np.complex128))
+    check_close(f"FT N={N}", X.cpu().numpy(), ref, 2e-6)
+    fft2(X, +1)
+    check_close(f"IFT(FT) N={N}", X.cpu().numpy(), x, 3e-6)
+
+
+@pytest.mark.parametrize("N", [32, 192, 256])
+def test_fft2_special_inputs(N):
+    from paper_2008_11511_gb300 import fft2
+    d = np.zeros((3, N, N), np.complex64)
+    d[0, 0, 0] = 1.0                                   # delta -> constant 1/N
+    d[1] = 1.0                                          # constant -> N delta at DC
+    yy, xx = np.mgrid[0:N, 0:N]
+    d[2] = np.exp(2j * np.pi * (3 * yy + 5 * xx) / N)   # single frequency -> N delta at (3, 5)
+    X = to_dev(d)
+    fft2(X, -1)
+    got = X.cpu().numpy()
+    exp0 = np.full((N, N), 1.0 / N)
+    exp1 = np.zeros((N, N)); exp1[0, 0] = N
+    exp2 = np.zeros((N, N), complex); exp2[3, 5] = N
+    assert np.abs(got[0] - exp0).max() < 1e-6
+    assert np.abs(got[1] - exp1).max() < 1e-3
+    assert np.abs(got[2] - exp2).max() < 2e-3
+
+
+def test_fft2_direct_dft_small():
+    from paper_2008_11511_gb300 import fft2
+    rng = np.random.default_rng(3)
+    for N in (8, 12, 16):
+        x = (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))).astype(np.complex64)
+        ref = np.zeros((N, N), complex)
+        y = np.arange(N)
+        for ky in range(N):
+            for kx in range(N):
+                ref[ky, kx] = (x * np.exp(-2j * np.pi * (ky * y[:, None] + kx * y[None, :]) / N)).sum() / N
+        X = to_dev(x[None])
+        fft2(X, -1)
+        check_close(f"direct DFT N={N}", X.cpu().numpy()[0], ref, 1e-6)
+
+
+# ------------------------------------------------------------------ LLK and gradient
+
+@pytest.mark.parametrize("cfg,J", [("ap64", 100), ("ml32fd", 16), ("dm256", 40)])
+def test_llk_exact_parity(cfg, J):
+    s, o, p = warm(cfg, J=J)
+    pb = gpu_problem(s, with_psi=False, obj=o, probe=p)
+    g = float(pb.llk())
+    ref = oracle.llk(o, p, data_of(s))
+    assert abs(g - ref) / abs(ref) < TOL1, (g, ref)
+    pb.close()
+
+
+def test_llk_with_mask_and_negative_intensities():
+    s, o, p = warm("ap64", J=30, mask_fraction=0.05)
+    s.iobs = s.iobs.copy()
+    s.iobs[0, 5, 7] = -2.0          # negative observations are clamped to 0
+    s.iobs[3, 0, 1] = -0.5
+    pb = gpu_problem(s, with_psi=False, obj=o, probe=p)
+    g = float(pb.llk())
+    ref = oracle.llk(o, p, data_of(s))
+    assert abs(g - ref) / abs(ref) < TOL1
+    pb.close()
+
+
+def test_llk_zero_at_noise_free_truth():
+    s = make_config("ap64", J=40, noise=False)
+    pb = gpu_problem(s, with_psi=False, obj=s.obj_true, probe=s.probe_true)
+    g = float(pb.llk())
+    assert 0 <= g < 1e-6 * float(s.iobs.sum()), g
+    pb.close()
+
+
+@pytest.mark.parametrize("cfg,J,tol", [("ml32fd", 16, 1e-4), ("ml256", 60, 1e-4)])
+def test_ml_grad_parity(cfg, J, tol):
+    """The gradient weight 2(1 - I_o/I_c) amplifies float32 errors of small I_c, so
+    the comparison starts after 3 AP cycles (ML follows DM/AP in the paper's chains)."""
+    s, obj, probe = warm(cfg, J=J, n_ap=3)
+    pb = gpu_problem(s, with_psi=False, obj=obj, probe=probe)
+    L, go, gp = pb.ml_grad()
+    ref_L, ref_go, ref_gp = oracle.ml_grad(obj, probe, data_of(s))
+    assert abs(float(L) - ref_L) / abs(ref_L) < TOL1
+    check_close("G_O", go.cpu().numpy(), ref_go, tol)
+    check_close("G_P", gp.cpu().numpy(), ref_gp, tol)
+    pb.close()
+
+
+def test_ml_grad_autograd_function():
+    from paper_2008_11511_gb300 import PtychoLLK
+    s, obj, probe = warm("ml32fd", n_ap=3)
+    pb = gpu_problem(s, with_psi=False)
+    o = to_dev(obj).requires_grad_(True)
+    p = to_dev(probe).requires_grad_(True)
+    L = PtychoLLK.apply(o, p, pb)
+    (3.0 * L).backward()
+    ref_L, ref_go, ref_gp = oracle.ml_grad(obj, probe, data_of(s))
+    assert abs(float(L.detach()) - ref_L) / abs(ref_L) < TOL1
+    check_close("autograd G_O", o.grad.cpu().numpy(), 3.0 * ref_go, 1e-4)
+    check_close("autograd G_P", p.grad.cpu().numpy(), 3.0 * ref_gp, 1e-4)
+    pb.close()
+
+
+# ------------------------------------------------------------------ AP / DM cycles
+
+def _compare_cycle_state(s, pb, o_ref, p_ref, tol, psi_ref=None):
+    o = pb.obj.cpu().numpy()
+    p = pb.probe.cpu().numpy()
+    ill = illuminated(s, p_ref)
+    e = {"obj": check_close("obj", o, o_ref, tol),
+         "obj_ill": check_close("obj (illuminated)", o[ill], o_ref[ill], tol),
+         "probe": check_close("probe", p, p_ref, tol)}
+    if psi_ref is not None:
+        e["psi"] = check_close("psi", pb.psi.cpu().numpy(), psi_ref, tol)
+    return e
+
+
+def test_ap_one_cycle_parity():
+    s, o0, p0 = warm("ap64")
+    pb = gpu_problem(s, with_psi=False, obj=o0, probe=p0)
+    llk = pb.ap(1).cpu().numpy()
+    o, p, l = oracle.ap_cycle(o0, p0, data_of(s))
+    _compare_cycle_state(s, pb, o, p, TOL1)
+    assert abs(llk[0] - l) / abs(l) < TOL1
+    pb.close()
+
+
+def test_ap64_20_cycles_parity():
+    """Plain AP, 64x64 probe, 256x256 object, 100 positions, 20 cycles."""
+    s, o0, p0 = warm("ap64")
+    pb = gpu_problem(s, with_psi=False, obj=o0, probe=p0)
+    llk = pb.ap(20).cpu().numpy()
+    o, p, _, llk_ref = oracle.cycles("AP", o0, p0, data_of(s), 20)
+    _compare_cycle_state(s, pb, o, p, TOL20)
+    np.testing.assert_allclose(llk, llk_ref, rtol=TOL20)
+    assert llk[-1] < llk[0]
+    pb.close()
+
+
+@pytest.mark.parametrize("flags", [(True, True), (True, False), (False, True), (False, False)])
+def test_ap_update_flags(flags):
+    s, o0, p0 = warm("ap64", J=30)
+    pb = gpu_problem(s, with_psi=False, obj=o0, probe=p0)
+    pb.ap(2, update_obj=flags[0], update_probe=flags[1])
+    o, p, _, _ = oracle.cycles("AP", o0, p0, data_of(s), 2, update_obj=flags[0], update_probe=flags[1])
+    _compare_cycle_state(s, pb, o, p, TOL1 * 2)
+    if not flags[0]:
+        assert np.array_equal(pb.obj.cpu().numpy(), o0)
+    if not flags[1]:
+        assert np.array_equal(pb.probe.cpu().numpy(), p0)
+    pb.close()
+
+
+def test_dm_cycles_parity_256_masked_ragged_batches():
+    """DM on 256x256 frames with the 2% detector-gap mask; J = 300 spans three
+    batches of the Fourier work stack with a ragged last batch."""
+    s, o0, p0 = warm("dm256", J=300, Ho=768, Wo=768)
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    llk = pb.dm(3, init_psi=True).cpu().numpy()
+    o, p, psi, llk_ref = oracle.cycles("DM", o0, p0, data_of(s), 3)
+    _compare_cycle_state(s, pb, o, p, TOL1 * 3, psi_ref=psi)
+    np.testing.assert_allclose(llk, llk_ref, rtol=TOL1 * 3)
+    pb.close()
+
+
+def test_dm_one_cycle_parity_from_given_psi():
+    s = make_config("ap64", J=50)
+    rng = np.random.default_rng(5)
+    phi = oracle.obj_probe_to_psi(s.obj0.astype(complex), s.probe0.astype(complex), s.positions)
+    psi0 = (phi + 0.1 * (rng.standard_normal(phi.shape) + 1j * rng.standard_normal(phi.shape))).astype(np.complex64)
+    from paper_2008_11511_gb300 import Ptycho
+    pb = Ptycho(to_dev(s.obj0), to_dev(s.probe0), to_dev(s.iobs), s.positions, s.mask, psi=to_dev(psi0))
+    llk = pb.dm(1).cpu().numpy()
+    o, p, psi, l = oracle.dm_cycle(s.obj0, s.probe0, psi0, data_of(s))
+    _compare_cycle_state(s, pb, o, p, TOL1, psi_ref=psi)
+    assert abs(llk[0] - l) / abs(l) < TOL1
+    pb.close()
+
+
+def test_graph_and_direct_launch_agree():
+    s, o0, p0 = warm("ap64", J=60)
+    a = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    b = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    la = a.dm(3, init_psi=True, graph=True).cpu().numpy()
+    lb = b.dm(3, init_psi=True, graph=False).cpu().numpy()
+    assert rel(a.obj.cpu().numpy(), b.obj.cpu().numpy()) < 1e-6
+    assert rel(a.probe.cpu().numpy(), b.probe.cpu().numpy()) < 1e-6
+    np.testing.assert_allclose(la, lb, rtol=1e-6)
+    a.close(); b.close()
+
+
+# ------------------------------------------------------------------ modes
+
+def test_multimode_dm_parity():
+    """Three orthogonalised Hermite-Gauss modes (powers 0.7/0.2/0.1), 512x512 frames."""
+    s, o0, p0 = warm("modes512", J=24, Ho=1024, Wo=1024)
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    llk = pb.dm(2, init_psi=True).cpu().numpy()
+    o, p, psi, llk_ref = oracle.cycles("DM", o0, p0, data_of(s), 2)
+    _compare_cycle_state(s, pb, o, p, TOL1 * 2, psi_ref=psi)
+    np.testing.assert_allclose(llk, llk_ref, rtol=TOL1 * 2)
+    pb.close()
+
+
+def test_zero_extra_mode_equals_single_mode():
+    s, o0, p0 = warm("ap64", J=30)
+    p2 = np.concatenate([p0, np.zeros_like(p0)])
+    a = gpu_problem(s, with_psi=False, obj=o0, probe=p0)
+    b = gpu_problem(s, with_psi=False, obj=o0, probe=p2)
+    a.ap(2, update_probe=False)
+    b.ap(2, update_probe=False)
+    assert rel(b.obj.cpu().numpy(), a.obj.cpu().numpy()) < 1e-6
+    a.close(); b.close()
+
+
+# ------------------------------------------------------------------ edge cases
+
+@pytest.mark.parametrize("N", [32, 192, 384])
+def test_other_frame_sizes_ap(N):
+    s = make_scan(f"n{N}", N=N, J=12, Ho=N + 40, Wo=N + 24, seed=N, photons=1e5, step=N / 12,
+                  probe_radius=N * 0.18, mask_fraction=0.02)
+    o0, p0, _ = oracle.ap_cycle(s.obj0, s.probe0, data_of(s))
+    o0, p0 = o0.astype(np.complex64), p0.astype(np.complex64)
+    pb = gpu_problem(s, with_psi=False, obj=o0, probe=p0)
+    llk = pb.ap(1).cpu().numpy()
+    o, p, l = oracle.ap_cycle(o0, p0, data_of(s))
+    _compare_cycle_state(s, pb, o, p, TOL1)
+    assert abs(llk[0] - l) / abs(l) < TOL1
+    pb.close()
+
+
+def test_single_frame_object_equals_frame_corner_positions():
+    """J = 1 and the object exactly one frame; then positions at both extreme corners."""
+    s = make_scan("one", N=64, J=1, Ho=64, Wo=64, seed=11, photons=1e5, step=10, probe_radius=20)
+    o0, p0, _ = oracle.ap_cycle(s.obj0, s.probe0, data_of(s))
+    o0, p0 = o0.astype(np.complex64), p0.astype(np.complex64)
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    pb.dm(2, init_psi=True)
+    o, p, psi, _ = oracle.cycles("DM", o0, p0, data_of(s), 2)
+    _compare_cycle_state(s, pb, o, p, TOL1 * 2, psi_ref=psi)
+    pb.close()
+    s2, o2, p2 = warm("ap64", J=4)
+    s2.positions = np.array([[0, 0], [256 - 64, 256 - 64], [0, 256 - 64], [256 - 64, 0]], dtype=np.int32)
+    o2, p2, _ = oracle.ap_cycle(o2, p2, data_of(s2))
+    o2, p2 = o2.astype(np.complex64), p2.astype(np.complex64)
+    pb = gpu_problem(s2, with_psi=False, obj=o2, probe=p2)
+    pb.ap(1)
+    o, p, _ = oracle.ap_cycle(o2, p2, data_of(s2))
+    _compare_cycle_state(s2, pb, o, p, TOL1)
+    pb.close()
+
+
+def test_fully_masked_detector_leaves_waves_free():
+    s, o0, p0 = warm("ap64", J=10)
+    s.mask = np.ones_like(s.mask)
+    pb = gpu_problem(s, with_psi=False, obj=o0, probe=p0)
+    llk = pb.ap(1).cpu().numpy()
+    assert llk[0] == 0.0
+    o, p, _ = oracle.ap_cycle(o0, p0, data_of(s))
+    _compare_cycle_state(s, pb, o, p, TOL1)
+    pb.close()
+
+
+def test_zero_probe_region_gives_zero_not_nan():
+    s, o0, p0 = warm("ap64", J=10)
+    probe = np.zeros_like(p0)
+    probe[0, 20:40, 20:40] = p0[0, 20:40, 20:40]
+    pb = gpu_problem(s, with_psi=False, obj=o0, probe=probe)
+    llk = pb.ap(1).cpu().numpy()
+    assert np.all(np.isfinite(pb.obj.cpu().numpy())) and np.all(np.isfinite(pb.probe.cpu().numpy()))
+    o, p, l = oracle.ap_cycle(o0, probe, data_of(s))
+    _compare_cycle_state(s, pb, o, p, TOL1)
+    assert abs(llk[0] - l) / abs(l) < TOL1
+    pb.close()
+
+
+def test_out_of_bounds_position_is_rejected():
+    from paper_2008_11511_gb300 import PtychoError
+    s = make_config("ap64", J=5)
+    s.positions[2] = [256 - 64 + 1, 3]
+    with pytest.raises(PtychoError, match="OUT_OF_BOUNDS"):
+        gpu_problem(s, with_psi=False)
+
+
+def test_accumulators_and_external_normalise_match_internal():
+    """Data-parallel form: cycles with normalise=False, then ptx_normalise, equal
+    the fused cycle (the all-reduce of a multi-GPU split would sit in between)."""
+    s, o0, p0 = warm("ap64", J=40)
+    a = gpu_problem(s, with_psi=False, obj=o0, probe=p0)
+    b = gpu_problem(s, with_psi=False, obj=o0, probe=p0)
+    a.ap(1)
+    b.ap(1, normalise=False)
+    acc_o, acc_p = b.accumulators()
+    assert float(acc_o[..., 2].max()) > 0
+    b.normalise()
+    assert rel(b.obj.cpu().numpy(), a.obj.cpu().numpy()) < 1e-6
+    assert rel(b.probe.cpu().numpy(), a.probe.cpu().numpy()) < 1e-6
+    assert float(b.accumulators()[0].abs().max()) == 0.0
+    a.close(); b.close()
+
+
+# ------------------------------------------------------------------ long runs and conditioning
+
+def test_dm_100_cycles_parity_ap64():
+    """DM, 100 cycles on the 64x64-frame scan: <= 1e-4 after 100 float32 cycles."""
+    s, o0, p0 = warm("ap64")
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    llk = pb.dm(100, init_psi=True).cpu().numpy()
+    o, p, psi, llk_ref = oracle.cycles("DM", o0, p0, data_of(s), 100)
+    _compare_cycle_state(s, pb, o, p, TOL20, psi_ref=psi)
+    np.testing.assert_allclose(llk, llk_ref, rtol=TOL20)
+    pb.close()
+
+
+def _single_precision_ap_cycle(obj, probe, data):
+    """The AP cycle with every transform and the projection in complex64 (SciPy's
+    single-precision FFT), accumulation and normalisation as the oracle: an
+    independent float32 evaluation used to measure the float32 floor."""
+    obj32 = obj.astype(np.complex64)
+    probe32 = probe.astype(np.complex64)
+    N = probe.shape[-1]
+    phi = np.stack([probe32 * obj32[r:r + N, c:c + N][None] for r, c in data.positions])
+    X = scipy.fft.fft2(phi, norm="ortho", axes=(-2, -1))
+    ic = (np.abs(X) ** 2).sum(1)
+    sc = np.where(data.mask, 1.0, np.sqrt(np.maximum(data.iobs, 0)) / np.maximum(np.sqrt(ic), 1e-20))
+    psi = scipy.fft.ifft2(X * sc[:, None].astype(np.float32), norm="ortho", axes=(-2, -1))
+    sums = oracle.psi_to_obj_probe_sums(psi.astype(complex), obj32.astype(complex), probe32.astype(complex),
+                                        data.positions, obj.shape)
+    return oracle.normalise(obj32.astype(complex), probe32.astype(complex), sums)
+
+
+@pytest.mark.parametrize("cfg,J", [("ap64", 100), ("dm256", 40)])
+def test_configured_start_is_at_the_float32_floor(cfg, J):
+    """From the configured start (flat object, blurred probe) one GPU AP cycle
+    differs from FP64 by no more than an independent single-precision cycle does."""
+    s = make_config(cfg, J=J)
+    data = data_of(s)
+    X = np.abs(oracle.ft(oracle.obj_probe_to_psi(s.obj0.astype(complex), s.probe0.astype(complex),
+                                                 s.positions[:1])))[0, 0]
+    assert (X < 1e-7 * X.max()).mean() > 0.01  # the start is ill-conditioned in float32
+    pb = gpu_problem(s, with_psi=False)
+    pb.ap(1)
+    o64, p64, _ = oracle.ap_cycle(s.obj0, s.probe0, data)
+    o32, p32 = _single_precision_ap_cycle(s.obj0, s.probe0, data)
+    floor_o, floor_p = rel(o32, o64), rel(p32, p64)
+    e_o, e_p = rel(pb.obj.cpu().numpy(), o64), rel(pb.probe.cpu().numpy(), p64)
+    assert e_o < 2 * floor_o + TOL1 and e_p < 2 * floor_p + TOL1, (e_o, floor_o, e_p, floor_p)
+    pb.close()
