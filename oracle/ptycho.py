@@ -32,9 +32,13 @@ Readings of points the paper leaves open (each is listed in the design doc):
   the log.  It is 0 on exact data and >= 0.
 * DM: beta = 1 difference map, Psi <- Psi + P_F(2 P_O Psi - Psi) - P_O Psi, with
   P_O Psi = Phi formed from the current O, P; Psi starts at Phi.
-* Psi2ObjProbe: one Jacobi step (object and probe both from the same pre-update
-  O, P) with inertia: O <- (N_O + d_O O) / (D_O + d_O), d_O = alpha_O max D_O,
-  and likewise for P with d_P = alpha_P max D_P.
+* Psi2ObjProbe: one alternation of the two least-squares updates, probe first:
+  P <- (N_P + d_P P) / (D_P + d_P) with N_P, D_P from the current object, then
+  O <- (N_O + d_O O) / (D_O + d_O) with N_O, D_O from the new probe; inertia
+  d = alpha max D.  (Updating both from the same pre-update O, P lets a scale
+  error of Psi enter both factors, so P O absorbs it twice; under DM that
+  doubling makes the iteration diverge, |Psi| x2.5 per cycle on the 64x64
+  scan.)
 * The per-cycle LLK is that of the wave being projected (Phi for AP, 2 Phi - Psi
   for DM); ``llk`` gives the exact L(O, P).
 """
@@ -140,60 +144,79 @@ def llk_poisson(icalc, iobs, mask):
     return float(llk_terms(icalc, iobs, mask).sum())
 
 
-def psi_to_obj_probe_sums(psi, obj, probe, positions, shape_obj):
-    """Psi2ObjProbe accumulation (numerators and denominators), all from the
-    same O, P (Jacobi):
+def psi_to_probe_sums(psi, obj, positions):
+    """Psi2ObjProbe probe numerator and denominator from the object O:
+      N_Pk(x) = sum_j conj(O(r_j + x)) Psi_jk(x),   D_P(x) = sum_j |O(r_j + x)|^2"""
+    J, K, N, _ = psi.shape
+    n_p = np.zeros((K, N, N), dtype=np.complex128)
+    d_p = np.zeros((N, N), dtype=np.float64)
+    for j, (r, c) in enumerate(positions):
+        patch = obj[r:r + N, c:c + N]
+        n_p += np.conj(patch)[None] * psi[j]
+        d_p += patch.real ** 2 + patch.imag ** 2
+    return n_p, d_p
 
-      N_O(r_j + x) += sum_k conj(P_k(x)) Psi_jk(x)     D_O(r_j + x) += sum_k |P_k(x)|^2
-      N_Pk(x)      += conj(O(r_j + x)) Psi_jk(x)        D_P(x)       += |O(r_j + x)|^2
-    """
+
+def psi_to_obj_sums(psi, probe, positions, shape_obj):
+    """Psi2ObjProbe object numerator and denominator from the probe P:
+      N_O(r_j + x) += sum_k conj(P_k(x)) Psi_jk(x),   D_O(r_j + x) += sum_k |P_k(x)|^2"""
     K, N, _ = probe.shape
     n_o = np.zeros(shape_obj, dtype=np.complex128)
     d_o = np.zeros(shape_obj, dtype=np.float64)
-    n_p = np.zeros((K, N, N), dtype=np.complex128)
-    d_p = np.zeros((N, N), dtype=np.float64)
     p_conj = np.conj(probe)
     p_pow = (probe.real ** 2 + probe.imag ** 2).sum(0)
     for j, (r, c) in enumerate(positions):
-        patch = obj[r:r + N, c:c + N]
         n_o[r:r + N, c:c + N] += (p_conj * psi[j]).sum(0)
         d_o[r:r + N, c:c + N] += p_pow
-        n_p += np.conj(patch)[None] * psi[j]
-        d_p += patch.real ** 2 + patch.imag ** 2
+    return n_o, d_o
+
+
+def psi_to_obj_probe_sums(psi, obj, probe, positions, shape_obj):
+    """All four sums from the same (O, P): (N_O, D_O, N_P, D_P)."""
+    n_o, d_o = psi_to_obj_sums(psi, probe, positions, shape_obj)
+    n_p, d_p = psi_to_probe_sums(psi, obj, positions)
     return n_o, d_o, n_p, d_p
+
+
+def inertia_update(old, num, den, alpha):
+    """(num + d old) / (den + d), d = alpha max(den) (inertia, Section 4 feature list).
+    A pixel whose denominator den + d is zero (alpha = 0 and never illuminated)
+    keeps its value (the paper is silent on this case).  ``den`` broadcasts over
+    leading axes of ``old`` (probe modes)."""
+    delta = alpha * den.max()
+    d = den + delta
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(d > 0, (num + delta * old) / d, old)
 
 
 def normalise(obj, probe, sums, alpha_obj=1e-2, alpha_probe=1e-2,
               update_obj=True, update_probe=True):
-    """Psi2ObjProbe normalisation with inertia:
-    O <- (N_O + d_O O) / (D_O + d_O), d_O = alpha_O max D_O; same for P.
-    A pixel whose denominator D + d is zero (alpha = 0 and never illuminated)
-    keeps its value (the paper is silent on this case)."""
+    """Normalisation of precomputed sums (N_O, D_O, N_P, D_P) with inertia."""
     n_o, d_o, n_p, d_p = sums
     if update_obj:
-        delta = alpha_obj * d_o.max()
-        den = d_o + delta
-        with np.errstate(divide="ignore", invalid="ignore"):
-            obj = np.where(den > 0, (n_o + delta * obj) / den, obj)
+        obj = inertia_update(obj, n_o, d_o, alpha_obj)
     if update_probe:
-        delta = alpha_probe * d_p.max()
-        den = (d_p + delta)[None]
-        with np.errstate(divide="ignore", invalid="ignore"):
-            probe = np.where(den > 0, (n_p + delta * probe) / den, probe)
+        probe = inertia_update(probe, n_p, d_p[None], alpha_probe)
+    return obj, probe
+
+
+def overlap_update(obj, probe, psi, positions, alpha_obj=1e-2, alpha_probe=1e-2,
+                   update_obj=True, update_probe=True):
+    """Psi2ObjProbe: update the probe and/or the object from the exit waves Psi
+    (paper: operator table): probe first from the current object, then the
+    object from the new probe."""
+    if update_probe:
+        n_p, d_p = psi_to_probe_sums(psi, obj, positions)
+        probe = inertia_update(probe, n_p, d_p[None], alpha_probe)
+    if update_obj:
+        n_o, d_o = psi_to_obj_sums(psi, probe, positions, obj.shape)
+        obj = inertia_update(obj, n_o, d_o, alpha_obj)
     return obj, probe
 
 
 def _stacks(J, stack=STACK):
     for lo in range(0, J, stack):
         yield lo, min(J, lo + stack)
-
-
-def _add_sums(acc, part):
-    if acc is None:
-        return [a.copy() for a in part]
-    for a, b in zip(acc, part):
-        a += b
-    return acc
 
 
 # --------------------------------------------------------------------------
@@ -207,16 +230,15 @@ def ap_cycle(obj, probe, data: Data, alpha_obj=1e-2, alpha_probe=1e-2,
     Psi2ObjProbe.  Returns (obj, probe, llk of FT(Phi))."""
     obj = np.asarray(obj, dtype=np.complex128)
     probe = np.asarray(probe, dtype=np.complex128)
-    sums = None
+    psi = np.empty((data.J,) + probe.shape, dtype=np.complex128)
     llk = 0.0
     for lo, hi in _stacks(data.J):
         pos = data.positions[lo:hi]
         phi = obj_probe_to_psi(obj, probe, pos)
         phi_hat = ft(phi)
         llk += llk_poisson(calc_intensity(phi_hat), data.iobs[lo:hi], data.mask)
-        psi = ift(apply_amplitude(phi_hat, data.iobs[lo:hi], data.mask))
-        sums = _add_sums(sums, psi_to_obj_probe_sums(psi, obj, probe, pos, obj.shape))
-    obj, probe = normalise(obj, probe, sums, alpha_obj, alpha_probe, update_obj, update_probe)
+        psi[lo:hi] = ift(apply_amplitude(phi_hat, data.iobs[lo:hi], data.mask))
+    obj, probe = overlap_update(obj, probe, psi, data.positions, alpha_obj, alpha_probe, update_obj, update_probe)
     return obj, probe, llk
 
 
@@ -233,7 +255,6 @@ def dm_cycle(obj, probe, psi, data: Data, alpha_obj=1e-2, alpha_probe=1e-2,
     if init_psi or psi is None:
         psi = np.empty((J,) + probe.shape, dtype=np.complex128)
         init_psi = True
-    sums = None
     llk = 0.0
     for lo, hi in _stacks(J):
         pos = data.positions[lo:hi]
@@ -245,8 +266,7 @@ def dm_cycle(obj, probe, psi, data: Data, alpha_obj=1e-2, alpha_probe=1e-2,
         llk += llk_poisson(calc_intensity(x_hat), data.iobs[lo:hi], data.mask)
         x_proj = ift(apply_amplitude(x_hat, data.iobs[lo:hi], data.mask))
         psi[lo:hi] = psi[lo:hi] + x_proj - phi
-        sums = _add_sums(sums, psi_to_obj_probe_sums(psi[lo:hi], obj, probe, pos, obj.shape))
-    obj, probe = normalise(obj, probe, sums, alpha_obj, alpha_probe, update_obj, update_probe)
+    obj, probe = overlap_update(obj, probe, psi, data.positions, alpha_obj, alpha_probe, update_obj, update_probe)
     return obj, probe, psi, llk
 
 
@@ -354,7 +374,8 @@ def frames_covering(positions, N, pixel):
 
 __all__ = [
     "Data", "ft", "ift", "obj_probe_to_psi", "calc_intensity", "apply_amplitude", "llk_terms",
-    "llk_poisson", "psi_to_obj_probe_sums", "normalise", "ap_cycle", "dm_cycle", "llk", "ml_grad",
+    "llk_poisson", "psi_to_probe_sums", "psi_to_obj_sums", "psi_to_obj_probe_sums", "inertia_update",
+    "normalise", "overlap_update", "ap_cycle", "dm_cycle", "llk", "ml_grad",
     "cycles", "dm_frame_update", "frames_llk", "object_denominator", "frames_covering",
     "ICALC_FLOOR", "AMP_FLOOR", "STACK",
 ]

@@ -25,13 +25,12 @@ def split_positions(positions, world: int, rank: int) -> np.ndarray:
     return np.sort(np.array_split(order, world)[rank])
 
 
-def allreduce_accumulators(acc_obj: torch.Tensor, acc_probe: torch.Tensor, llk: torch.Tensor | None = None,
-                           group=None):
-    """Sum the packed accumulators (and the LLK) over all ranks in place."""
-    dist.all_reduce(acc_obj, op=dist.ReduceOp.SUM, group=group)
-    dist.all_reduce(acc_probe, op=dist.ReduceOp.SUM, group=group)
-    if llk is not None:
-        dist.all_reduce(llk, op=dist.ReduceOp.SUM, group=group)
+def allreduce_accumulators(acc_obj: torch.Tensor | None, acc_probe: torch.Tensor | None,
+                           llk: torch.Tensor | None = None, group=None):
+    """Sum the given packed accumulators (and the LLK) over all ranks in place."""
+    for t in (acc_obj, acc_probe, llk):
+        if t is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
 
 
 def dm_cycles_data_parallel(pb, ncycles: int, update_obj=True, update_probe=True, init_psi=False, group=None):

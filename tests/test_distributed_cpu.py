@@ -52,13 +52,18 @@ def _worker(rank, world, port, outdir):
     llk = torch.tensor([oracle.llk_poisson(oracle.calc_intensity(phi_hat), data.iobs[mine], data.mask)],
                        dtype=torch.float64)
     psi = oracle.ift(oracle.apply_amplitude(phi_hat, data.iobs[mine], data.mask))
-    sums = oracle.psi_to_obj_probe_sums(psi, obj, probe, data.positions[mine], obj.shape)
-    ao, ap = _pack(sums, s.Ho, s.Wo, s.K, s.N)
-    allreduce_accumulators(ao, ap, llk)
-    a = ao.numpy()
+    # probe sums of this rank's frames -> all-reduce -> probe update
+    n_p, d_p = oracle.psi_to_probe_sums(psi, obj, data.positions[mine])
+    _, ap = _pack((np.zeros(obj.shape, complex), np.zeros(obj.shape), n_p, d_p), s.Ho, s.Wo, s.K, s.N)
+    allreduce_accumulators(None, ap, llk)
     p = ap.numpy()
-    tot = (a[..., 0] + 1j * a[..., 1], a[..., 2], p[..., 0] + 1j * p[..., 1], p[0, ..., 2])
-    o1, p1 = oracle.normalise(obj, probe, tot)
+    p1 = oracle.inertia_update(probe, p[..., 0] + 1j * p[..., 1], p[0, ..., 2][None], 1e-2)
+    # object sums with the new probe -> all-reduce -> object update
+    n_o, d_o = oracle.psi_to_obj_sums(psi, p1, data.positions[mine], obj.shape)
+    ao, _ = _pack((n_o, d_o, np.zeros_like(probe), np.zeros(probe.shape[1:])), s.Ho, s.Wo, s.K, s.N)
+    allreduce_accumulators(ao, None)
+    a = ao.numpy()
+    o1 = oracle.inertia_update(obj, a[..., 0] + 1j * a[..., 1], a[..., 2], 1e-2)
     np.save(os.path.join(outdir, f"obj{rank}.npy"), o1)
     np.save(os.path.join(outdir, f"probe{rank}.npy"), p1)
     np.save(os.path.join(outdir, f"llk{rank}.npy"), llk.numpy())

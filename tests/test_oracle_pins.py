@@ -428,20 +428,16 @@ def test_planted_mistakes_are_caught(monkeypatch):
     break the pins above."""
     obj, probe, pos, data = _exact_problem(seed=13)
 
-    def bad_sums(psi, obj_, probe_, positions, shape_obj):
+    def bad_sums(psi, probe_, positions, shape_obj):
         K, N, _ = probe_.shape
         n_o = np.zeros(shape_obj, complex); d_o = np.zeros(shape_obj)
-        n_p = np.zeros((K, N, N), complex); d_p = np.zeros((N, N))
         for j, (r, c) in enumerate(positions):
-            patch = obj_[r:r + N, c:c + N]
             n_o[r:r + N, c:c + N] += (probe_ * psi[j]).sum(0)  # conjugate dropped
             d_o[r:r + N, c:c + N] += (np.abs(probe_) ** 2).sum(0)
-            n_p += np.conj(patch)[None] * psi[j]
-            d_p += np.abs(patch) ** 2
-        return n_o, d_o, n_p, d_p
+        return n_o, d_o
 
     with monkeypatch.context() as m:
-        m.setattr(orc, "psi_to_obj_probe_sums", bad_sums)
+        m.setattr(orc, "psi_to_obj_sums", bad_sums)
         o1, _, _ = orc.ap_cycle(obj, probe, data)
         assert rel(o1, obj) > 1e-3
 
@@ -470,3 +466,48 @@ def test_planted_mistakes_are_caught(monkeypatch):
             return new
         bad_psi = dm_bad(obj, probe, psi_pert, data)
         assert rel(bad_psi, good[2]) > 1e-2
+
+
+# ---------------------------------------------------------------- overlap update order
+
+def test_dm_stays_bounded_over_100_cycles():
+    """Psi2ObjProbe updates the probe from the current object, then the object from
+    the new probe: DM stays bounded on the 64x64 scan (100 cycles)."""
+    s = make_config("ap64")
+    data = orc.Data.make(s.iobs, s.positions, s.mask)
+    o, p, _ = orc.ap_cycle(s.obj0, s.probe0, data)
+    _, _, psi, _ = orc.cycles("DM", o, p, data, 100)
+    assert np.abs(psi).max() < 1e2
+
+
+def test_simultaneous_update_would_diverge_under_dm():
+    """Why the update alternates: with both factors updated from the same (O, P), a
+    scale error of Psi enters O and P alike, the product takes it twice, and DM
+    grows geometrically (the same 64x64 scan, 20 cycles)."""
+    s = make_config("ap64")
+    data = orc.Data.make(s.iobs, s.positions, s.mask)
+    o, p, _ = orc.ap_cycle(s.obj0, s.probe0, data)
+    psi = None
+    for c in range(20):
+        phi = orc.obj_probe_to_psi(o, p, data.positions)
+        if psi is None:
+            psi = phi.copy()
+        x_hat = orc.ft(2 * phi - psi)
+        psi = psi + orc.ift(orc.apply_amplitude(x_hat, data.iobs, data.mask)) - phi
+        o, p = orc.normalise(o, p, orc.psi_to_obj_probe_sums(psi, o, p, data.positions, o.shape))
+    assert np.abs(psi).max() > 1e4
+
+
+def test_overlap_update_is_probe_then_object():
+    rng = np.random.default_rng(15)
+    N = 16
+    obj = crandn(rng, 40, 40)
+    probe = crandn(rng, 2, N, N)
+    pos = rng.integers(0, 40 - N + 1, size=(7, 2))
+    psi = crandn(rng, 7, 2, N, N)
+    o1, p1 = orc.overlap_update(obj, probe, psi, pos)
+    n_p, d_p = orc.psi_to_probe_sums(psi, obj, pos)
+    p_exp = (n_p + 1e-2 * d_p.max() * probe) / (d_p + 1e-2 * d_p.max())[None]
+    n_o, d_o = orc.psi_to_obj_sums(psi, p_exp, pos, obj.shape)
+    o_exp = np.where(d_o + 1e-2 * d_o.max() > 0, (n_o + 1e-2 * d_o.max() * obj) / (d_o + 1e-2 * d_o.max()), obj)
+    assert rel(p1, p_exp) < 1e-14 and rel(o1, o_exp) < 1e-14
