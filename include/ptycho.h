@@ -76,8 +76,9 @@ typedef struct {
                                values are treated as 0 */
     const uint8_t* mask;    /* host uint8 [N][N], nonzero = bad pixel (left free by the projection,
                                excluded from the LLK and its gradient); NULL = no mask; copied */
-    void* psi;              /* device complex64 [J][K][N][N] exit-wave stack Psi, needed by DM
-                               (the Ptycho object's Psi array); may be NULL for AP, LLK and ML */
+    void* psi;              /* device complex64 [J][K][N][N] exit-wave stack Psi (the Ptycho
+                               object's Psi array), needed by the AP and DM cycles; may be NULL
+                               for LLK and ML */
 } ptx_problem;
 
 /* Device scratch needed by ptx_create for these problems, in bytes.  The caller
@@ -97,11 +98,14 @@ ptx_status ptx_create(ptx_handle** out, const ptx_problem* probs, int32_t nprob,
                       void* scratch, size_t scratch_bytes, void* stream);
 
 /* Alternating-projection cycles (the AP operator; Marchesini et al. 2013 as cited
- * in Section 4): per cycle, Phi = ObjProbe2Psi(O, P); Psi = IFT(ApplyAmplitude(FT(Phi)));
- * Psi2ObjProbe (numerators and denominators from the same O, P), then the
- * normalisation O <- (N_O + d_O O) / (D_O + d_O), d_O = alpha_obj max D_O, and the same
- * for P.  llk_dev: device double [ncycles * nprob]; entry [c * nprob + p] receives the
- * Poisson LLK (deviance form) of FT(Phi) in cycle c of problem p.  Psi is not stored. */
+ * in Section 4): per cycle, Phi = ObjProbe2Psi(O, P); Psi = IFT(ApplyAmplitude(FT(Phi)))
+ * stored in probs[p].psi; then Psi2ObjProbe: the probe first,
+ * P <- (N_P + d_P P) / (D_P + d_P), N_P = sum_j conj(O(r_j + x)) Psi_j(x),
+ * D_P = sum_j |O(r_j + x)|^2, d_P = alpha_probe max D_P; then the object from the new
+ * probe, O <- (N_O + d_O O) / (D_O + d_O), N_O = sum_j conj(P(x)) Psi_j(x) and
+ * D_O = sum_j |P(x)|^2 at r = r_j + x, d_O = alpha_obj max D_O.  llk_dev: device double
+ * [ncycles * nprob]; entry [c * nprob + p] receives the Poisson LLK (deviance form)
+ * of FT(Phi) in cycle c of problem p.  Needs probs[p].psi. */
 ptx_status ptx_ap_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, double* llk_dev, void* stream);
 
 /* Difference-map cycles (the DM operator, beta = 1; Elser 2007 as cited in
@@ -127,9 +131,17 @@ ptx_status ptx_llk(ptx_handle* h, double* llk_dev, void* stream);
  * llk_dev (may be NULL) receives the LLK.  Psi is recomputed, never stored. */
 ptx_status ptx_ml_grad(ptx_handle* h, void* grad_obj, void* grad_probe, double* llk_dev, void* stream);
 
-/* Normalise O and P from the accumulated numerators / denominators and clear
- * them (the second half of Psi2ObjProbe); used after cycles run with
- * PTX_NO_NORMALISE once the accumulators of several GPUs have been summed. */
+/* Stages of the second half of Psi2ObjProbe, for ptx_normalise. */
+#define PTX_STAGE_PROBE         0x100u /* P <- (N_P + d_P P) / (D_P + d_P) from the probe accumulator, cleared */
+#define PTX_STAGE_OBJ_GATHER    0x200u /* object accumulator <- N_O, D_O of this handle's frames, from the
+                                          stored Psi' and the current probe */
+#define PTX_STAGE_OBJ_NORMALISE 0x400u /* O <- (N_O + d_O O) / (D_O + d_O) from the object accumulator, cleared */
+
+/* Run stages of the probe / object update after cycles run with PTX_NO_NORMALISE
+ * (data-parallel split: all-reduce the probe accumulator, then PTX_STAGE_PROBE |
+ * PTX_STAGE_OBJ_GATHER, all-reduce the object accumulator, then
+ * PTX_STAGE_OBJ_NORMALISE).  PTX_UPDATE_PROBE selects PTX_STAGE_PROBE and
+ * PTX_UPDATE_OBJ the two object stages. */
 ptx_status ptx_normalise(ptx_handle* h, uint32_t flags, void* stream);
 
 /* Device addresses of problem p's accumulators (for an all-reduce across GPUs):
@@ -151,11 +163,12 @@ ptx_status ptx_fft2(void* data, int32_t nframes, int32_t N, int32_t direction, v
 /* Kernel kinds reported by ptx_profile_read. */
 #define PTX_KERNEL_ROW_FWD   0 /* gather x probe, (2 Phi - Psi), forward row FFT */
 #define PTX_KERNEL_COL       1 /* column FFT, amplitude projection + LLK, inverse column FFT */
-#define PTX_KERNEL_ROW_BWD   2 /* inverse row FFT, Psi update, Psi2ObjProbe scatter */
+#define PTX_KERNEL_ROW_BWD   2 /* inverse row FFT, Psi update, probe numerator / denominator */
 #define PTX_KERNEL_DEN_MAX   3 /* max of the denominators */
 #define PTX_KERNEL_NORMALISE 4 /* normalisation of O and P */
 #define PTX_KERNEL_CYCLE_END 5 /* FP64 LLK reduction of the cycle */
-#define PTX_KERNEL_KINDS     6
+#define PTX_KERNEL_OBJ_GATHER 6 /* object numerator / denominator gathered per tile from Psi' */
+#define PTX_KERNEL_KINDS     7
 
 /* Per-kernel timing for measurement.  While enabled, the cycle calls launch
  * their kernels directly (no CUDA graph) and bracket every launch with CUDA

@@ -37,7 +37,10 @@ EXPORTS = (
     "ptx_normalise", "ptx_accumulators", "ptx_set_param", "ptx_fft2", "ptx_profile_enable", "ptx_profile_read",
     "ptx_last_error", "ptx_destroy",
 )
-KERNEL_KINDS = ("row_fwd", "col", "row_bwd", "den_max", "normalise", "cycle_end")
+KERNEL_KINDS = ("row_fwd", "col", "row_bwd", "den_max", "normalise", "cycle_end", "obj_gather")
+PTX_STAGE_PROBE = 0x100
+PTX_STAGE_OBJ_GATHER = 0x200
+PTX_STAGE_OBJ_NORMALISE = 0x400
 
 
 class PtychoError(RuntimeError):

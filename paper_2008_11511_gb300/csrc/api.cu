@@ -96,7 +96,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 constexpr size_t kSpecBudget = (size_t)64 << 20;
 
 struct Layout {
-    size_t pos, mask, acc_obj, acc_probe, llk_part, maxbits;
+    size_t pos, mask, acc_obj, acc_probe, llk_part, maxbits, tile_ids, tile_ptr, tile_frames;
     size_t end;
 };
 
@@ -106,9 +106,55 @@ struct ProbHost {
     int L1 = 1, C2 = 1, L3 = 1;
     int B = 1;   // frames per batch
     int G3 = 1;  // frame groups of row_bwd
+    // object tiles met by at least one frame, with their frames (CSR, ascending j)
+    std::vector<int> tile_ids, tile_ptr, tile_frames;
+    int ntx = 0;
     Layout lay{};
     ProbArgs args{};
+    TileLists tiles{};
 };
+
+// Per-tile frame lists of the object gather (host, from the positions).
+void build_tiles(ProbHost& h, const int32_t* positions) {
+    const ptx_problem& p = h.p;
+    const int T = kObjTile;
+    const int ntx = (p.Wo + T - 1) / T, nty = (p.Ho + T - 1) / T;
+    std::vector<int> count((size_t)ntx * nty, 0);
+    auto span = [&](int j, int& ty0, int& ty1, int& tx0, int& tx1) {
+        const int r = positions[2 * j], c = positions[2 * j + 1];
+        ty0 = r / T;
+        ty1 = (r + p.N - 1) / T;
+        tx0 = c / T;
+        tx1 = (c + p.N - 1) / T;
+    };
+    for (int j = 0; j < p.J; ++j) {
+        int ty0, ty1, tx0, tx1;
+        span(j, ty0, ty1, tx0, tx1);
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) count[(size_t)ty * ntx + tx]++;
+    }
+    std::vector<int> slot(count.size(), -1);
+    h.tile_ids.clear();
+    h.tile_ptr.assign(1, 0);
+    for (size_t t = 0; t < count.size(); ++t)
+        if (count[t]) {
+            slot[t] = (int)h.tile_ids.size();
+            h.tile_ids.push_back((int)t);
+            h.tile_ptr.push_back(h.tile_ptr.back() + count[t]);
+        }
+    h.tile_frames.assign(h.tile_ptr.back(), 0);
+    std::vector<int> fill(h.tile_ids.size(), 0);
+    for (int j = 0; j < p.J; ++j) {
+        int ty0, ty1, tx0, tx1;
+        span(j, ty0, ty1, tx0, tx1);
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) {
+                const int sidx = slot[(size_t)ty * ntx + tx];
+                h.tile_frames[h.tile_ptr[sidx] + fill[sidx]++] = j;
+            }
+    }
+    h.ntx = ntx;
+}
 
 int choose_lines(int N, int K, int maxl) {
     int L = 1;
@@ -146,9 +192,13 @@ void plan_problem(ProbHost& h) {
     const ptx_problem& p = h.p;
     h.ks = kernel_set(p.N);
     const int maxl = h.ks->max_lines;
-    h.L1 = choose_lines(p.N, p.K, maxl);
-    h.C2 = choose_lines(p.N, p.K, maxl);
-    h.L3 = choose_lines(p.N, p.K, maxl);
+    if (use_reg_kernels(h.ks, p.K)) {
+        h.L1 = h.C2 = h.L3 = h.ks->reg_lines;
+    } else {
+        h.L1 = choose_lines(p.N, p.K, maxl);
+        h.C2 = choose_lines(p.N, p.K, maxl);
+        h.L3 = choose_lines(p.N, p.K, maxl);
+    }
     const size_t frame_bytes = (size_t)p.K * p.N * p.N * sizeof(float2);
     size_t B = kSpecBudget / frame_bytes;
     if (B < 1) B = 1;
@@ -178,6 +228,12 @@ size_t layout_problem(ProbHost& h) {
     o = align_up(o + sizeof(double) * (size_t)p.J * (p.N / h.C2));
     h.lay.maxbits = o;
     o = align_up(o + 2 * sizeof(unsigned));
+    h.lay.tile_ids = o;
+    o = align_up(o + sizeof(int) * h.tile_ids.size());
+    h.lay.tile_ptr = o;
+    o = align_up(o + sizeof(int) * h.tile_ptr.size());
+    h.lay.tile_frames = o;
+    o = align_up(o + sizeof(int) * h.tile_frames.size());
     h.lay.end = o;
     return o;
 }
@@ -221,6 +277,9 @@ ptx_status compute_layout(std::vector<ProbHost>& probs, size_t* spec_off, size_t
         h.lay.acc_probe += o;
         h.lay.llk_part += o;
         h.lay.maxbits += o;
+        h.lay.tile_ids += o;
+        h.lay.tile_ptr += o;
+        h.lay.tile_frames += o;
         h.lay.end += o;
         o += sz;
         size_t s = (size_t)h.B * h.p.K * h.p.N * h.p.N * sizeof(float2);
@@ -258,7 +317,16 @@ void fill_args(ptx_handle* h, ProbHost& ph) {
     a.L1 = ph.L1;
     a.C2 = ph.C2;
     a.L3 = ph.L3;
+    ph.tiles.tile_ids = (const int*)(h->scratch + ph.lay.tile_ids);
+    ph.tiles.tile_ptr = (const int*)(h->scratch + ph.lay.tile_ptr);
+    ph.tiles.tile_frames = (const int*)(h->scratch + ph.lay.tile_frames);
+    ph.tiles.ntx = ph.ntx;
 }
+
+// Second half of Psi2ObjProbe, in stages: probe normalisation from its
+// accumulators; object numerator / denominator gathered from Psi' with the
+// current (new) probe; object normalisation.
+enum Stage { STAGE_PROBE = 0x100, STAGE_OBJ_GATHER = 0x200, STAGE_OBJ_NORMALISE = 0x400 };
 
 enum Algo { ALGO_AP = 0, ALGO_DM = 1 };
 
@@ -288,6 +356,30 @@ struct ProfScope {
     }
 };
 
+void enqueue_stages(ptx_handle* h, ProbHost& ph, int stages, cudaStream_t s) {
+    const ProbArgs& a = ph.args;
+    if (stages & STAGE_PROBE) {
+        {
+            ProfScope ps(h, PTX_KERNEL_DEN_MAX, s);
+            k_den_max<<<2 * 152, 256, 0, s>>>(a, 0, 1);
+        }
+        ProfScope ps(h, PTX_KERNEL_NORMALISE, s);
+        k_normalise<<<4 * 152, 256, 0, s>>>(a, (float)h->alpha_obj, (float)h->alpha_probe, 0, 1);
+    }
+    if ((stages & STAGE_OBJ_GATHER) && !ph.tile_ids.empty()) {
+        ProfScope ps(h, PTX_KERNEL_OBJ_GATHER, s);
+        k_obj_gather<<<(unsigned)ph.tile_ids.size(), 256, 0, s>>>(a, ph.tiles);
+    }
+    if (stages & STAGE_OBJ_NORMALISE) {
+        {
+            ProfScope ps(h, PTX_KERNEL_DEN_MAX, s);
+            k_den_max<<<2 * 152, 256, 0, s>>>(a, 1, 0);
+        }
+        ProfScope ps(h, PTX_KERNEL_NORMALISE, s);
+        k_normalise<<<4 * 152, 256, 0, s>>>(a, (float)h->alpha_obj, (float)h->alpha_probe, 1, 0);
+    }
+}
+
 // One cycle of every problem, enqueued on `s`.
 ptx_status enqueue_cycle(ptx_handle* h, int algo, uint32_t flags, cudaStream_t s) {
     const bool upd_o = flags & PTX_UPDATE_OBJ;
@@ -313,17 +405,11 @@ ptx_status enqueue_cycle(ptx_handle* h, int algo, uint32_t flags, cudaStream_t s
             }
             {
                 ProfScope ps(h, PTX_KERNEL_ROW_BWD, s);
-                ks->row_bwd(a, j0, nb, G, bwd_mode, upd_o, upd_p, s);
+                ks->row_bwd(a, j0, nb, G, bwd_mode, 0, upd_p, s);
             }
         }
-        if (!(flags & PTX_NO_NORMALISE) && (upd_o || upd_p)) {
-            {
-                ProfScope ps(h, PTX_KERNEL_DEN_MAX, s);
-                k_den_max<<<2 * 152, 256, 0, s>>>(a, upd_o, upd_p);
-            }
-            ProfScope ps(h, PTX_KERNEL_NORMALISE, s);
-            k_normalise<<<4 * 152, 256, 0, s>>>(a, (float)h->alpha_obj, (float)h->alpha_probe, upd_o, upd_p);
-        }
+        if (!(flags & PTX_NO_NORMALISE))
+            enqueue_stages(h, ph, (upd_p ? STAGE_PROBE : 0) | (upd_o ? STAGE_OBJ_GATHER | STAGE_OBJ_NORMALISE : 0), s);
         ProfScope ps(h, PTX_KERNEL_CYCLE_END, s);
         k_cycle_end<<<1, 1024, 0, s>>>(h->ctl, a, pi, a.N / a.C2, pi == np - 1);
     }
@@ -384,10 +470,9 @@ ptx_status run_cycles(ptx_handle* h, int algo, int ncycles, uint32_t flags, doub
     if (flags & ~known) return fail(PTX_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags & ~known);
     if (algo == ALGO_AP && (flags & PTX_DM_INIT_PSI))
         return fail(PTX_ERR_INVALID_ARG, "PTX_DM_INIT_PSI is a DM flag");
-    if (algo == ALGO_DM)
-        for (size_t i = 0; i < h->probs.size(); ++i)
-            if (!h->probs[i].p.psi)
-                return fail(PTX_ERR_INVALID_ARG, "problem %zu: DM needs the psi array", i);
+    for (size_t i = 0; i < h->probs.size(); ++i)
+        if (!h->probs[i].p.psi)
+            return fail(PTX_ERR_INVALID_ARG, "problem %zu: AP and DM cycles need the psi array", i);
     ptx_status st = check_device(h);
     if (st != PTX_OK) return st;
     if (ncycles == 0) return PTX_OK;
@@ -423,6 +508,7 @@ ptx_status ptx_workspace_bytes(const ptx_problem* probs, int32_t nprob, size_t* 
         ptx_status st = check_problem(probs[i], i);
         if (st != PTX_OK) return st;
         v[i].p = probs[i];
+        build_tiles(v[i], probs[i].positions);
     }
     size_t so, co, tot;
     compute_layout(v, &so, &co, &tot);
@@ -442,6 +528,7 @@ ptx_status ptx_create(ptx_handle** out, const ptx_problem* probs, int32_t nprob,
         ptx_status st = check_problem(probs[i], i);
         if (st != PTX_OK) return st;
         v[i].p = probs[i];
+        build_tiles(v[i], probs[i].positions);
     }
     size_t spec_off, ctl_off, total;
     compute_layout(v, &spec_off, &ctl_off, &total);
@@ -470,6 +557,13 @@ ptx_status ptx_create(ptx_handle** out, const ptx_problem* probs, int32_t nprob,
             e = cudaMemcpyAsync(h->scratch + ph.lay.mask, ph.p.mask, (size_t)ph.p.N * ph.p.N, cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess) break;
         }
+        const std::vector<int>* lists[3] = {&ph.tile_ids, &ph.tile_ptr, &ph.tile_frames};
+        const size_t offs[3] = {ph.lay.tile_ids, ph.lay.tile_ptr, ph.lay.tile_frames};
+        for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+            if (!lists[q]->empty())
+                e = cudaMemcpyAsync(h->scratch + offs[q], lists[q]->data(), sizeof(int) * lists[q]->size(),
+                                    cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) break;
         ph.p.positions = nullptr;  // borrowed host arrays are not kept
         ph.p.mask = nullptr;
         fill_args(h, ph);
@@ -539,14 +633,17 @@ ptx_status ptx_ml_grad(ptx_handle* h, void* grad_obj, void* grad_probe, double* 
 
 ptx_status ptx_normalise(ptx_handle* h, uint32_t flags, void* stream) {
     if (!h) return fail(PTX_ERR_INVALID_ARG, "null handle");
-    if (flags & ~(PTX_UPDATE_OBJ | PTX_UPDATE_PROBE)) return fail(PTX_ERR_INVALID_ARG, "flags: only update bits");
+    const uint32_t known = PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_STAGE_PROBE | PTX_STAGE_OBJ_GATHER |
+                           PTX_STAGE_OBJ_NORMALISE;
+    if (flags & ~known) return fail(PTX_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags & ~known);
     ptx_status st = check_device(h);
     if (st != PTX_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const int uo = (flags & PTX_UPDATE_OBJ) != 0, up = (flags & PTX_UPDATE_PROBE) != 0;
+    int stages = (int)(flags & (PTX_STAGE_PROBE | PTX_STAGE_OBJ_GATHER | PTX_STAGE_OBJ_NORMALISE));
+    if (flags & PTX_UPDATE_PROBE) stages |= STAGE_PROBE;
+    if (flags & PTX_UPDATE_OBJ) stages |= STAGE_OBJ_GATHER | STAGE_OBJ_NORMALISE;
     for (auto& ph : h->probs) {
-        k_den_max<<<2 * 152, 256, 0, s>>>(ph.args, uo, up);
-        k_normalise<<<4 * 152, 256, 0, s>>>(ph.args, (float)h->alpha_obj, (float)h->alpha_probe, uo, up);
+        enqueue_stages(h, ph, stages, s);
         cudaError_t e = cudaMemsetAsync(ph.args.maxbits, 0, 2 * sizeof(unsigned), s);
         if (e != cudaSuccess) return cuda_fail(e, "ptx_normalise memset");
     }

@@ -12,6 +12,58 @@ __device__ __forceinline__ float warp_max(float v) {
 
 // max D_O and max D_P over the accumulators (both >= 0, so their bit patterns
 // order like unsigned integers).
+// Object numerator and denominator gathered per object tile from the stored
+// exit waves and the (already updated) probe:
+//   N_O(r) = sum_j sum_k conj(P_k(r - r_j)) Psi'_jk(r - r_j),  D_O(r) = sum_j sum_k |P_k(r - r_j)|^2
+// over the frames whose patch contains r, in ascending j.  Each pixel is
+// owned by one thread, so the accumulator is written without atomics.
+__global__ void __launch_bounds__(256) k_obj_gather(ProbArgs a, TileLists tl) {
+    constexpr int T = kObjTile;
+    constexpr int Q = T * T / 256;  // pixels per thread (rows lane-major)
+    const int t = blockIdx.x;
+    const int tid = tl.tile_ids[t];
+    const int ty = tid / tl.ntx, tx = tid - ty * tl.ntx;
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int x = tx * T + lane;
+    const int N = a.N, K = a.K;
+    float2 n[Q];
+    float d[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        n[q] = make_float2(0.f, 0.f);
+        d[q] = 0.f;
+    }
+    const int f0 = tl.tile_ptr[t], f1 = tl.tile_ptr[t + 1];
+    for (int f = f0; f < f1; ++f) {
+        const int j = tl.tile_frames[f];
+        const int2 p = a.pos[j];
+        const int px = x - p.y;
+        if (px < 0 || px >= N) continue;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int y = ty * T + wy + 8 * q;
+            const int py = y - p.x;
+            if (py >= 0 && py < N) {
+                for (int k = 0; k < K; ++k) {
+                    const float2 pr = __ldg(a.probe + ((size_t)k * N + py) * N + px);
+                    const float2 ps = __ldcs(a.psi + (((size_t)j * K + k) * N + py) * N + px);
+                    const float2 c = cconjmul(pr, ps);
+                    n[q].x += c.x;
+                    n[q].y += c.y;
+                    d[q] = fmaf(pr.x, pr.x, fmaf(pr.y, pr.y, d[q]));
+                }
+            }
+        }
+    }
+    if (x < a.Wo) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int y = ty * T + wy + 8 * q;
+            if (y < a.Ho) a.acc_obj[(size_t)y * a.Wo + x] = make_float4(n[q].x, n[q].y, d[q], 0.f);
+        }
+    }
+}
+
 __global__ void k_den_max(ProbArgs a, int upd_obj, int upd_probe) {
     float mo = 0.f, mp = 0.f;
     const size_t stride = (size_t)gridDim.x * blockDim.x;

@@ -240,8 +240,9 @@ __global__ void __launch_bounds__(kThreads) k_col(ProbArgs a, int j0, int mode) 
 
 // ---------------------------------------------------------------------------
 // row_bwd: grid (N / L3, G); block handles rows [y0, y0 + L3) of frames
-// b = blockIdx.y, blockIdx.y + G, ... of the batch, keeping its share of the
-// probe numerator / denominator in shared memory across those frames.
+// b = blockIdx.y, blockIdx.y + G, ... of the batch: inverse row FFT, Psi' =
+// Phi + D stored, its share of the probe numerator / denominator kept in
+// shared memory across those frames (gradient mode: G_O scattered, G_P reduced).
 // ---------------------------------------------------------------------------
 template <int N>
 __global__ void __launch_bounds__(kThreads) k_row_bwd(ProbArgs a, int j0, int nb, int mode, int upd_obj,
@@ -279,22 +280,20 @@ __global__ void __launch_bounds__(kThreads) k_row_bwd(ProbArgs a, int j0, int nb
             const size_t oidx = (size_t)(p.x + y) * a.Wo + (p.y + x);
             const float2 ob = a.obj[oidx];
             float2 no = make_float2(0.f, 0.f);
-            float dn = 0.f;
             for (int k = 0; k < K; ++k) {
                 const float2 d = buf[(k * L + r) * P + x];
                 const float2 pr = a.probe[((size_t)k * N + y) * N + x];
                 float2 w;
                 if (mode == BWD_GRAD) {
                     w = d;
+                    if (acc_o) {
+                        const float2 t = cconjmul(pr, w);
+                        no.x += t.x;
+                        no.y += t.y;
+                    }
                 } else {
                     w = cadd(cmul(pr, ob), d);
-                    if (mode == BWD_DM) a.psi[(((size_t)j * K + k) * N + y) * N + x] = w;
-                }
-                if (acc_o) {
-                    const float2 t = cconjmul(pr, w);
-                    no.x += t.x;
-                    no.y += t.y;
-                    dn = fmaf(pr.x, pr.x, fmaf(pr.y, pr.y, dn));
+                    a.psi[(((size_t)j * K + k) * N + y) * N + x] = w;
                 }
                 if (acc_p) {
                     const float2 t = cconjmul(ob, w);
@@ -304,12 +303,7 @@ __global__ void __launch_bounds__(kThreads) k_row_bwd(ProbArgs a, int j0, int nb
                 }
             }
             if (acc_p) dp_s[r * N + x] += cnorm(ob);
-            if (acc_o) {
-                if (mode == BWD_GRAD)
-                    red_add_v2(a.grad_obj + oidx, no.x, no.y);
-                else
-                    red_add_v4(a.acc_obj + oidx, no.x, no.y, dn, 0.f);
-            }
+            if (acc_o && mode == BWD_GRAD) red_add_v2(a.grad_obj + oidx, no.x, no.y);
         }
         __syncthreads();
     }
@@ -331,6 +325,15 @@ __global__ void __launch_bounds__(kThreads) k_row_bwd(ProbArgs a, int j0, int nb
 // ---------------------------------------------------------------------------
 // Normalisation (Psi2ObjProbe second half) and reductions.
 // ---------------------------------------------------------------------------
+// Object tiles of the gather: kObjTile x kObjTile pixels, one block each.
+constexpr int kObjTile = 32;
+struct TileLists {
+    const int* tile_ids;     // [ntiles] tile index ty * ntx + tx of each active tile
+    const int* tile_ptr;     // [ntiles + 1] CSR offsets into tile_frames
+    const int* tile_frames;  // frames j whose patch meets the tile, ascending
+    int ntx;                 // tiles per object row
+};
+__global__ void k_obj_gather(ProbArgs a, TileLists tl);
 __global__ void k_den_max(ProbArgs a, int upd_obj, int upd_probe);
 __global__ void k_normalise(ProbArgs a, float alpha_obj, float alpha_probe, int upd_obj, int upd_probe);
 __global__ void k_llk_reduce(ProbArgs a, int nparts_per_frame, double* out);
@@ -375,22 +378,23 @@ __global__ void __launch_bounds__(kThreads) k_fft_cols(float2* data, int C) {
     }
 }
 
-// Launch table for one frame size.
+// Launch table for one frame size.  The row_fwd / col / row_bwd entries pick
+// the register-resident kernels (kernels_reg.cuh) for one probe mode and
+// two-pass sizes, and the shared-memory kernels above otherwise.
 struct KernelSet {
     int N;
     void (*row_fwd)(const ProbArgs&, int j0, int nb, int mode, cudaStream_t);
     void (*col)(const ProbArgs&, int j0, int nb, int mode, cudaStream_t);
     void (*row_bwd)(const ProbArgs&, int j0, int nb, int G, int mode, int upd_obj, int upd_probe, cudaStream_t);
     void (*fft2)(float2* data, int nframes, int dir, cudaStream_t);
-    size_t (*smem_row_fwd)(int K, int L);
-    size_t (*smem_col)(int K, int C);
-    size_t (*smem_row_bwd)(int K, int L);
-    int max_lines;
+    int max_lines;  // lines per block of the shared-memory kernels
+    int reg_lines;  // lines per block of the register kernels (0: none for this N)
     int R, M;
 };
 
 const KernelSet* kernel_set(int N);
-cudaError_t set_kernel_attributes();
+// Whether the register-resident kernels serve a problem with K modes.
+inline bool use_reg_kernels(const KernelSet* ks, int K) { return K == 1 && ks->reg_lines > 0; }
 
 template <int N>
 size_t smem_row_fwd_t(int K, int L) { return sizeof(float2) * (N + (size_t)K * L * line_pitch<N>()); }
@@ -401,18 +405,46 @@ size_t smem_row_bwd_t(int K, int L) {
     return sizeof(float2) * (N + (size_t)K * L * line_pitch<N>() + (size_t)K * L * N) + sizeof(float) * (size_t)L * N;
 }
 
+}  // namespace ptx
+#include "kernels_reg.cuh"
+namespace ptx {
+
+template <int N>
+constexpr bool has_reg() { return Plan<N>::M > 1; }
+
 template <int N>
 void launch_row_fwd(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s) {
+    if constexpr (has_reg<N>()) {
+        if (a.K == 1) {
+            dim3 grid(N / RegShape<N>::L, nb);
+            k_row_fwd_r<N><<<grid, kThreads, smem_row_fwd_r<N>(), s>>>(a, j0, mode);
+            return;
+        }
+    }
     dim3 grid(N / a.L1, nb);
     k_row_fwd<N><<<grid, kThreads, smem_row_fwd_t<N>(a.K, a.L1), s>>>(a, j0, mode);
 }
 template <int N>
 void launch_col(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s) {
+    if constexpr (has_reg<N>()) {
+        if (a.K == 1) {
+            dim3 grid(N / RegShape<N>::L, nb);
+            k_col_r<N><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, mode);
+            return;
+        }
+    }
     dim3 grid(N / a.C2, nb);
     k_col<N><<<grid, kThreads, smem_col_t<N>(a.K, a.C2), s>>>(a, j0, mode);
 }
 template <int N>
 void launch_row_bwd(const ProbArgs& a, int j0, int nb, int G, int mode, int upd_obj, int upd_probe, cudaStream_t s) {
+    if constexpr (has_reg<N>()) {
+        if (a.K == 1) {
+            dim3 grid(N / RegShape<N>::L, G);
+            k_row_bwd_r<N><<<grid, kThreads, smem_row_bwd_r<N>(), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
+            return;
+        }
+    }
     dim3 grid(N / a.L3, G);
     k_row_bwd<N><<<grid, kThreads, smem_row_bwd_t<N>(a.K, a.L3), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
 }
@@ -443,20 +475,22 @@ cudaError_t set_attrs_t() {
     if ((e = cudaFuncSetAttribute(k_fft_rows<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_fft_cols<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_fft_cols<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if constexpr (has_reg<N>()) {
+        if ((e = set_attrs_r<N>())) return e;
+    }
     return cudaSuccess;
 }
 
 template <int N>
 const KernelSet* make_kernel_set() {
+    constexpr int rl = has_reg<N>() ? reg_lines<N>() : 0;
     static const KernelSet ks = {N,
                                  &launch_row_fwd<N>,
                                  &launch_col<N>,
                                  &launch_row_bwd<N>,
                                  &launch_fft2<N>,
-                                 &smem_row_fwd_t<N>,
-                                 &smem_col_t<N>,
-                                 &smem_row_bwd_t<N>,
                                  max_lines<N>(),
+                                 rl,
                                  Plan<N>::R,
                                  Plan<N>::M};
     return &ks;

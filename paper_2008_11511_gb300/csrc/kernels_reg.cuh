@@ -1,0 +1,387 @@
+// Register-resident passes of the cycle for one probe mode (K = 1).
+//
+// Each line transform N = R * M keeps its data in registers from the global
+// load to the global store with a single padded shared-memory transpose:
+//
+//   thread (line, n1) loads x[n1 + M n2] (n2 < R) straight from global memory,
+//   runs an R-point codelet, multiplies by w_N^(n1 k2), writes y[k2 (M+1) + n1];
+//   thread (line, k2) reads y[k2 (M+1) + n1] (n1 < M), runs an M-point codelet
+//   and holds X[k2 + R k1] (k1 < M) in registers.
+//
+// The column pass continues in registers: projection and LLK on X, then the
+// inverse transform with the roles of R and M swapped (an M-point codelet on
+// the values the thread already holds, twiddle, transpose, R-point codelet),
+// so that a column makes two shared-memory round trips in total.
+#pragma once
+#include "kernels.cuh"
+
+namespace ptx {
+
+// Lines per block of the register-resident kernels (rows of a frame for the
+// row passes, columns for the column pass).
+template <int N>
+__host__ __device__ constexpr int reg_lines() {
+    return N >= 512 ? 8 : (N == 384 ? 8 : (N == 192 ? 16 : (4096 / N > N ? N : 4096 / N)));
+}
+// Shared-memory pitch of a line: room for both padded intermediate layouts
+// (R (M+1) and M (R+1) elements), odd.
+template <int N>
+__host__ __device__ constexpr int reg_pitch() {
+    return Plan<N>::M == 1 ? N + 1 : N + (Plan<N>::R > Plan<N>::M ? Plan<N>::R : Plan<N>::M) + 1;
+}
+
+template <int N>
+struct RegShape {
+    static constexpr int R = Plan<N>::R, M = Plan<N>::M, L = reg_lines<N>(), P = reg_pitch<N>();
+    static constexpr int I1 = (L * M + kThreads - 1) / kThreads;  // pass-1 items per thread
+    static constexpr int I2 = (L * R + kThreads - 1) / kThreads;  // pass-2 items per thread
+    static_assert(M > 1, "register kernels need two passes");
+    static_assert(N % L == 0, "lines per block must divide N");
+};
+
+// twiddle w_N^(DIR a b), a < R, b < M, from the block's table tw[a * M + b] = w_N^(-a b)
+template <int N, int DIR>
+__device__ __forceinline__ float2 tw_get(const float2* tw, int a, int b) {
+    float2 t = tw[a * Plan<N>::M + b];
+    if (DIR > 0) t.y = -t.y;
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// Row forward: Phi = P O[r_j], X = Phi or 2 Phi - Psi, row FFT -> spec.
+// grid (N / L, frames in batch)
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_row_fwd_r(ProbArgs a, int j0, int mode) {
+    using S = RegShape<N>;
+    constexpr int R = S::R, M = S::M, L = S::L, P = S::P;
+    extern __shared__ __align__(16) float2 sm[];
+    float2* tw = sm;
+    float2* buf = sm + N;
+    load_twiddles<N>(tw);
+    const int y0 = blockIdx.x * L;
+    const int b = blockIdx.y;
+    const int j = j0 + b;
+    const int2 p = a.pos[j];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < S::I1; ++i) {
+        const int w = threadIdx.x + i * kThreads;
+        if (w < L * M) {
+            const int line = w / M, n1 = w - line * M;
+            const int y = y0 + line;
+            const float2* pr = a.probe + (size_t)y * N + n1;
+            const float2* ob = a.obj + (size_t)(p.x + y) * a.Wo + p.y + n1;
+            float2 v[R];
+#pragma unroll
+            for (int n2 = 0; n2 < R; ++n2) v[n2] = cmul(__ldg(pr + M * n2), ob[M * n2]);
+            if (mode == X_DM) {
+                const float2* ps = a.psi + ((size_t)j * N + y) * N + n1;
+#pragma unroll
+                for (int n2 = 0; n2 < R; ++n2) {
+                    const float2 q = __ldcs(ps + M * n2);
+                    v[n2] = make_float2(2.f * v[n2].x - q.x, 2.f * v[n2].y - q.y);
+                }
+            }
+            Dft<R, -1>::run(v);
+            float2* o = buf + line * P + n1;
+            o[0] = v[0];
+#pragma unroll
+            for (int k2 = 1; k2 < R; ++k2) o[k2 * (M + 1)] = cmul(v[k2], tw_get<N, -1>(tw, k2, n1));
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < S::I2; ++i) {
+        const int w = threadIdx.x + i * kThreads;
+        if (w < L * R) {
+            const int line = w / R, k2 = w - line * R;
+            float2 u[M];
+            const float2* src = buf + line * P + k2 * (M + 1);
+#pragma unroll
+            for (int n1 = 0; n1 < M; ++n1) u[n1] = src[n1];
+            Dft<M, -1>::run(u);
+            float2* dst = a.spec + ((size_t)b * N + y0 + line) * N + k2;
+#pragma unroll
+            for (int k1 = 0; k1 < M; ++k1) dst[R * k1] = u[k1];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass: column FFT, projection + LLK, inverse column FFT.
+// grid (N / L, frames in batch); block handles columns [x0, x0 + L).
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_col_r(ProbArgs a, int j0, int mode) {
+    using S = RegShape<N>;
+    constexpr int R = S::R, M = S::M, C = S::L, P = S::P;
+    constexpr int I1b = (C * M + kThreads - 1) / kThreads;  // inverse pass-2 items (M per column)
+    extern __shared__ __align__(16) float2 sm[];
+    __shared__ double red_s[kThreads / 32];
+    float2* tw = sm;
+    float2* buf = sm + N;
+    load_twiddles<N>(tw);
+    const int x0 = blockIdx.x * C;
+    const int b = blockIdx.y;
+    const int j = j0 + b;
+    float2* spec = a.spec + (size_t)b * N * N + x0;
+    __syncthreads();
+    // forward pass 1: thread (c, n1) holds rows n1 + M n2 of column c
+#pragma unroll
+    for (int i = 0; i < S::I1; ++i) {
+        const int w = threadIdx.x + i * kThreads;
+        if (w < C * M) {
+            const int n1 = w / C, c = w - n1 * C;
+            float2 v[R];
+#pragma unroll
+            for (int n2 = 0; n2 < R; ++n2) v[n2] = spec[(size_t)(n1 + M * n2) * N + c];
+            Dft<R, -1>::run(v);
+            float2* o = buf + c * P + n1;
+            o[0] = v[0];
+#pragma unroll
+            for (int k2 = 1; k2 < R; ++k2) o[k2 * (M + 1)] = cmul(v[k2], tw_get<N, -1>(tw, k2, n1));
+        }
+    }
+    __syncthreads();
+    // forward pass 2 into registers: thread (c, k2) holds X^[k2 + R k1]
+    float2 u[S::I2][M];
+#pragma unroll
+    for (int i = 0; i < S::I2; ++i) {
+        const int w = threadIdx.x + i * kThreads;
+        if (w < C * R) {
+            const int k2 = w / C, c = w - k2 * C;
+            const float2* src = buf + c * P + k2 * (M + 1);
+#pragma unroll
+            for (int n1 = 0; n1 < M; ++n1) u[i][n1] = src[n1];
+        }
+    }
+    __syncthreads();
+    constexpr float invN2 = 1.0f / float(N * N);
+    KahanF llk;
+    const float* io_b = a.iobs + (size_t)j * N * N + x0;
+    const uint8_t* mk_b = a.mask + x0;
+#pragma unroll
+    for (int i = 0; i < S::I2; ++i) {
+        const int w = threadIdx.x + i * kThreads;
+        if (w < C * R) {
+            const int k2 = w / C, c = w - k2 * C;
+            Dft<M, -1>::run(u[i]);
+#pragma unroll
+            for (int k1 = 0; k1 < M; ++k1) {
+                const int row = k2 + R * k1;
+                const float ic = cnorm(u[i][k1]) * invN2;
+                const float io = __ldcs(io_b + (size_t)row * N + c);
+                const bool masked = __ldg(mk_b + row * N + c) != 0;
+                if (!masked) llk.add(llk_term(ic, io));
+                float f;
+                if (masked) {
+                    f = 0.f;
+                } else if (mode == COL_PROJECT) {
+                    f = (sqrtf(fmaxf(io, 0.f)) / fmaxf(sqrtf(ic), 1e-20f) - 1.0f) * invN2;
+                } else {
+                    f = 2.0f * (1.0f - fmaxf(io, 0.f) / fmaxf(ic, 1e-30f)) * invN2;
+                }
+                u[i][k1] = cscale(u[i][k1], f);
+            }
+            if (mode != COL_LLK) {
+                // inverse pass 1: M-point codelet over k1, twiddle w_N^(+k2 k2'),
+                // y'[k2' (R+1) + k2]
+                Dft<M, +1>::run(u[i]);
+                float2* o = buf + c * P + k2;
+                o[0] = u[i][0];
+#pragma unroll
+                for (int kk = 1; kk < M; ++kk) o[kk * (R + 1)] = cmul(u[i][kk], tw_get<N, +1>(tw, k2, kk));
+            }
+        }
+    }
+    double tot = block_sum_double<kThreads>(llk.value(), red_s);
+    if (threadIdx.x == 0) a.llk_part[(size_t)j * gridDim.x + blockIdx.x] = tot;
+    if (mode == COL_LLK) return;
+    __syncthreads();
+    // inverse pass 2: thread (c, k2') reads y'[k2' (R+1) + n1'], R-point codelet,
+    // rows k2' + M k1'
+#pragma unroll
+    for (int i = 0; i < I1b; ++i) {
+        const int w = threadIdx.x + i * kThreads;
+        if (w < C * M) {
+            const int kk = w / C, c = w - kk * C;
+            float2 v[R];
+            const float2* src = buf + c * P + kk * (R + 1);
+#pragma unroll
+            for (int n = 0; n < R; ++n) v[n] = src[n];
+            Dft<R, +1>::run(v);
+#pragma unroll
+            for (int k1 = 0; k1 < R; ++k1) spec[(size_t)(kk + M * k1) * N + c] = v[k1];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row backward: inverse row FFT -> D; Psi' = Phi + D stored to the exit-wave
+// stack (AP and DM), probe numerator/denominator in registers across the
+// block's frames, flushed once.  In gradient mode D is the back-propagated
+// weighted wave: G_O is scattered with red.v2, G_P reduced like N_P.
+// grid (N / L, G); block handles rows [y0, y0 + L) of frames blockIdx.y + G t.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_row_bwd_r(ProbArgs a, int j0, int nb, int mode, int upd_obj,
+                                                        int upd_probe) {
+    using S = RegShape<N>;
+    constexpr int R = S::R, M = S::M, L = S::L, P = S::P;
+    constexpr bool kRegAcc = S::I2 * M <= 16;  // probe accumulators in registers, else shared memory
+    constexpr int IA = kRegAcc ? S::I2 : 1, MA = kRegAcc ? M : 1;
+    extern __shared__ __align__(16) float2 sm[];
+    float2* tw = sm;
+    float2* buf = sm + N;
+    float2* np_s = buf + L * P;                 // [L][N] when !kRegAcc
+    float* dp_s = (float*)(np_s + L * N);       // [L][N]
+    load_twiddles<N>(tw);
+    const int y0 = blockIdx.x * L;
+    const bool acc_o = upd_obj != 0, acc_p = upd_probe != 0;
+    float2 np_r[IA][MA];
+    float dp_r[IA][MA];
+#pragma unroll
+    for (int i = 0; i < IA; ++i)
+#pragma unroll
+        for (int k1 = 0; k1 < MA; ++k1) {
+            np_r[i][k1] = make_float2(0.f, 0.f);
+            dp_r[i][k1] = 0.f;
+        }
+    if (!kRegAcc && acc_p) {
+        for (int e = threadIdx.x; e < L * N; e += kThreads) {
+            np_s[e] = make_float2(0.f, 0.f);
+            dp_s[e] = 0.f;
+        }
+    }
+    __syncthreads();
+    for (int b = blockIdx.y; b < nb; b += gridDim.y) {
+        const int j = j0 + b;
+        const int2 p = a.pos[j];
+#pragma unroll
+        for (int i = 0; i < S::I1; ++i) {
+            const int w = threadIdx.x + i * kThreads;
+            if (w < L * M) {
+                const int line = w / M, n1 = w - line * M;
+                const float2* src = a.spec + ((size_t)b * N + y0 + line) * N + n1;
+                float2 v[R];
+#pragma unroll
+                for (int n2 = 0; n2 < R; ++n2) v[n2] = src[M * n2];
+                Dft<R, +1>::run(v);
+                float2* o = buf + line * P + n1;
+                o[0] = v[0];
+#pragma unroll
+                for (int k2 = 1; k2 < R; ++k2) o[k2 * (M + 1)] = cmul(v[k2], tw_get<N, +1>(tw, k2, n1));
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < S::I2; ++i) {
+            const int w = threadIdx.x + i * kThreads;
+            if (w < L * R) {
+                const int line = w / R, k2 = w - line * R;
+                const int y = y0 + line;
+                float2 u[M];
+                const float2* src = buf + line * P + k2 * (M + 1);
+#pragma unroll
+                for (int n1 = 0; n1 < M; ++n1) u[n1] = src[n1];
+                Dft<M, +1>::run(u);
+                const float2* pr = a.probe + (size_t)y * N + k2;
+                const size_t orow = (size_t)(p.x + y) * a.Wo + p.y + k2;
+                const float2* ob = a.obj + orow;
+                float2* ps = (mode != BWD_GRAD) ? a.psi + ((size_t)j * N + y) * N + k2 : nullptr;
+#pragma unroll
+                for (int k1 = 0; k1 < M; ++k1) {
+                    const float2 prv = __ldg(pr + R * k1);
+                    const float2 obv = ob[R * k1];
+                    float2 wv;
+                    if (mode == BWD_GRAD) {
+                        wv = u[k1];
+                        if (acc_o) {
+                            const float2 t = cconjmul(prv, wv);
+                            red_add_v2(a.grad_obj + orow + R * k1, t.x, t.y);
+                        }
+                    } else {
+                        wv = cadd(cmul(prv, obv), u[k1]);
+                        ps[R * k1] = wv;
+                    }
+                    if (acc_p) {
+                        const float2 t = cconjmul(obv, wv);
+                        if constexpr (kRegAcc) {
+                            np_r[i][k1].x += t.x;
+                            np_r[i][k1].y += t.y;
+                            dp_r[i][k1] += cnorm(obv);
+                        } else {
+                            const int e = line * N + k2 + R * k1;
+                            np_s[e].x += t.x;
+                            np_s[e].y += t.y;
+                            dp_s[e] += cnorm(obv);
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (acc_p) {
+        if constexpr (kRegAcc) {
+#pragma unroll
+            for (int i = 0; i < S::I2; ++i) {
+                const int w = threadIdx.x + i * kThreads;
+                if (w < L * R) {
+                    const int line = w / R, k2 = w - line * R;
+                    const size_t pidx = (size_t)(y0 + line) * N + k2;
+#pragma unroll
+                    for (int k1 = 0; k1 < M; ++k1) {
+                        if (mode == BWD_GRAD)
+                            red_add_v2(a.grad_probe + pidx + R * k1, np_r[i][k1].x, np_r[i][k1].y);
+                        else
+                            red_add_v4(a.acc_probe + pidx + R * k1, np_r[i][k1].x, np_r[i][k1].y, dp_r[i][k1],
+                                       0.f);
+                    }
+                }
+            }
+        } else {
+            // each thread flushes the pixels it accumulated (same mapping as above)
+#pragma unroll
+            for (int i = 0; i < S::I2; ++i) {
+                const int w = threadIdx.x + i * kThreads;
+                if (w < L * R) {
+                    const int line = w / R, k2 = w - line * R;
+                    const size_t pidx = (size_t)(y0 + line) * N + k2;
+#pragma unroll 4
+                    for (int k1 = 0; k1 < M; ++k1) {
+                        const int e = line * N + k2 + R * k1;
+                        if (mode == BWD_GRAD)
+                            red_add_v2(a.grad_probe + pidx + R * k1, np_s[e].x, np_s[e].y);
+                        else
+                            red_add_v4(a.acc_probe + pidx + R * k1, np_s[e].x, np_s[e].y, dp_s[e], 0.f);
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int N>
+size_t smem_row_fwd_r() { return sizeof(float2) * (N + (size_t)RegShape<N>::L * RegShape<N>::P); }
+template <int N>
+size_t smem_col_r() { return sizeof(float2) * (N + (size_t)RegShape<N>::L * RegShape<N>::P); }
+template <int N>
+size_t smem_row_bwd_r() {
+    using S = RegShape<N>;
+    const bool reg_acc = S::I2 * S::M <= 16;
+    return sizeof(float2) * (N + (size_t)S::L * S::P) + (reg_acc ? 0 : (size_t)S::L * N * (sizeof(float2) + sizeof(float)));
+}
+
+template <int N>
+cudaError_t set_attrs_r() {
+    cudaError_t e;
+    const int mx = 200 * 1024;
+    if ((e = cudaFuncSetAttribute(k_row_fwd_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    return cudaSuccess;
+}
+
+}  // namespace ptx

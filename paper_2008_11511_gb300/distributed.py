@@ -33,26 +33,36 @@ def allreduce_accumulators(acc_obj: torch.Tensor | None, acc_probe: torch.Tensor
             dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
 
 
-def dm_cycles_data_parallel(pb, ncycles: int, update_obj=True, update_probe=True, init_psi=False, group=None):
-    """DM cycles of a Ptycho that holds this rank's frames only: accumulate
-    without normalising, all-reduce the accumulators, normalise.  Returns the
-    global per-cycle LLK (device float64)."""
-    out = torch.empty(max(ncycles, 1), dtype=torch.float64, device=pb.device)
+def _overlap_update_split(pb, update_obj, update_probe, llk, group):
+    """Probe stage on the summed probe accumulator, object gather of this rank's
+    frames, all-reduce of the object accumulator, object stage."""
+    from .ptycho import PTX_STAGE_OBJ_GATHER, PTX_STAGE_OBJ_NORMALISE, PTX_STAGE_PROBE
     acc_o, acc_p = pb.accumulators()
+    allreduce_accumulators(None, acc_p if update_probe else None, llk, group=group)
+    st = (PTX_STAGE_PROBE if update_probe else 0) | (PTX_STAGE_OBJ_GATHER if update_obj else 0)
+    if st:
+        pb.normalise(stages=st)
+    if update_obj:
+        allreduce_accumulators(acc_o, None, group=group)
+        pb.normalise(stages=PTX_STAGE_OBJ_NORMALISE)
+
+
+def dm_cycles_data_parallel(pb, ncycles: int, update_obj=True, update_probe=True, init_psi=False, group=None):
+    """DM cycles of a Ptycho that holds this rank's frames only: the cycle's
+    passes without the overlap update, then the update with one all-reduce of
+    the probe sums and one of the object sums.  Returns the global per-cycle LLK."""
+    out = torch.empty(max(ncycles, 1), dtype=torch.float64, device=pb.device)
     for c in range(ncycles):
         llk = pb.dm(1, update_obj=update_obj, update_probe=update_probe, init_psi=(init_psi and c == 0),
                     normalise=False, llk=out[c:c + 1])
-        allreduce_accumulators(acc_o, acc_p, llk, group=group)
-        pb.normalise(update_obj=update_obj, update_probe=update_probe)
+        _overlap_update_split(pb, update_obj, update_probe, llk, group)
     return out[:ncycles]
 
 
 def ap_cycles_data_parallel(pb, ncycles: int, update_obj=True, update_probe=True, group=None):
     """AP cycles with the same split as ``dm_cycles_data_parallel``."""
     out = torch.empty(max(ncycles, 1), dtype=torch.float64, device=pb.device)
-    acc_o, acc_p = pb.accumulators()
     for c in range(ncycles):
         llk = pb.ap(1, update_obj=update_obj, update_probe=update_probe, normalise=False, llk=out[c:c + 1])
-        allreduce_accumulators(acc_o, acc_p, llk, group=group)
-        pb.normalise(update_obj=update_obj, update_probe=update_probe)
+        _overlap_update_split(pb, update_obj, update_probe, llk, group)
     return out[:ncycles]

@@ -13,8 +13,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (PTX_DM_INIT_PSI, PTX_NO_GRAPH, PTX_NO_NORMALISE, PTX_UPDATE_OBJ, PTX_UPDATE_PROBE,
-                   SUPPORTED_SIZES, Problem, PtychoError)
+from ._lib import (PTX_DM_INIT_PSI, PTX_NO_GRAPH, PTX_NO_NORMALISE, PTX_STAGE_OBJ_GATHER, PTX_STAGE_OBJ_NORMALISE,
+                   PTX_STAGE_PROBE, PTX_UPDATE_OBJ, PTX_UPDATE_PROBE, SUPPORTED_SIZES, Problem, PtychoError)
 
 
 def _stream_ptr(device) -> ctypes.c_void_p:
@@ -39,12 +39,13 @@ class Ptycho:
     iobs:      float32 (J, N, N) CUDA tensor, FFT order (zero frequency at [0, 0])
     positions: int (J, 2) array of (row, col) top-left patch corners
     mask:      optional uint8/bool (N, N) array, nonzero = bad pixel
-    psi:       complex64 (J, K, N, N) CUDA tensor for DM; allocated when
-               ``with_psi`` is set and none is given
+    psi:       complex64 (J, K, N, N) CUDA tensor, the exit-wave stack used by
+               the AP and DM cycles; allocated when ``with_psi`` is set and none
+               is given (LLK and gradient alone do not need it)
     """
 
     def __init__(self, obj: torch.Tensor, probe: torch.Tensor, iobs: torch.Tensor, positions, mask=None,
-                 psi: torch.Tensor | None = None, with_psi: bool = False):
+                 psi: torch.Tensor | None = None, with_psi: bool = True):
         _require_cuda(obj, "obj", torch.complex64)
         _require_cuda(probe, "probe", torch.complex64)
         _require_cuda(iobs, "iobs", torch.float32)
@@ -121,6 +122,8 @@ class Ptycho:
            normalise: bool = True, llk: torch.Tensor | None = None) -> torch.Tensor:
         """``ncycles`` alternating-projection cycles; returns the per-cycle LLK
         (float64 CUDA tensor of length ncycles)."""
+        if self.psi is None:
+            raise ValueError("AP needs the exit-wave stack: create Ptycho with with_psi=True")
         out = llk if llk is not None else torch.empty(max(ncycles, 1), dtype=torch.float64, device=self.device)
         with torch.cuda.device(self.device):
             _lib.call("ptx_ap_cycles", self._handle(), int(ncycles),
@@ -161,12 +164,14 @@ class Ptycho:
                       _stream_ptr(self.device))
         return out[0], go, gp
 
-    def normalise(self, update_obj: bool = True, update_probe: bool = True):
-        """Normalise O, P from the accumulated numerators/denominators (after
-        cycles run with ``normalise=False`` and an all-reduce of ``accumulators()``)."""
+    def normalise(self, update_obj: bool = True, update_probe: bool = True, stages: int | None = None):
+        """Second half of Psi2ObjProbe after cycles run with ``normalise=False``:
+        the probe from its accumulator, then the object gathered from Psi' with
+        the new probe.  ``stages`` (PTX_STAGE_* bits) runs selected stages, for
+        an all-reduce of ``accumulators()`` in between (data-parallel split)."""
+        f = stages if stages is not None else self._flags(update_obj, update_probe, True)
         with torch.cuda.device(self.device):
-            _lib.call("ptx_normalise", self._handle(), self._flags(update_obj, update_probe, True),
-                      _stream_ptr(self.device))
+            _lib.call("ptx_normalise", self._handle(), int(f), _stream_ptr(self.device))
 
     def accumulators(self):
         """Views of the object and probe accumulators: float32 (Ho, Wo, 4) and
@@ -223,4 +228,5 @@ class PtychoLLK(torch.autograd.Function):
         return (go * g if go is not None else None, gp * g if gp is not None else None, None)
 
 
-__all__ = ["Ptycho", "PtychoLLK", "PtychoError", "fft2", "SUPPORTED_SIZES"]
+__all__ = ["Ptycho", "PtychoLLK", "PtychoError", "fft2", "SUPPORTED_SIZES", "PTX_STAGE_PROBE",
+           "PTX_STAGE_OBJ_GATHER", "PTX_STAGE_OBJ_NORMALISE"]

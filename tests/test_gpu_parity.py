@@ -216,7 +216,7 @@ def _compare_cycle_state(s, pb, o_ref, p_ref, tol, psi_ref=None):
 
 def test_ap_one_cycle_parity():
     s, o0, p0 = warm("ap64")
-    pb = gpu_problem(s, with_psi=False, obj=o0, probe=p0)
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
     llk = pb.ap(1).cpu().numpy()
     o, p, l = oracle.ap_cycle(o0, p0, data_of(s))
     _compare_cycle_state(s, pb, o, p, TOL1)
@@ -227,7 +227,7 @@ def test_ap_one_cycle_parity():
 def test_ap64_20_cycles_parity():
     """Plain AP, 64x64 probe, 256x256 object, 100 positions, 20 cycles."""
     s, o0, p0 = warm("ap64")
-    pb = gpu_problem(s, with_psi=False, obj=o0, probe=p0)
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
     llk = pb.ap(20).cpu().numpy()
     o, p, _, llk_ref = oracle.cycles("AP", o0, p0, data_of(s), 20)
     _compare_cycle_state(s, pb, o, p, TOL20)
@@ -239,7 +239,7 @@ def test_ap64_20_cycles_parity():
 @pytest.mark.parametrize("flags", [(True, True), (True, False), (False, True), (False, False)])
 def test_ap_update_flags(flags):
     s, o0, p0 = warm("ap64", J=30)
-    pb = gpu_problem(s, with_psi=False, obj=o0, probe=p0)
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
     pb.ap(2, update_obj=flags[0], update_probe=flags[1])
     o, p, _, _ = oracle.cycles("AP", o0, p0, data_of(s), 2, update_obj=flags[0], update_probe=flags[1])
     _compare_cycle_state(s, pb, o, p, TOL1 * 2)
@@ -304,8 +304,8 @@ def test_multimode_dm_parity():
 def test_zero_extra_mode_equals_single_mode():
     s, o0, p0 = warm("ap64", J=30)
     p2 = np.concatenate([p0, np.zeros_like(p0)])
-    a = gpu_problem(s, with_psi=False, obj=o0, probe=p0)
-    b = gpu_problem(s, with_psi=False, obj=o0, probe=p2)
+    a = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    b = gpu_problem(s, with_psi=True, obj=o0, probe=p2)
     a.ap(2, update_probe=False)
     b.ap(2, update_probe=False)
     assert rel(b.obj.cpu().numpy(), a.obj.cpu().numpy()) < 1e-6
@@ -320,7 +320,7 @@ def test_other_frame_sizes_ap(N):
                   probe_radius=N * 0.18, mask_fraction=0.02)
     o0, p0, _ = oracle.ap_cycle(s.obj0, s.probe0, data_of(s))
     o0, p0 = o0.astype(np.complex64), p0.astype(np.complex64)
-    pb = gpu_problem(s, with_psi=False, obj=o0, probe=p0)
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
     llk = pb.ap(1).cpu().numpy()
     o, p, l = oracle.ap_cycle(o0, p0, data_of(s))
     _compare_cycle_state(s, pb, o, p, TOL1)
@@ -342,7 +342,7 @@ def test_single_frame_object_equals_frame_corner_positions():
     s2.positions = np.array([[0, 0], [256 - 64, 256 - 64], [0, 256 - 64], [256 - 64, 0]], dtype=np.int32)
     o2, p2, _ = oracle.ap_cycle(o2, p2, data_of(s2))
     o2, p2 = o2.astype(np.complex64), p2.astype(np.complex64)
-    pb = gpu_problem(s2, with_psi=False, obj=o2, probe=p2)
+    pb = gpu_problem(s2, with_psi=True, obj=o2, probe=p2)
     pb.ap(1)
     o, p, _ = oracle.ap_cycle(o2, p2, data_of(s2))
     _compare_cycle_state(s2, pb, o, p, TOL1)
@@ -352,7 +352,7 @@ def test_single_frame_object_equals_frame_corner_positions():
 def test_fully_masked_detector_leaves_waves_free():
     s, o0, p0 = warm("ap64", J=10)
     s.mask = np.ones_like(s.mask)
-    pb = gpu_problem(s, with_psi=False, obj=o0, probe=p0)
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
     llk = pb.ap(1).cpu().numpy()
     assert llk[0] == 0.0
     o, p, _ = oracle.ap_cycle(o0, p0, data_of(s))
@@ -364,7 +364,7 @@ def test_zero_probe_region_gives_zero_not_nan():
     s, o0, p0 = warm("ap64", J=10)
     probe = np.zeros_like(p0)
     probe[0, 20:40, 20:40] = p0[0, 20:40, 20:40]
-    pb = gpu_problem(s, with_psi=False, obj=o0, probe=probe)
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=probe)
     llk = pb.ap(1).cpu().numpy()
     assert np.all(np.isfinite(pb.obj.cpu().numpy())) and np.all(np.isfinite(pb.probe.cpu().numpy()))
     o, p, l = oracle.ap_cycle(o0, probe, data_of(s))
@@ -385,13 +385,17 @@ def test_accumulators_and_external_normalise_match_internal():
     """Data-parallel form: cycles with normalise=False, then ptx_normalise, equal
     the fused cycle (the all-reduce of a multi-GPU split would sit in between)."""
     s, o0, p0 = warm("ap64", J=40)
-    a = gpu_problem(s, with_psi=False, obj=o0, probe=p0)
-    b = gpu_problem(s, with_psi=False, obj=o0, probe=p0)
+    a = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    b = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
     a.ap(1)
     b.ap(1, normalise=False)
     acc_o, acc_p = b.accumulators()
+    assert float(acc_p[..., 2].max()) > 0
+    assert float(acc_o.abs().max()) == 0.0  # the object sums are gathered after the probe update
+    from paper_2008_11511_gb300.ptycho import PTX_STAGE_OBJ_GATHER, PTX_STAGE_OBJ_NORMALISE, PTX_STAGE_PROBE
+    b.normalise(stages=PTX_STAGE_PROBE | PTX_STAGE_OBJ_GATHER)
     assert float(acc_o[..., 2].max()) > 0
-    b.normalise()
+    b.normalise(stages=PTX_STAGE_OBJ_NORMALISE)
     assert rel(b.obj.cpu().numpy(), a.obj.cpu().numpy()) < 1e-6
     assert rel(b.probe.cpu().numpy(), a.probe.cpu().numpy()) < 1e-6
     assert float(b.accumulators()[0].abs().max()) == 0.0
@@ -400,14 +404,70 @@ def test_accumulators_and_external_normalise_match_internal():
 
 # ------------------------------------------------------------------ long runs and conditioning
 
-def test_dm_100_cycles_parity_ap64():
-    """DM, 100 cycles on the 64x64-frame scan: <= 1e-4 after 100 float32 cycles."""
-    s, o0, p0 = warm("ap64")
+def test_dm_100_cycles_parity_noise_free():
+    """DM, 100 cycles on noise-free 64x64-frame data from a start near the solution,
+    where the iteration converges: <= 1e-4 after 100 float32 cycles."""
+    s = make_config("ap64", noise=False)
+    rng = np.random.default_rng(21)
+    o0 = (s.obj_true * (1 + 0.02 * (rng.standard_normal(s.obj_true.shape)
+                                     + 1j * rng.standard_normal(s.obj_true.shape)))).astype(np.complex64)
+    p0 = (s.probe_true * (1 + 0.02 * (rng.standard_normal(s.probe_true.shape)
+                                       + 1j * rng.standard_normal(s.probe_true.shape)))).astype(np.complex64)
     pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
     llk = pb.dm(100, init_psi=True).cpu().numpy()
     o, p, psi, llk_ref = oracle.cycles("DM", o0, p0, data_of(s), 100)
     _compare_cycle_state(s, pb, o, p, TOL20, psi_ref=psi)
     np.testing.assert_allclose(llk, llk_ref, rtol=TOL20)
+    assert llk[-1] < llk[0]
+    pb.close()
+
+
+def _dm32_cycle(obj, probe, psi, data, init):
+    """DM cycle with transforms and projection in complex64 (SciPy), overlap update
+    as the oracle: an independent float32 evaluation."""
+    obj32, probe32 = obj.astype(np.complex64), probe.astype(np.complex64)
+    N = probe.shape[-1]
+    phi = np.stack([probe32 * obj32[r:r + N, c:c + N][None] for r, c in data.positions])
+    if init:
+        psi = phi.copy()
+    X = scipy.fft.fft2(2 * phi - psi, norm="ortho", axes=(-2, -1))
+    ic = (np.abs(X) ** 2).sum(1)
+    sc = np.where(data.mask, 1.0, np.sqrt(np.maximum(data.iobs, 0)) / np.maximum(np.sqrt(ic), 1e-20))
+    psi = (psi + scipy.fft.ifft2(X * sc[:, None].astype(np.float32), norm="ortho", axes=(-2, -1)) - phi)
+    psi = psi.astype(np.complex64)
+    o, p = oracle.overlap_update(obj32.astype(complex), probe32.astype(complex), psi.astype(complex), data.positions)
+    return o.astype(np.complex64), p.astype(np.complex64), psi
+
+
+def test_dm_noisy_trajectory_per_cycle_and_drift():
+    """On noisy data DM does not converge and its trajectory is sensitive to
+    rounding: any float32 evaluation drifts from FP64 (about x1.8 per cycle here).
+    Checked: one GPU cycle from the oracle's state at cycles 1, 10 and 30 matches
+    to 1e-5, and over 20 cycles the GPU drifts no more than an independent
+    single-precision implementation does."""
+    s, o0, p0 = warm("ap64")
+    data = data_of(s)
+    from paper_2008_11511_gb300 import Ptycho
+    o, p, psi = o0.astype(complex), p0.astype(complex), None
+    for c in range(31):
+        if c in (1, 10, 30):
+            pb = Ptycho(to_dev(o.astype(np.complex64)), to_dev(p.astype(np.complex64)), to_dev(s.iobs), s.positions,
+                        s.mask, psi=to_dev(psi.astype(np.complex64)))
+            pb.dm(1)
+            o1, p1, psi1, _ = oracle.dm_cycle(o.astype(np.complex64), p.astype(np.complex64),
+                                              psi.astype(np.complex64), data)
+            _compare_cycle_state(s, pb, o1, p1, TOL1, psi_ref=psi1)
+            pb.close()
+        o, p, psi, _ = oracle.dm_cycle(o, p, psi, data, init_psi=(c == 0))
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    pb.dm(20, init_psi=True)
+    o64, p64, _, _ = oracle.cycles("DM", o0, p0, data, 20)
+    o32, p32, psi32 = o0, p0, None
+    for c in range(20):
+        o32, p32, psi32 = _dm32_cycle(o32, p32, psi32, data, c == 0)
+    e_gpu = rel(pb.obj.cpu().numpy(), o64)
+    e_f32 = rel(o32, o64)
+    assert e_gpu < 5 * e_f32 + TOL1, (e_gpu, e_f32)
     pb.close()
 
 
@@ -423,9 +483,7 @@ def _single_precision_ap_cycle(obj, probe, data):
     ic = (np.abs(X) ** 2).sum(1)
     sc = np.where(data.mask, 1.0, np.sqrt(np.maximum(data.iobs, 0)) / np.maximum(np.sqrt(ic), 1e-20))
     psi = scipy.fft.ifft2(X * sc[:, None].astype(np.float32), norm="ortho", axes=(-2, -1))
-    sums = oracle.psi_to_obj_probe_sums(psi.astype(complex), obj32.astype(complex), probe32.astype(complex),
-                                        data.positions, obj.shape)
-    return oracle.normalise(obj32.astype(complex), probe32.astype(complex), sums)
+    return oracle.overlap_update(obj32.astype(complex), probe32.astype(complex), psi.astype(complex), data.positions)
 
 
 @pytest.mark.parametrize("cfg,J", [("ap64", 100), ("dm256", 40)])
@@ -437,7 +495,7 @@ def test_configured_start_is_at_the_float32_floor(cfg, J):
     X = np.abs(oracle.ft(oracle.obj_probe_to_psi(s.obj0.astype(complex), s.probe0.astype(complex),
                                                  s.positions[:1])))[0, 0]
     assert (X < 1e-7 * X.max()).mean() > 0.01  # the start is ill-conditioned in float32
-    pb = gpu_problem(s, with_psi=False)
+    pb = gpu_problem(s, with_psi=True)
     pb.ap(1)
     o64, p64, _ = oracle.ap_cycle(s.obj0, s.probe0, data)
     o32, p32 = _single_precision_ap_cycle(s.obj0, s.probe0, data)
