@@ -230,7 +230,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     from paper_2008_11511_gb300 import Ptycho, _lib
     from synthetic import make_config
-    s = make_config(WORKLOAD)
+    s = make_config(WORKLOAD) if not args.frames else make_config(WORKLOAD, J=args.frames)
     obj = torch.tensor(s.obj0, device=dev)
     probe = torch.tensor(s.probe0, device=dev)
     iobs = torch.tensor(s.iobs, device=dev)
@@ -261,6 +261,13 @@ def run_ours(args):
     ms_max = max_over_ranks(ms, ws)
     value = s.J * args.steps * ws / (ms_max / 1e3)
     ms_per_step = ms_max / args.steps
+
+    if args.timing_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms_per_step,
+                              "frames": s.J, "steps": args.steps, "timing_only": True}), flush=True)
+        pb.close()
+        return
 
     # per-kernel durations, live, with events on the launch stream (direct launches)
     _lib.call("ptx_profile_enable", pb._handle(), 1)
@@ -357,6 +364,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames", type=int, default=0,
+                    help="use only the first FRAMES frames of the workload (small cases for profiling)")
+    ap.add_argument("--timing-only", action="store_true",
+                    help="stop after the timed region (no per-kernel pass, e2e or CPU baseline)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
