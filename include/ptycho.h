@@ -180,6 +180,35 @@ ptx_status ptx_profile_enable(ptx_handle* h, int32_t enable);
  * duration in milliseconds (host double array) since profiling was enabled. */
 ptx_status ptx_profile_read(ptx_handle* h, int32_t nkinds, int64_t* launches, double* total_ms);
 
+/* Size of the fixed device array used by ptx_llk_static. */
+#define PTX_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* The exact Poisson log-likelihood of ptx_llk, computed without any device
+ * allocation, for callers that cannot allocate: code embedded in a host
+ * application that owns all device memory and hands out only its input and
+ * output buffers, or a loop that must never enter an allocator (cudaMalloc,
+ * torch's caching allocator).  The paper has no counterpart; this is a service
+ * of this library.
+ *
+ * Inputs: obj device complex64 [Ho][Wo], probe device complex64 [K][N][N],
+ * iobs device float32 [J][N][N] (FFT order), positions host int32 [J][2]
+ * (row, col), mask host uint8 [N][N] or NULL.  Output: llk_dev, one device
+ * double.  No handle, no scratch argument: all working memory (copied
+ * positions and mask, the Fourier work stack, the FP64 partial sums) lives in
+ * one file-scope device array of PTX_STATIC_SCRATCH_BYTES (16 MiB) that every
+ * GPU loading the library holds until the process exits.  The first call on
+ * a device looks up that array's address with cudaGetSymbolAddress, clears its mask region
+ * and synchronises the device once: make that first call before any stream
+ * capture.  Sizes beyond the array (J > 65536, J * N / lines > 65536 partial
+ * sums, or one frame's K * N * N * 8-byte work stack larger than the array's
+ * work region) are rejected with PTX_ERR_UNSUPPORTED and a message; nothing
+ * is enqueued then.  All calls share the array and it keeps the last call's
+ * contents; every call rewrites what it reads, but calls that overlap on the
+ * GPU race on it.  Calls no cudaMalloc, cudaFree or allocating library routine. */
+ptx_status ptx_llk_static(int32_t N, int32_t K, int32_t J, int32_t Ho, int32_t Wo, const void* obj,
+                          const void* probe, const int32_t* positions, const float* iobs, const uint8_t* mask,
+                          double* llk_dev, void* stream);
+
 /* Text of the last failure on the calling thread ("" if none). */
 const char* ptx_last_error(void);
 

@@ -84,6 +84,15 @@ ptx_status fail(ptx_status st, const char* fmt, ...) {
     return st;
 }
 
+}  // namespace
+
+namespace ptx {
+// Lets other translation units of the library report through ptx_last_error.
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace ptx
+
+namespace {
+
 ptx_status cuda_fail(cudaError_t e, const char* what) {
     return fail(PTX_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
