@@ -34,25 +34,38 @@ __global__ void __launch_bounds__(256) k_obj_gather(ProbArgs a, TileLists tl) {
         d[q] = 0.f;
     }
     const int f0 = tl.tile_ptr[t], f1 = tl.tile_ptr[t + 1];
-    for (int f = f0; f < f1; ++f) {
-        const int j = tl.tile_frames[f];
-        const int2 p = a.pos[j];
-        const int px = x - p.y;
-        if (px < 0 || px >= N) continue;
+    const int y0 = ty * T + wy;
+    // F frames per step: all their loads are issued before any is used, so each
+    // thread keeps up to 2 F Q loads in flight (the loop is latency-bound otherwise)
+    constexpr int F = 4;
+    for (int f = f0; f < f1; f += F) {
+        float2 pr[F][Q], ps[F][Q];
+        bool ok[F][Q];
+        for (int k = 0; k < K; ++k) {
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int y = ty * T + wy + 8 * q;
-            const int py = y - p.x;
-            if (py >= 0 && py < N) {
-                for (int k = 0; k < K; ++k) {
-                    const float2 pr = __ldg(a.probe + ((size_t)k * N + py) * N + px);
-                    const float2 ps = __ldcs(a.psi + (((size_t)j * K + k) * N + py) * N + px);
-                    const float2 c = cconjmul(pr, ps);
-                    n[q].x += c.x;
-                    n[q].y += c.y;
-                    d[q] = fmaf(pr.x, pr.x, fmaf(pr.y, pr.y, d[q]));
+            for (int u = 0; u < F; ++u) {
+                const int fi = f + u;
+                const int j = fi < f1 ? tl.tile_frames[fi] : 0;
+                const int2 p = a.pos[j];
+                const int px = x - p.y;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const int py = y0 + 8 * q - p.x;
+                    ok[u][q] = fi < f1 && px >= 0 && px < N && py >= 0 && py < N;
+                    const size_t off = ok[u][q] ? ((size_t)k * N + py) * N + px : 0;
+                    pr[u][q] = ok[u][q] ? __ldg(a.probe + off) : make_float2(0.f, 0.f);
+                    ps[u][q] = ok[u][q] ? __ldcs(a.psi + (size_t)j * K * N * N + off) : make_float2(0.f, 0.f);
                 }
             }
+#pragma unroll
+            for (int u = 0; u < F; ++u)
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const float2 c = cconjmul(pr[u][q], ps[u][q]);
+                    n[q].x += c.x;
+                    n[q].y += c.y;
+                    d[q] = fmaf(pr[u][q].x, pr[u][q].x, fmaf(pr[u][q].y, pr[u][q].y, d[q]));
+                }
         }
     }
     if (x < a.Wo) {

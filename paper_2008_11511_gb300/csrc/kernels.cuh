@@ -56,6 +56,14 @@ struct Ctl {
     int pad;
 };
 
+// Asynchronous 16-byte global -> shared copy (cp.async, bypassing L1).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void red_add_v4(float4* addr, float a, float b, float c, float d) {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
                  : "memory");
@@ -83,6 +91,34 @@ __device__ __forceinline__ float llk_term(float ic, float io) {
         f = u - logf(icf / io);
     }
     return io * f;
+}
+
+// The same term with hardware-approximate division and logarithm (each a few
+// ulp): u, t by __fdividef, ln by __logf in the branch where |u - ln(1+u)| is
+// at least 0.19 |u|, so the term keeps a relative error of a few 1e-7.
+__device__ __forceinline__ float llk_term_fast(float ic, float io) {
+    if (!(io > 0.f)) return ic;
+    const float icf = fmaxf(ic, 1e-30f);
+    const float u = __fdividef(icf - io, io);
+    float f;
+    if (u > -0.5f && u < 1.0f) {
+        const float t = __fdividef(u, 2.0f + u);
+        const float t2 = t * t;
+        const float poly = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, 1.f / 15.f, 1.f / 13.f), 1.f / 11.f),
+                                                           1.f / 9.f), 1.f / 7.f), 1.f / 5.f), 1.f / 3.f);
+        f = fmaf(u, t, -2.0f * t * t2 * poly);
+    } else {
+        f = u - __logf(__fdividef(icf, io));
+    }
+    return io * f;
+}
+
+// sqrt(max(io, 0)) / max(sqrt(ic), 1e-20): the amplitude-projection factor, with
+// reciprocal square roots (<= 2 ulp each); ic below 1e-40 keeps the floor.
+__device__ __forceinline__ float amp_ratio(float io, float ic) {
+    const float iop = fmaxf(io, 0.f);
+    const float sq_io = iop > 0.f ? iop * rsqrtf(iop) : 0.f;
+    return ic > 1e-38f ? sq_io * rsqrtf(ic) : sq_io * 1e20f;
 }
 
 // Kahan-compensated float accumulation (per thread), reduced in FP64 across the block.

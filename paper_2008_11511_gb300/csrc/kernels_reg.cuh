@@ -35,6 +35,9 @@ struct RegShape {
     static constexpr int R = Plan<N>::R, M = Plan<N>::M, L = reg_lines<N>(), P = reg_pitch<N>();
     static constexpr int I1 = (L * M + kThreads - 1) / kThreads;  // pass-1 items per thread
     static constexpr int I2 = (L * R + kThreads - 1) / kThreads;  // pass-2 items per thread
+    // blocks per SM the register budget is sized for: large codelets (24, 32
+    // points) need more registers per thread
+    static constexpr int MinBlocks = (R > M ? R : M) >= 24 ? 2 : 5;
     static_assert(M > 1, "register kernels need two passes");
     static_assert(N % L == 0, "lines per block must divide N");
 };
@@ -52,7 +55,7 @@ __device__ __forceinline__ float2 tw_get(const float2* tw, int a, int b) {
 // grid (N / L, frames in batch)
 // ---------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(kThreads) k_row_fwd_r(ProbArgs a, int j0, int mode) {
+__global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_r(ProbArgs a, int j0, int mode) {
     using S = RegShape<N>;
     constexpr int R = S::R, M = S::M, L = S::L, P = S::P;
     extern __shared__ __align__(16) float2 sm[];
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(kThreads) k_row_fwd_r(ProbArgs a, int j0, int 
 // grid (N / L, frames in batch); block handles columns [x0, x0 + L).
 // ---------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(kThreads) k_col_r(ProbArgs a, int j0, int mode) {
+__global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_col_r(ProbArgs a, int j0, int mode) {
     using S = RegShape<N>;
     constexpr int R = S::R, M = S::M, C = S::L, P = S::P;
     constexpr int I1b = (C * M + kThreads - 1) / kThreads;  // inverse pass-2 items (M per column)
@@ -173,14 +176,14 @@ __global__ void __launch_bounds__(kThreads) k_col_r(ProbArgs a, int j0, int mode
                 const float ic = cnorm(u[i][k1]) * invN2;
                 const float io = __ldcs(io_b + (size_t)row * N + c);
                 const bool masked = __ldg(mk_b + row * N + c) != 0;
-                if (!masked) llk.add(llk_term(ic, io));
+                if (!masked) llk.add(llk_term_fast(ic, io));
                 float f;
                 if (masked) {
                     f = 0.f;
                 } else if (mode == COL_PROJECT) {
-                    f = (sqrtf(fmaxf(io, 0.f)) / fmaxf(sqrtf(ic), 1e-20f) - 1.0f) * invN2;
+                    f = (amp_ratio(io, ic) - 1.0f) * invN2;
                 } else {
-                    f = 2.0f * (1.0f - fmaxf(io, 0.f) / fmaxf(ic, 1e-30f)) * invN2;
+                    f = 2.0f * (1.0f - __fdividef(fmaxf(io, 0.f), fmaxf(ic, 1e-30f))) * invN2;
                 }
                 u[i][k1] = cscale(u[i][k1], f);
             }
@@ -225,19 +228,27 @@ __global__ void __launch_bounds__(kThreads) k_col_r(ProbArgs a, int j0, int mode
 // grid (N / L, G); block handles rows [y0, y0 + L) of frames blockIdx.y + G t.
 // ---------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(kThreads) k_row_bwd_r(ProbArgs a, int j0, int nb, int mode, int upd_obj,
-                                                        int upd_probe) {
+__global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, int nb, int mode, int upd_obj,
+                                                           int upd_probe) {
     using S = RegShape<N>;
     constexpr int R = S::R, M = S::M, L = S::L, P = S::P;
     constexpr bool kRegAcc = S::I2 * M <= 16;  // probe accumulators in registers, else shared memory
     constexpr int IA = kRegAcc ? S::I2 : 1, MA = kRegAcc ? M : 1;
     extern __shared__ __align__(16) float2 sm[];
     float2* tw = sm;
-    float2* buf = sm + N;
+    float2* stage = sm + N;                     // [L][N] next frame's rows (cp.async)
+    float2* buf = stage + L * N;
     float2* np_s = buf + L * P;                 // [L][N] when !kRegAcc
     float* dp_s = (float*)(np_s + L * N);       // [L][N]
     load_twiddles<N>(tw);
     const int y0 = blockIdx.x * L;
+    // the rows [y0, y0 + L) of frame b are contiguous: copy them in 16-byte chunks
+    auto prefetch = [&](int b) {
+        const float2* src = a.spec + ((size_t)b * N + y0) * N;
+        for (int e = threadIdx.x; e < L * N / 2; e += kThreads) cp_async16(stage + 2 * e, src + 2 * e);
+        cp_async_commit();
+    };
+    if (blockIdx.y < nb) prefetch(blockIdx.y);
     const bool acc_o = upd_obj != 0, acc_p = upd_probe != 0;
     float2 np_r[IA][MA];
     float dp_r[IA][MA];
@@ -258,12 +269,14 @@ __global__ void __launch_bounds__(kThreads) k_row_bwd_r(ProbArgs a, int j0, int 
     for (int b = blockIdx.y; b < nb; b += gridDim.y) {
         const int j = j0 + b;
         const int2 p = a.pos[j];
+        cp_async_wait_all();
+        __syncthreads();
 #pragma unroll
         for (int i = 0; i < S::I1; ++i) {
             const int w = threadIdx.x + i * kThreads;
             if (w < L * M) {
                 const int line = w / M, n1 = w - line * M;
-                const float2* src = a.spec + ((size_t)b * N + y0 + line) * N + n1;
+                const float2* src = stage + line * N + n1;
                 float2 v[R];
 #pragma unroll
                 for (int n2 = 0; n2 < R; ++n2) v[n2] = src[M * n2];
@@ -275,6 +288,7 @@ __global__ void __launch_bounds__(kThreads) k_row_bwd_r(ProbArgs a, int j0, int 
             }
         }
         __syncthreads();
+        if (b + (int)gridDim.y < nb) prefetch(b + gridDim.y);  // stage is free again
 #pragma unroll
         for (int i = 0; i < S::I2; ++i) {
             const int w = threadIdx.x + i * kThreads;
@@ -371,16 +385,21 @@ template <int N>
 size_t smem_row_bwd_r() {
     using S = RegShape<N>;
     const bool reg_acc = S::I2 * S::M <= 16;
-    return sizeof(float2) * (N + (size_t)S::L * S::P) + (reg_acc ? 0 : (size_t)S::L * N * (sizeof(float2) + sizeof(float)));
+    return sizeof(float2) * (N + (size_t)S::L * N + (size_t)S::L * S::P) +
+           (reg_acc ? 0 : (size_t)S::L * N * (sizeof(float2) + sizeof(float)));
 }
 
 template <int N>
 cudaError_t set_attrs_r() {
     cudaError_t e;
     const int mx = 200 * 1024;
+    const int carve = cudaSharedmemCarveoutMaxShared;  // room for 5-6 blocks of ~37 KB per SM
     if ((e = cudaFuncSetAttribute(k_row_fwd_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_row_bwd_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_fwd_r<N>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_r<N>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     return cudaSuccess;
 }
 
