@@ -235,6 +235,8 @@ def run_ours(args):
     probe = torch.tensor(s.probe0, device=dev)
     iobs = torch.tensor(s.iobs, device=dev)
     pb = Ptycho(obj, probe, iobs, s.positions, s.mask, with_psi=True)
+    if args.lanes:
+        pb.set_param("lanes", args.lanes)
     stream = torch.cuda.current_stream(dev)
     llk_buf = torch.empty(max(args.steps, args.warmup, 1), dtype=torch.float64, device=dev)
 
@@ -366,6 +368,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=0,
                     help="use only the first FRAMES frames of the workload (small cases for profiling)")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="batches in flight per cycle (library default when 0)")
     ap.add_argument("--timing-only", action="store_true",
                     help="stop after the timed region (no per-kernel pass, e2e or CPU baseline)")
     args = ap.parse_args()

@@ -103,6 +103,10 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // Default size of the Fourier-space batch work stack: small enough to stay
 // resident in the 129 MB L2 together with the streamed exit waves.
 constexpr size_t kSpecBudget = (size_t)64 << 20;
+// Batches in flight per cycle (streams): the next batch's row passes overlap the
+// current batch's column pass, and kernel tails fill in.
+constexpr int kDefaultLanes = 2;
+constexpr int kMaxLanes = 4;
 
 struct Layout {
     size_t pos, mask, acc_obj, acc_probe, llk_part, maxbits, tile_ids, tile_ptr, tile_frames;
@@ -197,6 +201,23 @@ ptx_status check_problem(const ptx_problem& p, int idx) {
     return PTX_OK;
 }
 
+// Batches of frames: `lanes` batches are in flight at once (one per stream),
+// each with its own slice of the work-stack region of `spec_bytes`.
+void set_batch(ProbHost& h, size_t spec_bytes, int lanes) {
+    const ptx_problem& p = h.p;
+    const size_t frame_bytes = (size_t)p.K * p.N * p.N * sizeof(float2);
+    size_t B = spec_bytes / ((size_t)lanes * frame_bytes);
+    if (B < 1) B = 1;
+    if (B > (size_t)p.J) B = p.J;
+    if (B > 32768) B = 32768;  // grid.y limit of the batch kernels
+    h.B = (int)B;
+    const int rowblk = p.N / h.L3;
+    int G = (2 * 152 + rowblk - 1) / rowblk;
+    if (G > h.B) G = h.B;
+    if (G < 1) G = 1;
+    h.G3 = G;
+}
+
 void plan_problem(ProbHost& h) {
     const ptx_problem& p = h.p;
     h.ks = kernel_set(p.N);
@@ -208,17 +229,7 @@ void plan_problem(ProbHost& h) {
         h.C2 = choose_lines(p.N, p.K, maxl);
         h.L3 = choose_lines(p.N, p.K, maxl);
     }
-    const size_t frame_bytes = (size_t)p.K * p.N * p.N * sizeof(float2);
-    size_t B = kSpecBudget / frame_bytes;
-    if (B < 1) B = 1;
-    if (B > (size_t)p.J) B = p.J;
-    if (B > 32768) B = 32768;  // grid.y limit of the batch kernels
-    h.B = (int)B;
-    const int rowblk = p.N / h.L3;
-    int G = (2 * 152 + rowblk - 1) / rowblk;
-    if (G > h.B) G = h.B;
-    if (G < 1) G = 1;
-    h.G3 = G;
+    set_batch(h, kSpecBudget, kDefaultLanes);
 }
 
 // Per-problem regions (offsets relative to the problem's base).
@@ -265,6 +276,12 @@ struct ptx_handle {
     int device = 0;
     cudaStream_t cap_stream = nullptr;
     std::map<GraphKey, cudaGraphExec_t> graphs;
+    // batch lanes: extra streams and fork / join events (lane 0 is the call's stream)
+    int lanes = kDefaultLanes;
+    size_t spec_bytes = 0;
+    cudaStream_t lane_stream[kMaxLanes] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kMaxLanes] = {};
     // per-kernel timing (ptx_profile_enable)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -291,7 +308,7 @@ ptx_status compute_layout(std::vector<ProbHost>& probs, size_t* spec_off, size_t
         h.lay.tile_frames += o;
         h.lay.end += o;
         o += sz;
-        size_t s = (size_t)h.B * h.p.K * h.p.N * h.p.N * sizeof(float2);
+        size_t s = (size_t)h.B * kDefaultLanes * h.p.K * h.p.N * h.p.N * sizeof(float2);
         if (s > spec) spec = s;
     }
     *ctl_off = o;
@@ -389,33 +406,70 @@ void enqueue_stages(ptx_handle* h, ProbHost& ph, int stages, cudaStream_t s) {
     }
 }
 
-// One cycle of every problem, enqueued on `s`.
+ptx_status ensure_lanes(ptx_handle* h) {
+    cudaError_t e;
+    if (!h->fork_ev && (e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventCreate");
+    for (int l = 1; l < kMaxLanes; ++l) {
+        if (!h->lane_stream[l] &&
+            (e = cudaStreamCreateWithFlags(&h->lane_stream[l], cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamCreateWithFlags");
+        if (!h->join_ev[l] && (e = cudaEventCreateWithFlags(&h->join_ev[l], cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventCreate");
+    }
+    return PTX_OK;
+}
+
+// One cycle of every problem, enqueued on `s`.  Batches go round-robin to the
+// lanes (lane 0 = s), each lane with its own work stack; the lanes fork from
+// and join back into s around the batch passes.
 ptx_status enqueue_cycle(ptx_handle* h, int algo, uint32_t flags, cudaStream_t s) {
     const bool upd_o = flags & PTX_UPDATE_OBJ;
     const bool upd_p = flags & PTX_UPDATE_PROBE;
     const bool init = flags & PTX_DM_INIT_PSI;
     const int np = (int)h->probs.size();
+    const int lanes = h->profiling ? 1 : h->lanes;  // per-kernel timing wants kernels alone
+    if (lanes > 1) {
+        ptx_status st = ensure_lanes(h);
+        if (st != PTX_OK) return st;
+    }
     for (int pi = 0; pi < np; ++pi) {
         ProbHost& ph = h->probs[pi];
+        set_batch(ph, h->spec_bytes, lanes);
         const ProbArgs& a = ph.args;
         const KernelSet* ks = ph.ks;
         const int fwd_mode = (algo == ALGO_DM && !init) ? X_DM : X_PHI;
         const int bwd_mode = (algo == ALGO_DM) ? BWD_DM : BWD_AP;
-        for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
+        const int nbatch = (ph.p.J + ph.B - 1) / ph.B;
+        const int used = std::min(lanes, nbatch);
+        if (used > 1) {
+            cudaEventRecord(h->fork_ev, s);
+            for (int l = 1; l < used; ++l) cudaStreamWaitEvent(h->lane_stream[l], h->fork_ev, 0);
+        }
+        const size_t lane_elems = (size_t)ph.B * ph.p.K * ph.p.N * ph.p.N;
+        for (int bi = 0, j0 = 0; j0 < ph.p.J; ++bi, j0 += ph.B) {
             const int nb = std::min(ph.B, ph.p.J - j0);
             const int G = std::min(ph.G3, nb);
+            const int lane = bi % used;
+            cudaStream_t ls = lane == 0 ? s : h->lane_stream[lane];
+            ProbArgs al = a;
+            al.spec = a.spec + lane * lane_elems;
             {
-                ProfScope ps(h, PTX_KERNEL_ROW_FWD, s);
-                ks->row_fwd(a, j0, nb, fwd_mode, s);
+                ProfScope ps(h, PTX_KERNEL_ROW_FWD, ls);
+                ks->row_fwd(al, j0, nb, fwd_mode, ls);
             }
             {
-                ProfScope ps(h, PTX_KERNEL_COL, s);
-                ks->col(a, j0, nb, COL_PROJECT, s);
+                ProfScope ps(h, PTX_KERNEL_COL, ls);
+                ks->col(al, j0, nb, COL_PROJECT, ls);
             }
             {
-                ProfScope ps(h, PTX_KERNEL_ROW_BWD, s);
-                ks->row_bwd(a, j0, nb, G, bwd_mode, 0, upd_p, s);
+                ProfScope ps(h, PTX_KERNEL_ROW_BWD, ls);
+                ks->row_bwd(al, j0, nb, G, bwd_mode, 0, upd_p, ls);
             }
+        }
+        for (int l = 1; l < used; ++l) {
+            cudaEventRecord(h->join_ev[l], h->lane_stream[l]);
+            cudaStreamWaitEvent(s, h->join_ev[l], 0);
         }
         if (!(flags & PTX_NO_NORMALISE))
             enqueue_stages(h, ph, (upd_p ? STAGE_PROBE : 0) | (upd_o ? STAGE_OBJ_GATHER | STAGE_OBJ_NORMALISE : 0), s);
@@ -438,6 +492,10 @@ ptx_status get_graph(ptx_handle* h, int algo, uint32_t flags, cudaGraphExec_t* o
     if (!h->cap_stream) {
         if ((e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    if (h->lanes > 1) {
+        ptx_status st0 = ensure_lanes(h);
+        if (st0 != PTX_OK) return st0;
     }
     if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_fail(e, "cudaStreamBeginCapture");
@@ -551,6 +609,7 @@ ptx_status ptx_create(ptx_handle** out, const ptx_problem* probs, int32_t nprob,
     h->scratch_bytes = scratch_bytes;
     h->spec_off = spec_off;
     h->ctl_off = ctl_off;
+    h->spec_bytes = total - spec_off;
     h->ctl = (Ctl*)(h->scratch + ctl_off);
     cudaGetDevice(&h->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -679,6 +738,10 @@ ptx_status ptx_set_param(ptx_handle* h, const char* name, double value) {
         h->alpha_obj = value;
     } else if (!strcmp(name, "alpha_probe")) {
         h->alpha_probe = value;
+    } else if (!strcmp(name, "lanes")) {
+        if (value < 1 || value > kMaxLanes || value != (int)value)
+            return fail(PTX_ERR_INVALID_ARG, "lanes must be an integer in 1..%d", kMaxLanes);
+        h->lanes = (int)value;
     } else {
         return fail(PTX_ERR_INVALID_ARG, "unknown parameter '%s'", name);
     }
@@ -735,6 +798,11 @@ void ptx_destroy(ptx_handle* h) {
     drop_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    for (int l = 1; l < kMaxLanes; ++l) {
+        if (h->lane_stream[l]) cudaStreamDestroy(h->lane_stream[l]);
+        if (h->join_ev[l]) cudaEventDestroy(h->join_ev[l]);
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     delete h;
 }
 
