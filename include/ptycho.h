@@ -73,7 +73,8 @@ typedef struct {
                                  each must satisfy 0 <= row <= Ho-N, 0 <= col <= Wo-N */
     const float* iobs;      /* device float32 [J][N][N] observed intensities, FFT order; borrowed,
                                read-only, must stay valid for the handle's lifetime; negative
-                               values are treated as 0 */
+                               values are treated as 0.  iobs, probe and psi must be 16-byte
+                               aligned and obj 8-byte aligned (PTX_ERR_INVALID_ARG otherwise) */
     const uint8_t* mask;    /* host uint8 [N][N], nonzero = bad pixel (left free by the projection,
                                excluded from the LLK and its gradient); NULL = no mask; copied */
     void* psi;              /* device complex64 [J][K][N][N] exit-wave stack Psi (the Ptycho
@@ -192,7 +193,8 @@ ptx_status ptx_profile_read(ptx_handle* h, int32_t nkinds, int64_t* launches, do
  *
  * Inputs: obj device complex64 [Ho][Wo], probe device complex64 [K][N][N],
  * iobs device float32 [J][N][N] (FFT order), positions host int32 [J][2]
- * (row, col), mask host uint8 [N][N] or NULL.  Output: llk_dev, one device
+ * (row, col), mask host uint8 [N][N] or NULL; iobs and probe 16-byte aligned,
+ * obj 8-byte aligned.  Output: llk_dev, one device
  * double.  No handle, no scratch argument: all working memory (copied
  * positions and mask, the Fourier work stack, the FP64 partial sums) lives in
  * one file-scope device array of PTX_STATIC_SCRATCH_BYTES (16 MiB) that every

@@ -192,6 +192,8 @@ ptx_status check_problem(const ptx_problem& p, int idx) {
         return fail(PTX_ERR_INVALID_ARG, "problem %d: object %dx%d smaller than the frame %d", idx, p.Ho, p.Wo, p.N);
     if (!p.obj || !p.probe || !p.positions || !p.iobs)
         return fail(PTX_ERR_INVALID_ARG, "problem %d: obj, probe, positions and iobs must be non-null", idx);
+    if ((uintptr_t)p.iobs % 16 || (uintptr_t)p.obj % 8 || (uintptr_t)p.probe % 16 || (uintptr_t)p.psi % 16)
+        return fail(PTX_ERR_INVALID_ARG, "problem %d: iobs, probe and psi must be 16-byte aligned, obj 8-byte", idx);
     for (int j = 0; j < p.J; ++j) {
         const int r = p.positions[2 * j], c = p.positions[2 * j + 1];
         if (r < 0 || c < 0 || r > p.Ho - p.N || c > p.Wo - p.N)

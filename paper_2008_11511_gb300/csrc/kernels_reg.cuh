@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_col_r(Prob
     using S = RegShape<N>;
     constexpr int R = S::R, M = S::M, C = S::L, P = S::P;
     constexpr int I1b = (C * M + kThreads - 1) / kThreads;  // inverse pass-2 items (M per column)
+    static_assert(C % 8 == 0 && (C * P) % 2 == 0, "8- / 16-byte chunks and a 16-byte aligned stage");
     extern __shared__ __align__(16) float2 sm[];
     __shared__ double red_s[kThreads / 32];
     float2* tw = sm;
@@ -129,6 +130,28 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_col_r(Prob
     const int b = blockIdx.y;
     const int j = j0 + b;
     float2* spec = a.spec + (size_t)b * N * N + x0;
+    // the block's intensities and mask, copied to shared memory (cp.async) while
+    // the forward transform runs; C = 16 columns are 64 bytes of I and 16 of mask per row
+    float* io_s = (float*)(buf + C * P);          // [N][C]
+    uint8_t* mk_s = (uint8_t*)(io_s + N * C);     // [N][C]
+    {
+        const float* io_g = a.iobs + (size_t)j * N * N + x0;
+        constexpr int CH = C * 4 / 16;  // 16-byte chunks per row of intensities
+        for (int e = threadIdx.x; e < N * CH; e += kThreads) {
+            const int row = e / CH, q = e - row * CH;
+            cp_async16(io_s + row * C + 4 * q, io_g + (size_t)row * N + 4 * q);
+        }
+        if constexpr (C >= 16) {
+            constexpr int MC = C / 16;  // 16-byte chunks per row of mask
+            for (int e = threadIdx.x; e < N * MC; e += kThreads) {
+                const int row = e / MC, q = e - row * MC;
+                cp_async16(mk_s + row * C + 16 * q, a.mask + row * N + x0 + 16 * q);
+            }
+        } else {
+            for (int row = threadIdx.x; row < N; row += kThreads) cp_async8(mk_s + row * C, a.mask + row * N + x0);
+        }
+        cp_async_commit();
+    }
     __syncthreads();
     // forward pass 1: thread (c, n1) holds rows n1 + M n2 of column c
 #pragma unroll
@@ -159,11 +182,10 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_col_r(Prob
             for (int n1 = 0; n1 < M; ++n1) u[i][n1] = src[n1];
         }
     }
+    cp_async_wait_all();
     __syncthreads();
     constexpr float invN2 = 1.0f / float(N * N);
     KahanF llk;
-    const float* io_b = a.iobs + (size_t)j * N * N + x0;
-    const uint8_t* mk_b = a.mask + x0;
 #pragma unroll
     for (int i = 0; i < S::I2; ++i) {
         const int w = threadIdx.x + i * kThreads;
@@ -174,8 +196,8 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_col_r(Prob
             for (int k1 = 0; k1 < M; ++k1) {
                 const int row = k2 + R * k1;
                 const float ic = cnorm(u[i][k1]) * invN2;
-                const float io = __ldcs(io_b + (size_t)row * N + c);
-                const bool masked = __ldg(mk_b + row * N + c) != 0;
+                const float io = io_s[row * C + c];
+                const bool masked = mk_s[row * C + c] != 0;
                 if (!masked) llk.add(llk_term_fast(ic, io));
                 float f;
                 if (masked) {
@@ -236,20 +258,41 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
     constexpr int IA = kRegAcc ? S::I2 : 1, MA = kRegAcc ? M : 1;
     extern __shared__ __align__(16) float2 sm[];
     float2* tw = sm;
+    // object rows are staged too when the probe sums live in registers (the
+    // shared-memory budget of the large sizes has no room for them)
+    constexpr bool kStageObj = kRegAcc;
     float2* stage = sm + N;                     // [L][N] next frame's rows (cp.async)
-    float2* buf = stage + L * N;
+    float2* ostage = stage + L * N;             // [L][N] next frame's object rows (cp.async)
+    float2* buf = ostage + (kStageObj ? L * N : 0);
     float2* np_s = buf + L * P;                 // [L][N] when !kRegAcc
     float* dp_s = (float*)(np_s + L * N);       // [L][N]
     load_twiddles<N>(tw);
     const int y0 = blockIdx.x * L;
+    const bool acc_p = upd_probe != 0;
     // the rows [y0, y0 + L) of frame b are contiguous: copy them in 16-byte chunks
-    auto prefetch = [&](int b) {
+    // The work-stack stage is free once pass 1 has read it; the object stage only
+    // after the update that reads it, so the two are refilled at different points.
+    auto prefetch_spec = [&](int b) {
         const float2* src = a.spec + ((size_t)b * N + y0) * N;
         for (int e = threadIdx.x; e < L * N / 2; e += kThreads) cp_async16(stage + 2 * e, src + 2 * e);
         cp_async_commit();
     };
-    if (blockIdx.y < nb) prefetch(blockIdx.y);
-    const bool acc_o = upd_obj != 0, acc_p = upd_probe != 0;
+    auto prefetch_obj = [&](int b) {
+        if (kStageObj && (mode != BWD_GRAD || acc_p)) {
+            // object patch rows: 8-byte aligned only (arbitrary column offset)
+            const int2 q = a.pos[j0 + b];
+            for (int e = threadIdx.x; e < L * N; e += kThreads) {
+                const int line = e / N, x = e - line * N;
+                cp_async8(ostage + e, a.obj + (size_t)(q.x + y0 + line) * a.Wo + q.y + x);
+            }
+        }
+        cp_async_commit();
+    };
+    if (blockIdx.y < nb) {
+        prefetch_spec(blockIdx.y);
+        prefetch_obj(blockIdx.y);
+    }
+    const bool acc_o = upd_obj != 0;
     float2 np_r[IA][MA];
     float dp_r[IA][MA];
 #pragma unroll
@@ -288,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
             }
         }
         __syncthreads();
-        if (b + (int)gridDim.y < nb) prefetch(b + gridDim.y);  // stage is free again
+        if (b + (int)gridDim.y < nb) prefetch_spec(b + gridDim.y);  // the work-stack stage is free again
 #pragma unroll
         for (int i = 0; i < S::I2; ++i) {
             const int w = threadIdx.x + i * kThreads;
@@ -302,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
                 Dft<M, +1>::run(u);
                 const float2* pr = a.probe + (size_t)y * N + k2;
                 const size_t orow = (size_t)(p.x + y) * a.Wo + p.y + k2;
-                const float2* ob = a.obj + orow;
+                const float2* ob = (kStageObj && (mode != BWD_GRAD || acc_p)) ? ostage + line * N + k2 : a.obj + orow;
                 float2* ps = (mode != BWD_GRAD) ? a.psi + ((size_t)j * N + y) * N + k2 : nullptr;
 #pragma unroll
                 for (int k1 = 0; k1 < M; ++k1) {
@@ -336,6 +379,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
             }
         }
         __syncthreads();
+        if (b + (int)gridDim.y < nb) prefetch_obj(b + gridDim.y);  // the object stage is free again
     }
     if (acc_p) {
         if constexpr (kRegAcc) {
@@ -380,12 +424,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
 template <int N>
 size_t smem_row_fwd_r() { return sizeof(float2) * (N + (size_t)RegShape<N>::L * RegShape<N>::P); }
 template <int N>
-size_t smem_col_r() { return sizeof(float2) * (N + (size_t)RegShape<N>::L * RegShape<N>::P); }
+size_t smem_col_r() {
+    using S = RegShape<N>;
+    return sizeof(float2) * (N + (size_t)S::L * S::P) + (size_t)N * S::L * (sizeof(float) + 1);
+}
 template <int N>
 size_t smem_row_bwd_r() {
     using S = RegShape<N>;
     const bool reg_acc = S::I2 * S::M <= 16;
-    return sizeof(float2) * (N + (size_t)S::L * N + (size_t)S::L * S::P) +
+    return sizeof(float2) * (N + (reg_acc ? 2 : 1) * (size_t)S::L * N + (size_t)S::L * S::P) +
            (reg_acc ? 0 : (size_t)S::L * N * (sizeof(float2) + sizeof(float)));
 }
 

@@ -118,6 +118,8 @@ extern "C" ptx_status ptx_llk_static(int32_t N, int32_t K, int32_t J, int32_t Ho
     if (J < 1 || Ho < N || Wo < N) return fail(PTX_ERR_INVALID_ARG, "J >= 1 and an object of at least N x N needed");
     if (!obj || !probe || !positions || !iobs || !llk_dev)
         return fail(PTX_ERR_INVALID_ARG, "obj, probe, positions, iobs and llk_dev must be non-null");
+    if ((uintptr_t)iobs % 16 || (uintptr_t)probe % 16 || (uintptr_t)obj % 8)
+        return fail(PTX_ERR_INVALID_ARG, "iobs and probe must be 16-byte aligned, obj 8-byte");
     const ptx::KernelSet* ks = ptx::kernel_set(N);
     const int L = lines_for(ks, N, K);
     const size_t nparts = (size_t)N / L;
