@@ -503,3 +503,50 @@ def test_configured_start_is_at_the_float32_floor(cfg, J):
     e_o, e_p = rel(pb.obj.cpu().numpy(), o64), rel(pb.probe.cpu().numpy(), p64)
     assert e_o < 2 * floor_o + TOL1 and e_p < 2 * floor_p + TOL1, (e_o, floor_o, e_p, floor_p)
     pb.close()
+
+
+@pytest.mark.parametrize("N,J", [(64, 700), (128, 300), (192, 200), (384, 60), (512, 40)])
+def test_several_frames_per_block_all_sizes(N, J):
+    """Enough frames that every inverse-row block handles several frames (its
+    staged rows are refilled between frames), for each register-kernel size:
+    one AP and one DM cycle from a warm state."""
+    step = N / 10
+    ext = int(2 * step / np.sqrt(np.pi) * np.sqrt(J)) + N + 8
+    s = make_scan(f"many{N}", N=N, J=J, Ho=ext, Wo=ext + 8, seed=100 + N, photons=1e5, step=step,
+                  probe_radius=N * 0.16, mask_fraction=0.02)
+    data = data_of(s)
+    o0, p0, _ = oracle.ap_cycle(s.obj0, s.probe0, data)
+    o0, p0 = o0.astype(np.complex64), p0.astype(np.complex64)
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    llk = pb.ap(1).cpu().numpy()
+    o, p, l = oracle.ap_cycle(o0, p0, data)
+    _compare_cycle_state(s, pb, o, p, TOL1)
+    assert abs(llk[0] - l) / abs(l) < TOL1
+    pb.close()
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    pb.dm(1, init_psi=True)
+    o, p, psi, _ = oracle.dm_cycle(o0, p0, None, data, init_psi=True)
+    _compare_cycle_state(s, pb, o, p, TOL1, psi_ref=psi)
+    pb.close()
+
+
+def test_full_size_dm256_cycle_in_bench_configuration():
+    """The headline workload at full size — 4000 frames of 256x256, 2048x2048 object,
+    2 % mask — in bench.py's launch configuration (CUDA graph, two batch lanes):
+    one DM cycle from an exit-wave stack Psi = P O + 10 % noise (well-conditioned
+    in float32), against the FP64 oracle: every frame's Psi', the probe, the
+    object (illuminated region) and the cycle's LLK."""
+    s = make_config("dm256")
+    data = data_of(s)
+    rng = np.random.default_rng(30)
+    phi = oracle.obj_probe_to_psi(s.obj0.astype(complex), s.probe0.astype(complex), s.positions)
+    scale = 0.1 * np.sqrt(np.mean(np.abs(phi) ** 2))
+    psi0 = (phi + scale * (rng.standard_normal(phi.shape) + 1j * rng.standard_normal(phi.shape))).astype(np.complex64)
+    del phi
+    from paper_2008_11511_gb300 import Ptycho
+    pb = Ptycho(to_dev(s.obj0), to_dev(s.probe0), to_dev(s.iobs), s.positions, s.mask, psi=to_dev(psi0))
+    llk = pb.dm(1).cpu().numpy()
+    o, p, psi, l = oracle.dm_cycle(s.obj0, s.probe0, psi0, data)
+    _compare_cycle_state(s, pb, o, p, TOL1, psi_ref=psi)
+    assert abs(llk[0] - l) / abs(l) < TOL1
+    pb.close()
