@@ -116,6 +116,20 @@ ptx_status ptx_ap_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, double*
  * set at the first cycle.  llk_dev as for AP, with the LLK of FT(X). */
 ptx_status ptx_dm_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, double* llk_dev, void* stream);
 
+/* Algorithms of ptx_cycles. */
+#define PTX_ALGO_AP 0
+#define PTX_ALGO_DM 1
+
+/* Cycles of a batched handle (nprob independent problems of any sizes), each
+ * problem with its own algorithm: algorithms is a host int32 array [nprob] of
+ * PTX_ALGO_AP / PTX_ALGO_DM.  One cycle is one CUDA graph over all problems: the
+ * batches of every problem share the handle's lanes (streams), and a problem's
+ * overlap update runs as soon as its own batches are done.  Semantics per
+ * problem as ptx_ap_cycles / ptx_dm_cycles (PTX_DM_INIT_PSI applies to the DM
+ * problems); llk_dev as there. */
+ptx_status ptx_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, const int32_t* algorithms, double* llk_dev,
+                      void* stream);
+
 /* Exact Poisson log-likelihood of the current (O, P) (the LLK operator):
  * sum over frames and unmasked pixels of I_c - I_o + I_o ln(I_o / I_c) (I_c where
  * I_o = 0), I_c = sum_k |FT(Phi_jk)|^2.  Writes nprob doubles to llk_dev. */
@@ -152,7 +166,9 @@ ptx_status ptx_accumulators(ptx_handle* h, int32_t p, void** obj_acc, size_t* ob
                             void** probe_acc, size_t* probe_acc_bytes);
 
 /* Set a scalar parameter: "alpha_obj" or "alpha_probe" (inertia factors of the
- * normalisation, default 0.01 each, must be >= 0). */
+ * normalisation, default 0.01 each, must be >= 0); "lanes" (batches in flight per
+ * cycle, 1..4, default 2); "batch_frames" (upper bound on frames per batch, 0 =
+ * as many as the work stack holds). */
 ptx_status ptx_set_param(ptx_handle* h, const char* name, double value);
 
 /* In-place orthonormal 2D FFT of `nframes` N x N complex64 frames (the FT

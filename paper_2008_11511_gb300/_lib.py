@@ -29,11 +29,13 @@ PTX_DM_INIT_PSI = 0x4
 PTX_NO_NORMALISE = 0x8
 PTX_NO_GRAPH = 0x10
 PTX_MAX_MODES = 8
+PTX_ALGO_AP = 0
+PTX_ALGO_DM = 1
 SUPPORTED_SIZES = (8, 12, 16, 32, 64, 128, 192, 256, 384, 512)
 
 # Every symbol include/ptycho.h declares.
 EXPORTS = (
-    "ptx_workspace_bytes", "ptx_create", "ptx_ap_cycles", "ptx_dm_cycles", "ptx_llk", "ptx_ml_grad",
+    "ptx_workspace_bytes", "ptx_create", "ptx_ap_cycles", "ptx_dm_cycles", "ptx_cycles", "ptx_llk", "ptx_ml_grad",
     "ptx_normalise", "ptx_accumulators", "ptx_set_param", "ptx_fft2", "ptx_profile_enable", "ptx_profile_read",
     "ptx_llk_static", "ptx_last_error", "ptx_destroy",
 )
@@ -91,6 +93,7 @@ def load(path: str | None = None):
         "ptx_create": (st, [ctypes.POINTER(vp), ctypes.POINTER(Problem), i32, vp, sz, vp]),
         "ptx_ap_cycles": (st, [vp, i32, u32, vp, vp]),
         "ptx_dm_cycles": (st, [vp, i32, u32, vp, vp]),
+        "ptx_cycles": (st, [vp, i32, u32, vp, vp, vp]),
         "ptx_llk": (st, [vp, vp, vp]),
         "ptx_ml_grad": (st, [vp, vp, vp, vp, vp]),
         "ptx_normalise": (st, [vp, u32, vp]),

@@ -205,10 +205,11 @@ ptx_status check_problem(const ptx_problem& p, int idx) {
 
 // Batches of frames: `lanes` batches are in flight at once (one per stream),
 // each with its own slice of the work-stack region of `spec_bytes`.
-void set_batch(ProbHost& h, size_t spec_bytes, int lanes) {
+void set_batch(ProbHost& h, size_t spec_bytes, int lanes, int cap = 0) {
     const ptx_problem& p = h.p;
     const size_t frame_bytes = (size_t)p.K * p.N * p.N * sizeof(float2);
-    size_t B = spec_bytes / ((size_t)lanes * frame_bytes);
+    size_t B = (spec_bytes / lanes) / 256 * 256 / frame_bytes;
+    if (cap > 0 && B > (size_t)cap) B = cap;
     if (B < 1) B = 1;
     if (B > (size_t)p.J) B = p.J;
     if (B > 32768) B = 32768;  // grid.y limit of the batch kernels
@@ -261,9 +262,14 @@ size_t layout_problem(ProbHost& h) {
 }
 
 struct GraphKey {
-    int algo;
+    std::vector<int> algos;
     uint32_t flags;
-    bool operator<(const GraphKey& o) const { return algo != o.algo ? algo < o.algo : flags < o.flags; }
+    int lanes;
+    bool operator<(const GraphKey& o) const {
+        if (flags != o.flags) return flags < o.flags;
+        if (lanes != o.lanes) return lanes < o.lanes;
+        return algos < o.algos;
+    }
 };
 
 }  // namespace
@@ -280,10 +286,12 @@ struct ptx_handle {
     std::map<GraphKey, cudaGraphExec_t> graphs;
     // batch lanes: extra streams and fork / join events (lane 0 is the call's stream)
     int lanes = kDefaultLanes;
+    int batch_cap = 0;  // ptx_set_param "batch_frames"
     size_t spec_bytes = 0;
     cudaStream_t lane_stream[kMaxLanes] = {};
     cudaEvent_t fork_ev = nullptr;
     cudaEvent_t join_ev[kMaxLanes] = {};
+    std::vector<cudaEvent_t> prob_ev;  // [problem][lane]: a problem's batches done on a lane
     // per-kernel timing (ptx_profile_enable)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -412,7 +420,13 @@ ptx_status ensure_lanes(ptx_handle* h) {
     cudaError_t e;
     if (!h->fork_ev && (e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming)) != cudaSuccess)
         return cuda_fail(e, "cudaEventCreate");
-    for (int l = 1; l < kMaxLanes; ++l) {
+    while (h->prob_ev.size() < h->probs.size() * kMaxLanes) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventCreate");
+        h->prob_ev.push_back(ev);
+    }
+    for (int l = 0; l < kMaxLanes; ++l) {
         if (!h->lane_stream[l] &&
             (e = cudaStreamCreateWithFlags(&h->lane_stream[l], cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_fail(e, "cudaStreamCreateWithFlags");
@@ -422,10 +436,13 @@ ptx_status ensure_lanes(ptx_handle* h) {
     return PTX_OK;
 }
 
-// One cycle of every problem, enqueued on `s`.  Batches go round-robin to the
-// lanes (lane 0 = s), each lane with its own work stack; the lanes fork from
-// and join back into s around the batch passes.
-ptx_status enqueue_cycle(ptx_handle* h, int algo, uint32_t flags, cudaStream_t s) {
+// One cycle of every problem, enqueued on `s`.  With one lane everything runs
+// on s.  With several, the batches of all problems go round-robin to the lane
+// streams, each lane with its own slice of the work-stack region; s forks the
+// lanes, waits for a problem's batches before running that problem's overlap
+// update and LLK reduction (while the lanes go on with the next problem), and
+// joins the lanes at the end.
+ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t flags, cudaStream_t s) {
     const bool upd_o = flags & PTX_UPDATE_OBJ;
     const bool upd_p = flags & PTX_UPDATE_PROBE;
     const bool init = flags & PTX_DM_INIT_PSI;
@@ -434,28 +451,30 @@ ptx_status enqueue_cycle(ptx_handle* h, int algo, uint32_t flags, cudaStream_t s
     if (lanes > 1) {
         ptx_status st = ensure_lanes(h);
         if (st != PTX_OK) return st;
+        cudaEventRecord(h->fork_ev, s);
+        for (int l = 0; l < lanes; ++l) cudaStreamWaitEvent(h->lane_stream[l], h->fork_ev, 0);
     }
+    // lane slices of the work stack, in elements, 256-byte aligned
+    const size_t slice = (h->spec_bytes / lanes) / 256 * 256 / sizeof(float2);
+    int next_lane = 0;
     for (int pi = 0; pi < np; ++pi) {
         ProbHost& ph = h->probs[pi];
-        set_batch(ph, h->spec_bytes, lanes);
+        set_batch(ph, h->spec_bytes, lanes, h->batch_cap);
         const ProbArgs& a = ph.args;
         const KernelSet* ks = ph.ks;
+        const int algo = algos[pi];
         const int fwd_mode = (algo == ALGO_DM && !init) ? X_DM : X_PHI;
         const int bwd_mode = (algo == ALGO_DM) ? BWD_DM : BWD_AP;
-        const int nbatch = (ph.p.J + ph.B - 1) / ph.B;
-        const int used = std::min(lanes, nbatch);
-        if (used > 1) {
-            cudaEventRecord(h->fork_ev, s);
-            for (int l = 1; l < used; ++l) cudaStreamWaitEvent(h->lane_stream[l], h->fork_ev, 0);
-        }
-        const size_t lane_elems = (size_t)ph.B * ph.p.K * ph.p.N * ph.p.N;
-        for (int bi = 0, j0 = 0; j0 < ph.p.J; ++bi, j0 += ph.B) {
+        bool used[kMaxLanes] = {};
+        for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
             const int nb = std::min(ph.B, ph.p.J - j0);
             const int G = std::min(ph.G3, nb);
-            const int lane = bi % used;
-            cudaStream_t ls = lane == 0 ? s : h->lane_stream[lane];
+            const int lane = next_lane;
+            next_lane = (next_lane + 1) % lanes;
+            used[lane] = true;
+            cudaStream_t ls = lanes == 1 ? s : h->lane_stream[lane];
             ProbArgs al = a;
-            al.spec = a.spec + lane * lane_elems;
+            al.spec = a.spec + lane * slice;
             {
                 ProfScope ps(h, PTX_KERNEL_ROW_FWD, ls);
                 ks->row_fwd(al, j0, nb, fwd_mode, ls);
@@ -469,22 +488,30 @@ ptx_status enqueue_cycle(ptx_handle* h, int algo, uint32_t flags, cudaStream_t s
                 ks->row_bwd(al, j0, nb, G, bwd_mode, 0, upd_p, ls);
             }
         }
-        for (int l = 1; l < used; ++l) {
-            cudaEventRecord(h->join_ev[l], h->lane_stream[l]);
-            cudaStreamWaitEvent(s, h->join_ev[l], 0);
-        }
+        if (lanes > 1)
+            for (int l = 0; l < lanes; ++l)
+                if (used[l]) {
+                    cudaEvent_t ev = h->prob_ev[(size_t)pi * kMaxLanes + l];
+                    cudaEventRecord(ev, h->lane_stream[l]);
+                    cudaStreamWaitEvent(s, ev, 0);
+                }
         if (!(flags & PTX_NO_NORMALISE))
             enqueue_stages(h, ph, (upd_p ? STAGE_PROBE : 0) | (upd_o ? STAGE_OBJ_GATHER | STAGE_OBJ_NORMALISE : 0), s);
         ProfScope ps(h, PTX_KERNEL_CYCLE_END, s);
         k_cycle_end<<<1, 1024, 0, s>>>(h->ctl, a, pi, a.N / a.C2, pi == np - 1);
     }
+    if (lanes > 1)
+        for (int l = 0; l < lanes; ++l) {
+            cudaEventRecord(h->join_ev[l], h->lane_stream[l]);
+            cudaStreamWaitEvent(s, h->join_ev[l], 0);
+        }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return PTX_OK;
 }
 
-ptx_status get_graph(ptx_handle* h, int algo, uint32_t flags, cudaGraphExec_t* out) {
-    GraphKey key{algo, flags};
+ptx_status get_graph(ptx_handle* h, const std::vector<int>& algos, uint32_t flags, cudaGraphExec_t* out) {
+    GraphKey key{algos, flags, h->lanes};
     auto it = h->graphs.find(key);
     if (it != h->graphs.end()) {
         *out = it->second;
@@ -501,7 +528,7 @@ ptx_status get_graph(ptx_handle* h, int algo, uint32_t flags, cudaGraphExec_t* o
     }
     if ((e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_fail(e, "cudaStreamBeginCapture");
-    ptx_status st = enqueue_cycle(h, algo, flags, h->cap_stream);
+    ptx_status st = enqueue_cycle(h, algos, flags, h->cap_stream);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(h->cap_stream, &g);
     if (st != PTX_OK) {
@@ -532,13 +559,15 @@ ptx_status check_device(ptx_handle* h) {
     return PTX_OK;
 }
 
-ptx_status run_cycles(ptx_handle* h, int algo, int ncycles, uint32_t flags, double* llk_dev, void* stream) {
+ptx_status run_cycles(ptx_handle* h, const std::vector<int>& algos, int ncycles, uint32_t flags, double* llk_dev,
+                      void* stream) {
     if (!h) return fail(PTX_ERR_INVALID_ARG, "null handle");
     if (ncycles < 0) return fail(PTX_ERR_INVALID_ARG, "ncycles=%d must be >= 0", ncycles);
     const uint32_t known = PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_DM_INIT_PSI | PTX_NO_NORMALISE | PTX_NO_GRAPH;
     if (flags & ~known) return fail(PTX_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags & ~known);
-    if (algo == ALGO_AP && (flags & PTX_DM_INIT_PSI))
-        return fail(PTX_ERR_INVALID_ARG, "PTX_DM_INIT_PSI is a DM flag");
+    if ((int)algos.size() != (int)h->probs.size()) return fail(PTX_ERR_INVALID_ARG, "one algorithm per problem");
+    for (int a : algos)
+        if (a != ALGO_AP && a != ALGO_DM) return fail(PTX_ERR_INVALID_ARG, "algorithm %d is neither AP nor DM", a);
     for (size_t i = 0; i < h->probs.size(); ++i)
         if (!h->probs[i].p.psi)
             return fail(PTX_ERR_INVALID_ARG, "problem %zu: AP and DM cycles need the psi array", i);
@@ -554,11 +583,11 @@ ptx_status run_cycles(ptx_handle* h, int algo, int ncycles, uint32_t flags, doub
         if (c == 0 && (flags & PTX_DM_INIT_PSI)) f |= PTX_DM_INIT_PSI;
         if (graph) {
             cudaGraphExec_t ex;
-            if ((st = get_graph(h, algo, f, &ex)) != PTX_OK) return st;
+            if ((st = get_graph(h, algos, f, &ex)) != PTX_OK) return st;
             cudaError_t e = cudaGraphLaunch(ex, s);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
         } else {
-            if ((st = enqueue_cycle(h, algo, f, s)) != PTX_OK) return st;
+            if ((st = enqueue_cycle(h, algos, f, s)) != PTX_OK) return st;
         }
     }
     cudaError_t e = cudaGetLastError();
@@ -648,11 +677,20 @@ ptx_status ptx_create(ptx_handle** out, const ptx_problem* probs, int32_t nprob,
 }
 
 ptx_status ptx_ap_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, double* llk_dev, void* stream) {
-    return run_cycles(h, ALGO_AP, ncycles, flags, llk_dev, stream);
+    if (!h) return fail(PTX_ERR_INVALID_ARG, "null handle");
+    if (flags & PTX_DM_INIT_PSI) return fail(PTX_ERR_INVALID_ARG, "PTX_DM_INIT_PSI is a DM flag");
+    return run_cycles(h, std::vector<int>(h->probs.size(), ALGO_AP), ncycles, flags, llk_dev, stream);
 }
 
 ptx_status ptx_dm_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, double* llk_dev, void* stream) {
-    return run_cycles(h, ALGO_DM, ncycles, flags, llk_dev, stream);
+    if (!h) return fail(PTX_ERR_INVALID_ARG, "null handle");
+    return run_cycles(h, std::vector<int>(h->probs.size(), ALGO_DM), ncycles, flags, llk_dev, stream);
+}
+
+ptx_status ptx_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, const int32_t* algorithms, double* llk_dev,
+                      void* stream) {
+    if (!h || !algorithms) return fail(PTX_ERR_INVALID_ARG, "null handle or algorithms");
+    return run_cycles(h, std::vector<int>(algorithms, algorithms + h->probs.size()), ncycles, flags, llk_dev, stream);
 }
 
 ptx_status ptx_llk(ptx_handle* h, double* llk_dev, void* stream) {
@@ -744,6 +782,10 @@ ptx_status ptx_set_param(ptx_handle* h, const char* name, double value) {
         if (value < 1 || value > kMaxLanes || value != (int)value)
             return fail(PTX_ERR_INVALID_ARG, "lanes must be an integer in 1..%d", kMaxLanes);
         h->lanes = (int)value;
+    } else if (!strcmp(name, "batch_frames")) {
+        if (value != (int)value || value > 32768)
+            return fail(PTX_ERR_INVALID_ARG, "batch_frames must be an integer in 0..32768");
+        h->batch_cap = (int)value;
     } else {
         return fail(PTX_ERR_INVALID_ARG, "unknown parameter '%s'", name);
     }
@@ -800,10 +842,11 @@ void ptx_destroy(ptx_handle* h) {
     drop_graphs(h);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-    for (int l = 1; l < kMaxLanes; ++l) {
+    for (int l = 0; l < kMaxLanes; ++l) {
         if (h->lane_stream[l]) cudaStreamDestroy(h->lane_stream[l]);
         if (h->join_ev[l]) cudaEventDestroy(h->join_ev[l]);
     }
+    for (cudaEvent_t e : h->prob_ev) cudaEventDestroy(e);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     delete h;
 }

@@ -191,6 +191,90 @@ class Ptycho:
         _lib.call("ptx_set_param", self._handle(), name.encode(), float(value))
 
 
+class PtychoBatch:
+    """Several independent ptychography problems (any frame sizes and scan
+    lengths) in one handle: one CUDA graph per cycle over all of them, each
+    problem with its own algorithm (AP or DM).
+
+    problems: list of dicts with keys obj, probe, iobs, positions and optionally
+    mask and psi (allocated when absent), as for :class:`Ptycho`."""
+
+    def __init__(self, problems):
+        if not problems:
+            raise ValueError("no problems")
+        self.items = []
+        keep = []
+        arr = (Problem * len(problems))()
+        dev = None
+        for i, d in enumerate(problems):
+            obj, probe, iobs = d["obj"], d["probe"], d["iobs"]
+            _require_cuda(obj, "obj", torch.complex64)
+            _require_cuda(probe, "probe", torch.complex64)
+            _require_cuda(iobs, "iobs", torch.float32)
+            K, N, _ = probe.shape
+            J = iobs.shape[0]
+            dev = dev or obj.device
+            psi = d.get("psi")
+            if psi is None:
+                psi = torch.empty((J, K, N, N), dtype=torch.complex64, device=dev)
+            _require_cuda(psi, "psi", torch.complex64)
+            pos = np.ascontiguousarray(np.asarray(d["positions"], dtype=np.int32).reshape(J, 2))
+            m = d.get("mask")
+            m = None if m is None else np.ascontiguousarray(np.asarray(m).astype(np.uint8).reshape(N, N))
+            keep += [pos, m]
+            arr[i] = Problem(N=N, K=K, J=J, Ho=obj.shape[0], Wo=obj.shape[1], obj=obj.data_ptr(),
+                             probe=probe.data_ptr(), positions=pos.ctypes.data, iobs=iobs.data_ptr(),
+                             mask=(m.ctypes.data if m is not None else None), psi=psi.data_ptr())
+            self.items.append(dict(obj=obj, probe=probe, iobs=iobs, psi=psi, positions=pos, mask=m))
+        self.device = dev
+        self.nprob = len(problems)
+        nbytes = ctypes.c_size_t(0)
+        _lib.call("ptx_workspace_bytes", arr, self.nprob, ctypes.byref(nbytes))
+        with torch.cuda.device(dev):
+            self.scratch = torch.empty(int(nbytes.value), dtype=torch.uint8, device=dev)
+            h = ctypes.c_void_p()
+            _lib.call("ptx_create", ctypes.byref(h), arr, self.nprob, ctypes.c_void_p(self.scratch.data_ptr()), nbytes,
+                      _stream_ptr(dev))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            torch.cuda.current_stream(self.device).synchronize()
+            _lib.load().ptx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _handle(self):
+        if not self._h:
+            raise RuntimeError("PtychoBatch handle is closed")
+        return self._h
+
+    def cycles(self, ncycles: int, algorithms, update_obj: bool = True, update_probe: bool = True,
+               init_psi: bool = False, graph: bool = True) -> torch.Tensor:
+        """``ncycles`` cycles of every problem; ``algorithms`` lists "AP" / "DM" per
+        problem.  Returns the LLK as a float64 CUDA tensor (ncycles, nprob)."""
+        codes = np.array([_lib.PTX_ALGO_DM if str(a).upper() == "DM" else _lib.PTX_ALGO_AP for a in algorithms],
+                         dtype=np.int32)
+        if len(codes) != self.nprob:
+            raise ValueError("one algorithm per problem")
+        f = Ptycho._flags(update_obj, update_probe, graph)
+        if init_psi:
+            f |= PTX_DM_INIT_PSI
+        out = torch.empty(max(ncycles, 1) * self.nprob, dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            _lib.call("ptx_cycles", self._handle(), int(ncycles), f, ctypes.c_void_p(codes.ctypes.data),
+                      ctypes.c_void_p(out.data_ptr()), _stream_ptr(self.device))
+        return out[:ncycles * self.nprob].view(ncycles, self.nprob)
+
+    def set_param(self, name: str, value: float):
+        _lib.call("ptx_set_param", self._handle(), name.encode(), float(value))
+
+
 def fft2(x: torch.Tensor, direction: int = -1) -> torch.Tensor:
     """In-place orthonormal 2D FFT of complex64 frames (..., N, N) on the GPU
     (the FT operator; ``direction=+1`` is IFT).  Returns ``x``."""
@@ -228,5 +312,5 @@ class PtychoLLK(torch.autograd.Function):
         return (go * g if go is not None else None, gp * g if gp is not None else None, None)
 
 
-__all__ = ["Ptycho", "PtychoLLK", "PtychoError", "fft2", "SUPPORTED_SIZES", "PTX_STAGE_PROBE",
+__all__ = ["Ptycho", "PtychoBatch", "PtychoLLK", "PtychoError", "fft2", "SUPPORTED_SIZES", "PTX_STAGE_PROBE",
            "PTX_STAGE_OBJ_GATHER", "PTX_STAGE_OBJ_NORMALISE"]

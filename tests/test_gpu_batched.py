@@ -1,0 +1,103 @@
+"""Batched uneven scans through one handle (ptx_cycles): problems of different
+frame sizes and scan lengths, AP and DM alternately, each against its own FP64
+oracle cycle; and the schedule autotuner restoring the state it tunes on."""
+import numpy as np
+import pytest
+
+import oracle
+from synthetic import make_scan
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL1 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2008_11511_gb300 import build as b
+    b.build()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), device="cuda")
+
+
+def _problems():
+    specs = [(128, 150), (192, 60), (256, 90), (384, 30), (512, 20), (64, 300)]
+    out = []
+    for i, (N, J) in enumerate(specs):
+        step = N / 10
+        ext = int(2 * step / np.sqrt(np.pi) * np.sqrt(J)) + N + 8
+        s = make_scan(f"b{i}", N=N, J=J, Ho=ext, Wo=ext + 4, seed=200 + i, photons=10 ** (4 + i % 3), step=step,
+                      probe_radius=N * 0.16, mask_fraction=0.02 if i % 2 else 0.0)
+        data = oracle.Data.make(s.iobs, s.positions, s.mask)
+        o0, p0, _ = oracle.ap_cycle(s.obj0, s.probe0, data)
+        out.append((s, data, o0.astype(np.complex64), p0.astype(np.complex64)))
+    return out
+
+
+def test_batched_cycles_match_oracle_per_problem():
+    from paper_2008_11511_gb300 import PtychoBatch
+    probs = _problems()
+    algos = ["AP" if i % 2 == 0 else "DM" for i in range(len(probs))]
+    items = [dict(obj=dev(o0), probe=dev(p0), iobs=dev(s.iobs), positions=s.positions, mask=s.mask)
+             for s, data, o0, p0 in probs]
+    pb = PtychoBatch(items)
+    llk = pb.cycles(1, algos, init_psi=True).cpu().numpy()
+    for i, ((s, data, o0, p0), a) in enumerate(zip(probs, algos)):
+        if a == "AP":
+            o, p, l = oracle.ap_cycle(o0, p0, data)
+        else:
+            o, p, psi, l = oracle.dm_cycle(o0, p0, None, data, init_psi=True)
+            assert rel(pb.items[i]["psi"].cpu().numpy(), psi) < TOL1, i
+        assert rel(pb.items[i]["obj"].cpu().numpy(), o) < TOL1, (i, a)
+        assert rel(pb.items[i]["probe"].cpu().numpy(), p) < TOL1, (i, a)
+        assert abs(llk[0, i] - l) < TOL1 * abs(l), (i, a, llk[0, i], l)
+    pb.close()
+
+
+def test_batched_equals_separate_handles_over_cycles():
+    from paper_2008_11511_gb300 import Ptycho, PtychoBatch
+    probs = _problems()[:3]
+    algos = ["DM", "AP", "DM"]
+    items = [dict(obj=dev(o0), probe=dev(p0), iobs=dev(s.iobs), positions=s.positions, mask=s.mask)
+             for s, data, o0, p0 in probs]
+    pb = PtychoBatch(items)
+    pb.cycles(3, algos, init_psi=True)
+    for i, (s, data, o0, p0) in enumerate(probs):
+        one = Ptycho(dev(o0), dev(p0), dev(s.iobs), s.positions, s.mask)
+        if algos[i] == "DM":
+            one.dm(3, init_psi=True)
+        else:
+            one.ap(3)
+        assert rel(pb.items[i]["obj"].cpu().numpy(), one.obj.cpu().numpy()) < 1e-6
+        assert rel(pb.items[i]["probe"].cpu().numpy(), one.probe.cpu().numpy()) < 1e-6
+        one.close()
+    pb.close()
+
+
+def test_autotune_restores_state_and_sets_a_schedule():
+    from paper_2008_11511_gb300 import Ptycho
+    from paper_2008_11511_gb300.autotune import autotune
+    s, data, o0, p0 = _problems()[2]
+    pb = Ptycho(dev(o0), dev(p0), dev(s.iobs), s.positions, s.mask)
+    pb.dm(1, init_psi=True)
+    before = [t.clone() for t in (pb.obj, pb.probe, pb.psi)]
+    best, times = autotune(pb, ["DM"], lanes=(1, 2), batch_frames=(0, 16), use_cache=False)
+    assert best in times and len(times) == 4
+    for t, b in zip((pb.obj, pb.probe, pb.psi), before):
+        assert torch.equal(t, b)
+    # tuned schedule gives the same cycle as the default one
+    ref = Ptycho(before[0].clone(), before[1].clone(), dev(s.iobs), s.positions, s.mask, psi=before[2].clone())
+    pb.dm(1)
+    ref.dm(1)
+    assert rel(pb.obj.cpu().numpy(), ref.obj.cpu().numpy()) < 1e-6
+    pb.close()
+    ref.close()
