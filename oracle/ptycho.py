@@ -314,6 +314,77 @@ def ml_grad(obj, probe, data: Data):
     return total, g_o, g_p
 
 
+def ml_line_coeffs(obj, probe, d_obj, d_probe, data: Data):
+    """Derivatives of L(alpha) = L(O + alpha dO, P + alpha dP) at alpha = 0 from the
+    expansion of the far field along the direction (ML line search, Thibault &
+    Guizar-Sicairos 2012):
+      FT((P + a dP)(O + a dO)) = A + a B + a^2 C,
+      A = FT(P O), B = FT(dP O + P dO), C = FT(dP dO);
+      I_c(a) = sum_k |A + a B + a^2 C|^2 = I_c + a dI + a^2 d2I / 2 + O(a^3),
+      dI = 2 sum_k Re(conj(A) B),  d2I = 2 sum_k (|B|^2 + 2 Re(conj(A) C));
+      L'(0) = sum (1 - I_o / I_c) dI,
+      L''(0) = sum [(1 - I_o / I_c) d2I + (I_o / I_c^2) dI^2]   (unmasked pixels).
+    Returns (L'(0), L''(0))."""
+    obj = np.asarray(obj, dtype=np.complex128)
+    probe = np.asarray(probe, dtype=np.complex128)
+    d_obj = np.asarray(d_obj, dtype=np.complex128)
+    d_probe = np.asarray(d_probe, dtype=np.complex128)
+    l1 = l2 = 0.0
+    for lo, hi in _stacks(data.J):
+        pos = data.positions[lo:hi]
+        A = ft(obj_probe_to_psi(obj, probe, pos))
+        B = ft(obj_probe_to_psi(obj, d_probe, pos) + obj_probe_to_psi(d_obj, probe, pos))
+        C = ft(obj_probe_to_psi(d_obj, d_probe, pos))
+        ic = calc_intensity(A)
+        di = 2.0 * (np.conj(A) * B).real.sum(axis=-3)
+        d2i = 2.0 * ((B.real ** 2 + B.imag ** 2) + 2.0 * (np.conj(A) * C).real).sum(axis=-3)
+        io = np.maximum(data.iobs[lo:hi], 0.0)
+        icf = np.maximum(ic, ICALC_FLOOR)
+        w1 = np.where(data.mask, 0.0, 1.0 - io / icf)
+        w2 = np.where(data.mask, 0.0, io / icf ** 2)
+        l1 += float((w1 * di).sum())
+        l2 += float((w1 * d2i + w2 * di ** 2).sum())
+    return l1, l2
+
+
+def _dot(a, b):
+    """Real inner product Re sum conj(a) b of complex arrays."""
+    return float(np.real(np.vdot(a, b)))
+
+
+def ml_cg(obj, probe, data: Data, n, update_obj=True, update_probe=False):
+    """n steps of maximum-likelihood conjugate gradient on the Poisson LLK (the ML
+    operator; Thibault & Guizar-Sicairos 2012; the paper's ML defaults update the
+    object only).  Polak-Ribiere direction with beta = max(0, beta_PR) (0 at the
+    first step); step alpha = -L'(0) / L''(0) from ``ml_line_coeffs`` (no step
+    when L''(0) <= 0).  Returns (obj, probe, [LLK before each step])."""
+    obj = np.asarray(obj, dtype=np.complex128).copy()
+    probe = np.asarray(probe, dtype=np.complex128).copy()
+    g_prev = d = None
+    llks = []
+    for it in range(n):
+        l, go, gp = ml_grad(obj, probe, data)
+        llks.append(l)
+        go = go if update_obj else np.zeros_like(go)
+        gp = gp if update_probe else np.zeros_like(gp)
+        if g_prev is None:
+            beta = 0.0
+        else:
+            den = _dot(g_prev[0], g_prev[0]) + _dot(g_prev[1], g_prev[1])
+            num = _dot(go, go - g_prev[0]) + _dot(gp, gp - g_prev[1])
+            beta = max(0.0, num / den) if den > 0 else 0.0
+        if d is None:
+            d = (-go, -gp)
+        else:
+            d = (-go + beta * d[0], -gp + beta * d[1])
+        l1, l2 = ml_line_coeffs(obj, probe, d[0], d[1], data)
+        alpha = -l1 / l2 if l2 > 0 else 0.0
+        obj = obj + alpha * d[0]
+        probe = probe + alpha * d[1]
+        g_prev = (go, gp)
+    return obj, probe, llks
+
+
 def cycles(algorithm, obj, probe, data: Data, n, psi=None, init_psi=True, **kw):
     """Run ``n`` AP or DM cycles; returns (obj, probe, psi, [llk per cycle])."""
     llks = []
@@ -376,7 +447,7 @@ __all__ = [
     "Data", "ft", "ift", "obj_probe_to_psi", "calc_intensity", "apply_amplitude", "llk_terms",
     "llk_poisson", "psi_to_probe_sums", "psi_to_obj_sums", "psi_to_obj_probe_sums", "inertia_update",
     "normalise", "overlap_update", "ap_cycle", "dm_cycle", "llk", "ml_grad",
-    "cycles", "dm_frame_update", "frames_llk", "object_denominator", "frames_covering",
+    "cycles", "dm_frame_update", "frames_llk", "object_denominator", "frames_covering", "ml_line_coeffs", "ml_cg",
     "ICALC_FLOOR", "AMP_FLOOR", "STACK",
 ]
 

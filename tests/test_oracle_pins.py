@@ -511,3 +511,41 @@ def test_overlap_update_is_probe_then_object():
     n_o, d_o = orc.psi_to_obj_sums(psi, p_exp, pos, obj.shape)
     o_exp = np.where(d_o + 1e-2 * d_o.max() > 0, (n_o + 1e-2 * d_o.max() * obj) / (d_o + 1e-2 * d_o.max()), obj)
     assert rel(p1, p_exp) < 1e-14 and rel(o1, o_exp) < 1e-14
+
+
+# ---------------------------------------------------------------- ML conjugate gradient
+
+def test_ml_line_coeffs_match_gradient_and_finite_differences():
+    """L'(0) of the line expansion equals the directional derivative Re<G, D> of the
+    gradient; L''(0) matches a central second difference of L along D."""
+    s, data, obj, probe = _fd_problem()
+    obj, probe, _ = orc.ap_cycle(obj, probe, data)
+    obj, probe, _ = orc.ap_cycle(obj, probe, data)
+    rng = np.random.default_rng(31)
+    do = 0.01 * crandn(rng, *obj.shape)
+    dp = 0.01 * crandn(rng, *probe.shape)
+    l1, l2 = orc.ml_line_coeffs(obj, probe, do, dp, data)
+    _, go, gp = orc.ml_grad(obj, probe, data)
+    assert abs(l1 - (orc._dot(go, do) + orc._dot(gp, dp))) < 1e-9 * abs(l1)
+    f = lambda a: orc.llk(obj + a * do, probe + a * dp, data)
+    h = 1e-3
+    fd2 = (f(h) - 2 * f(0.0) + f(-h)) / h ** 2
+    assert abs(fd2 - l2) < 1e-4 * abs(l2), (fd2, l2)
+
+
+def test_ml_cg_decreases_llk_and_takes_the_model_step():
+    """CG lowers the LLK every step; its first step is steepest descent with the
+    step that minimises the second-order model a L'(0) + a^2 L''(0) / 2 (whose
+    derivatives are pinned above).  The Poisson LLK is far from quadratic where
+    I_c is small, so the model step undershoots the line minimum but descends."""
+    s, data, obj, probe = _fd_problem()
+    o, p, llks = orc.ml_cg(obj, probe, data, 6)
+    assert all(b < a for a, b in zip(llks[:-1], llks[1:]))
+    _, go, gp = orc.ml_grad(obj, probe, data)
+    l1, l2 = orc.ml_line_coeffs(obj, probe, -go, np.zeros_like(gp), data)
+    a = -l1 / l2
+    assert a > 0 and orc.llk(obj - a * go, probe, data) < orc.llk(obj, probe, data)
+    o1, p1, _ = orc.ml_cg(obj, probe, data, 1)
+    assert rel(o1, obj - a * go) < 1e-12 and rel(p1, probe) == 0.0
+    o2, p2, l2s = orc.ml_cg(obj, probe, data, 3, update_obj=True, update_probe=True)
+    assert l2s[-1] < l2s[0]
