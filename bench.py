@@ -237,6 +237,8 @@ def run_ours(args):
     pb = Ptycho(obj, probe, iobs, s.positions, s.mask, with_psi=True)
     if args.lanes:
         pb.set_param("lanes", args.lanes)
+    if args.batch_frames:
+        pb.set_param("batch_frames", args.batch_frames)
     stream = torch.cuda.current_stream(dev)
     llk_buf = torch.empty(max(args.steps, args.warmup, 1), dtype=torch.float64, device=dev)
 
@@ -370,6 +372,8 @@ def main():
                     help="use only the first FRAMES frames of the workload (small cases for profiling)")
     ap.add_argument("--lanes", type=int, default=0,
                     help="batches in flight per cycle (library default when 0)")
+    ap.add_argument("--batch-frames", type=int, default=0,
+                    help="upper bound on frames per batch (library default when 0)")
     ap.add_argument("--timing-only", action="store_true",
                     help="stop after the timed region (no per-kernel pass, e2e or CPU baseline)")
     args = ap.parse_args()

@@ -146,6 +146,32 @@ ptx_status ptx_llk(ptx_handle* h, double* llk_dev, void* stream);
  * llk_dev (may be NULL) receives the LLK.  Psi is recomputed, never stored. */
 ptx_status ptx_ml_grad(ptx_handle* h, void* grad_obj, void* grad_probe, double* llk_dev, void* stream);
 
+/* Flag of ptx_ml_cycles: forget the previous gradient and direction first
+ * (the next step is steepest descent). */
+#define PTX_ML_RESTART 0x20u
+
+/* Maximum-likelihood conjugate-gradient cycles on the Poisson LLK (the ML
+ * operator; Thibault & Guizar-Sicairos 2012): per cycle the gradient G of
+ * ptx_ml_grad (object and/or probe by PTX_UPDATE_OBJ / PTX_UPDATE_PROBE; the
+ * paper's ML default updates the object only), the Polak-Ribiere direction
+ * D <- -G + beta D with beta = max(0, (<G,G> - <G,Gp>) / <Gp,Gp>) (0 without a
+ * previous gradient Gp; <a,b> = Re sum conj(a) b over object and probe), and the
+ * step O += alpha D_O, P += alpha D_P with alpha = -L'(0) / L''(0) from the
+ * expansion of the far field along the line (ptx_ml_line_coeffs), no step if
+ * L''(0) <= 0.  The CG state lives in the handle's scratch and carries over
+ * between calls.  llk_dev (may be NULL): device double [ncycles], the LLK before
+ * each step.  nprob must be 1.  Runs entirely on the device (no host sync). */
+ptx_status ptx_ml_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, double* llk_dev, void* stream);
+
+/* Line-search coefficients of the ML step along (d_obj, d_probe) (device
+ * complex64 [Ho][Wo] and [K][N][N]; either may be NULL = zero): with
+ * FT((P + a dP)(O + a dO)) = A + a B + a^2 C, A = FT(P O), B = FT(dP O + P dO),
+ * C = FT(dP dO), coeffs_dev[0] = L'(0) = sum (1 - I_o/I_c) dI and coeffs_dev[1] =
+ * L''(0) = sum [(1 - I_o/I_c) d2I + (I_o/I_c^2) dI^2] over unmasked pixels, where
+ * dI = 2 sum_k Re(conj(A) B) and d2I = 2 sum_k (|B|^2 + 2 Re(conj(A) C)).  FP64. */
+ptx_status ptx_ml_line_coeffs(ptx_handle* h, const void* d_obj, const void* d_probe, double* coeffs_dev,
+                              void* stream);
+
 /* Stages of the second half of Psi2ObjProbe, for ptx_normalise. */
 #define PTX_STAGE_PROBE         0x100u /* P <- (N_P + d_P P) / (D_P + d_P) from the probe accumulator, cleared */
 #define PTX_STAGE_OBJ_GATHER    0x200u /* object accumulator <- N_O, D_O of this handle's frames, from the

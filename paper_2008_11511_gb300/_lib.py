@@ -28,6 +28,7 @@ PTX_UPDATE_PROBE = 0x2
 PTX_DM_INIT_PSI = 0x4
 PTX_NO_NORMALISE = 0x8
 PTX_NO_GRAPH = 0x10
+PTX_ML_RESTART = 0x20
 PTX_MAX_MODES = 8
 PTX_ALGO_AP = 0
 PTX_ALGO_DM = 1
@@ -36,6 +37,7 @@ SUPPORTED_SIZES = (8, 12, 16, 32, 64, 128, 192, 256, 384, 512)
 # Every symbol include/ptycho.h declares.
 EXPORTS = (
     "ptx_workspace_bytes", "ptx_create", "ptx_ap_cycles", "ptx_dm_cycles", "ptx_cycles", "ptx_llk", "ptx_ml_grad",
+    "ptx_ml_cycles", "ptx_ml_line_coeffs",
     "ptx_normalise", "ptx_accumulators", "ptx_set_param", "ptx_fft2", "ptx_profile_enable", "ptx_profile_read",
     "ptx_llk_static", "ptx_last_error", "ptx_destroy",
 )
@@ -96,6 +98,8 @@ def load(path: str | None = None):
         "ptx_cycles": (st, [vp, i32, u32, vp, vp, vp]),
         "ptx_llk": (st, [vp, vp, vp]),
         "ptx_ml_grad": (st, [vp, vp, vp, vp, vp]),
+        "ptx_ml_cycles": (st, [vp, i32, u32, vp, vp]),
+        "ptx_ml_line_coeffs": (st, [vp, vp, vp, vp, vp]),
         "ptx_normalise": (st, [vp, u32, vp]),
         "ptx_accumulators": (st, [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(sz), ctypes.POINTER(vp),
                                   ctypes.POINTER(sz)]),

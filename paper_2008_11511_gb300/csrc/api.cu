@@ -110,6 +110,7 @@ constexpr int kMaxLanes = 4;
 
 struct Layout {
     size_t pos, mask, acc_obj, acc_probe, llk_part, maxbits, tile_ids, tile_ptr, tile_frames;
+    size_t cg_obj, cg_probe, ls_part, cg;  // ML conjugate-gradient state
     size_t end;
 };
 
@@ -257,6 +258,15 @@ size_t layout_problem(ProbHost& h) {
     o = align_up(o + sizeof(int) * h.tile_ptr.size());
     h.lay.tile_frames = o;
     o = align_up(o + sizeof(int) * h.tile_frames.size());
+    // CG: gradient, previous gradient and direction of object and probe
+    h.lay.cg_obj = o;
+    o = align_up(o + 3 * sizeof(float2) * (size_t)p.Ho * p.Wo);
+    h.lay.cg_probe = o;
+    o = align_up(o + 3 * sizeof(float2) * (size_t)p.K * p.N * p.N);
+    h.lay.ls_part = o;
+    o = align_up(o + 2 * sizeof(double) * (size_t)p.J * (p.N / h.ks->ls_lines));
+    h.lay.cg = o;
+    o = align_up(o + 8 * sizeof(double));
     h.lay.end = o;
     return o;
 }
@@ -316,6 +326,10 @@ ptx_status compute_layout(std::vector<ProbHost>& probs, size_t* spec_off, size_t
         h.lay.tile_ids += o;
         h.lay.tile_ptr += o;
         h.lay.tile_frames += o;
+        h.lay.cg_obj += o;
+        h.lay.cg_probe += o;
+        h.lay.ls_part += o;
+        h.lay.cg += o;
         h.lay.end += o;
         o += sz;
         size_t s = (size_t)h.B * kDefaultLanes * h.p.K * h.p.N * h.p.N * sizeof(float2);
@@ -353,6 +367,9 @@ void fill_args(ptx_handle* h, ProbHost& ph) {
     a.L1 = ph.L1;
     a.C2 = ph.C2;
     a.L3 = ph.L3;
+    a.dir_obj = nullptr;
+    a.dir_probe = nullptr;
+    a.ls_part = (double*)(h->scratch + ph.lay.ls_part);
     ph.tiles.tile_ids = (const int*)(h->scratch + ph.lay.tile_ids);
     ph.tiles.tile_ptr = (const int*)(h->scratch + ph.lay.tile_ptr);
     ph.tiles.tile_frames = (const int*)(h->scratch + ph.lay.tile_frames);
@@ -736,6 +753,122 @@ ptx_status ptx_ml_grad(ptx_handle* h, void* grad_obj, void* grad_probe, double* 
     if (llk_dev) k_llk_reduce<<<1, 1024, 0, s>>>(a, a.N / a.C2, llk_dev);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "ptx_ml_grad launch");
+    return PTX_OK;
+}
+
+namespace {
+
+CgArgs cg_args(ptx_handle* h, ProbHost& ph) {
+    CgArgs c;
+    const size_t no = (size_t)ph.p.Ho * ph.p.Wo, npr = (size_t)ph.p.K * ph.p.N * ph.p.N;
+    float2* o = (float2*)(h->scratch + ph.lay.cg_obj);
+    float2* pr = (float2*)(h->scratch + ph.lay.cg_probe);
+    c.g_obj = o;
+    c.gp_obj = o + no;
+    c.d_obj = o + 2 * no;
+    c.g_probe = pr;
+    c.gp_probe = pr + npr;
+    c.d_probe = pr + 2 * npr;
+    c.n_obj = no;
+    c.n_probe = npr;
+    c.cg = (double*)(h->scratch + ph.lay.cg);
+    return c;
+}
+
+// Line-search pass: L'(0), L''(0) along (dir_obj, dir_probe) into out[0..1].
+ptx_status enqueue_line_coeffs(ptx_handle* h, ProbHost& ph, const float2* d_obj, const float2* d_probe, double* out,
+                               cudaStream_t s) {
+    ProbArgs a = ph.args;
+    a.dir_obj = d_obj;
+    a.dir_probe = d_probe;
+    const size_t frame3 = 3 * (size_t)ph.p.K * ph.p.N * ph.p.N * sizeof(float2);
+    size_t B = h->spec_bytes / frame3;
+    if (B < 1) B = 1;
+    if (B > (size_t)ph.p.J) B = ph.p.J;
+    if (B > 32768) B = 32768;
+    for (int j0 = 0; j0 < ph.p.J; j0 += (int)B) {
+        const int nb = std::min((int)B, ph.p.J - j0);
+        ph.ks->row_fwd_ls(a, j0, nb, 0, s);
+        ph.ks->col_ls(a, j0, nb, 0, s);
+    }
+    k_ls_reduce<<<1, 1024, 0, s>>>(a.ls_part, (size_t)ph.p.J * (ph.p.N / ph.ks->ls_lines), out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "line-search launch");
+    return PTX_OK;
+}
+
+// Gradient of the LLK into (g_obj, g_probe) (each may be null), LLK into llk_out.
+ptx_status enqueue_grad(ptx_handle* h, ProbHost& ph, float2* g_obj, float2* g_probe, double* llk_out, cudaStream_t s) {
+    ProbArgs a = ph.args;
+    a.grad_obj = g_obj;
+    a.grad_probe = g_probe;
+    cudaError_t e = cudaSuccess;
+    if (g_obj) e = cudaMemsetAsync(g_obj, 0, sizeof(float2) * (size_t)a.Ho * a.Wo, s);
+    if (e == cudaSuccess && g_probe) e = cudaMemsetAsync(g_probe, 0, sizeof(float2) * (size_t)a.K * a.N * a.N, s);
+    if (e != cudaSuccess) return cuda_fail(e, "gradient memset");
+    set_batch(ph, h->spec_bytes, 1, h->batch_cap);
+    for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
+        const int nb = std::min(ph.B, ph.p.J - j0);
+        ph.ks->row_fwd(a, j0, nb, X_PHI, s);
+        ph.ks->col(a, j0, nb, COL_GRAD, s);
+        if (g_obj || g_probe)
+            ph.ks->row_bwd(a, j0, nb, std::min(ph.G3, nb), BWD_GRAD, g_obj != nullptr, g_probe != nullptr, s);
+    }
+    if (llk_out) k_llk_reduce<<<1, 1024, 0, s>>>(a, a.N / a.C2, llk_out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "gradient launch");
+    return PTX_OK;
+}
+
+}  // namespace
+
+ptx_status ptx_ml_line_coeffs(ptx_handle* h, const void* d_obj, const void* d_probe, double* coeffs_dev,
+                              void* stream) {
+    if (!h || !coeffs_dev) return fail(PTX_ERR_INVALID_ARG, "null handle or coeffs_dev");
+    if (h->probs.size() != 1) return fail(PTX_ERR_INVALID_ARG, "ML needs a single-problem handle");
+    ptx_status st = check_device(h);
+    if (st != PTX_OK) return st;
+    return enqueue_line_coeffs(h, h->probs[0], (const float2*)d_obj, (const float2*)d_probe, coeffs_dev,
+                               (cudaStream_t)stream);
+}
+
+ptx_status ptx_ml_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, double* llk_dev, void* stream) {
+    if (!h) return fail(PTX_ERR_INVALID_ARG, "null handle");
+    if (h->probs.size() != 1) return fail(PTX_ERR_INVALID_ARG, "ML needs a single-problem handle");
+    if (ncycles < 0) return fail(PTX_ERR_INVALID_ARG, "ncycles=%d must be >= 0", ncycles);
+    const uint32_t known = PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_ML_RESTART;
+    if (flags & ~known) return fail(PTX_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags & ~known);
+    ptx_status st = check_device(h);
+    if (st != PTX_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    ProbHost& ph = h->probs[0];
+    CgArgs c = cg_args(h, ph);
+    const bool uo = flags & PTX_UPDATE_OBJ, up = flags & PTX_UPDATE_PROBE;
+    cudaError_t e = cudaSuccess;
+    if (flags & PTX_ML_RESTART) {
+        e = cudaMemsetAsync(c.gp_obj, 0, 2 * sizeof(float2) * c.n_obj, s);  // previous gradient and direction
+        if (e == cudaSuccess) e = cudaMemsetAsync(c.gp_probe, 0, 2 * sizeof(float2) * c.n_probe, s);
+        if (e != cudaSuccess) return cuda_fail(e, "ML restart memset");
+    }
+    const int nblk = 4 * 152;
+    for (int cyc = 0; cyc < ncycles; ++cyc) {
+        // gradient (zero where a part is not updated) and the LLK before the step
+        if (!uo && (e = cudaMemsetAsync(c.g_obj, 0, sizeof(float2) * c.n_obj, s)) != cudaSuccess)
+            return cuda_fail(e, "memset");
+        if (!up && (e = cudaMemsetAsync(c.g_probe, 0, sizeof(float2) * c.n_probe, s)) != cudaSuccess)
+            return cuda_fail(e, "memset");
+        if ((st = enqueue_grad(h, ph, uo ? c.g_obj : nullptr, up ? c.g_probe : nullptr, llk_dev ? llk_dev + cyc : nullptr,
+                               s)) != PTX_OK)
+            return st;
+        if ((e = cudaMemsetAsync(c.cg, 0, 8 * sizeof(double), s)) != cudaSuccess) return cuda_fail(e, "memset");
+        k_cg_dots<<<nblk, 256, 0, s>>>(c);
+        k_cg_direction<<<nblk, 256, 0, s>>>(c);
+        if ((st = enqueue_line_coeffs(h, ph, uo ? c.d_obj : nullptr, up ? c.d_probe : nullptr, c.cg + 3, s)) != PTX_OK)
+            return st;
+        k_cg_step<<<nblk, 256, 0, s>>>(c, ph.args.obj, ph.args.probe);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ML cycle launch");
     return PTX_OK;
 }
 

@@ -170,3 +170,103 @@ __global__ void k_set_ctl(Ctl* ctl, double* llk_out, int nprob) {
 }
 
 }  // namespace ptx
+
+namespace ptx {
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// <G,G>, <G,Gp>, <Gp,Gp> over the object and probe parts (FP64 partials, one
+// atomic per warp; cg[0..2] must be zero on entry).
+__global__ void k_cg_dots(CgArgs c) {
+    double gg = 0.0, ggp = 0.0, gpgp = 0.0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t tot = c.n_obj + c.n_probe;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += stride) {
+        const bool o = i < c.n_obj;
+        const size_t k = o ? i : i - c.n_obj;
+        const float2 g = o ? c.g_obj[k] : c.g_probe[k];
+        const float2 q = o ? c.gp_obj[k] : c.gp_probe[k];
+        gg += (double)g.x * g.x + (double)g.y * g.y;
+        ggp += (double)g.x * q.x + (double)g.y * q.y;
+        gpgp += (double)q.x * q.x + (double)q.y * q.y;
+    }
+    gg = warp_sum_d(gg);
+    ggp = warp_sum_d(ggp);
+    gpgp = warp_sum_d(gpgp);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(c.cg + 0, gg);
+        atomicAdd(c.cg + 1, ggp);
+        atomicAdd(c.cg + 2, gpgp);
+    }
+}
+
+// Polak-Ribiere: beta = max(0, (<G,G> - <G,Gp>) / <Gp,Gp>) (0 without a previous
+// gradient); D <- -G + beta D; Gp <- G.
+__global__ void k_cg_direction(CgArgs c) {
+    const double den = c.cg[2];
+    const double beta = den > 0.0 ? fmax(0.0, (c.cg[0] - c.cg[1]) / den) : 0.0;
+    const float b = (float)beta;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t tot = c.n_obj + c.n_probe;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += stride) {
+        const bool o = i < c.n_obj;
+        const size_t k = o ? i : i - c.n_obj;
+        float2* g = o ? c.g_obj + k : c.g_probe + k;
+        float2* gp = o ? c.gp_obj + k : c.gp_probe + k;
+        float2* d = o ? c.d_obj + k : c.d_probe + k;
+        const float2 gv = *g;
+        const float2 dv = *d;
+        *d = make_float2(fmaf(b, dv.x, -gv.x), fmaf(b, dv.y, -gv.y));
+        *gp = gv;
+    }
+}
+
+// alpha = -L'(0) / L''(0) (0 when L''(0) <= 0); O += alpha D_O, P += alpha D_P.
+__global__ void k_cg_step(CgArgs c, float2* obj, float2* probe) {
+    const double l1 = c.cg[3], l2 = c.cg[4];
+    const float alpha = l2 > 0.0 ? (float)(-l1 / l2) : 0.f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) c.cg[5] = l2 > 0.0 ? -l1 / l2 : 0.0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t tot = c.n_obj + c.n_probe;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += stride) {
+        const bool o = i < c.n_obj;
+        const size_t k = o ? i : i - c.n_obj;
+        float2* z = o ? obj + k : probe + k;
+        const float2 d = o ? c.d_obj[k] : c.d_probe[k];
+        const float2 v = *z;
+        *z = make_float2(fmaf(alpha, d.x, v.x), fmaf(alpha, d.y, v.y));
+    }
+}
+
+// Sum of the line-search partials (pairs) in a fixed order: out[0] = L'(0), out[1] = L''(0).
+__global__ void k_ls_reduce(const double* part, size_t nparts, double* out) {
+    __shared__ double red[2][32];
+    double a = 0.0, b = 0.0;
+    for (size_t i = threadIdx.x; i < nparts; i += blockDim.x) {
+        a += part[2 * i];
+        b += part[2 * i + 1];
+    }
+    a = warp_sum_d(a);
+    b = warp_sum_d(b);
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = a;
+        red[1][threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        a = threadIdx.x < (blockDim.x >> 5) ? red[0][threadIdx.x] : 0.0;
+        b = threadIdx.x < (blockDim.x >> 5) ? red[1][threadIdx.x] : 0.0;
+        a = warp_sum_d(a);
+        b = warp_sum_d(b);
+        if (threadIdx.x == 0) {
+            out[0] = a;
+            out[1] = b;
+        }
+    }
+}
+
+}  // namespace ptx

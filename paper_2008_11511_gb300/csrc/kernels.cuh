@@ -45,6 +45,9 @@ struct ProbArgs {
     unsigned* maxbits;      // [2] max D_O, max D_P (float bits; values >= 0)
     float2* grad_obj;       // [Ho][Wo] (ML gradient) or null
     float2* grad_probe;     // [K][N][N] or null
+    const float2* dir_obj;  // [Ho][Wo] ML search direction (line-search pass) or null
+    const float2* dir_probe;  // [K][N][N] or null
+    double* ls_part;        // [J][ncolblk][2] line-search partial sums
     int L1, C2, L3;         // rows per row_fwd block, columns per col block, rows per row_bwd block
 };
 
@@ -55,6 +58,37 @@ struct Ctl {
     int err;
     int pad;
 };
+
+// L2 eviction-priority policies (createpolicy) and loads / stores carrying them.
+// The Fourier work stack of a batch is written and re-read by the three passes
+// and must stay in L2; everything touched once (exit waves read or written,
+// intensities, the stack's last read) is marked evict-first so it does not push
+// the stack out.
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ float2 ld_hint(const float2* ptr, uint64_t pol) {
+    float2 v;
+    asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_hint(float2* ptr, float2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(ptr), "f"(v.x), "f"(v.y), "l"(pol)
+                 : "memory");
+}
+// 16-byte cp.async with an L2 policy
+__device__ __forceinline__ void cp_async16_hint(void* smem_dst, const void* gmem_src, uint64_t pol) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem_src), "l"(pol)
+                 : "memory");
+}
 
 // Asynchronous 16-byte global -> shared copy (cp.async, bypassing L1).
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
@@ -363,6 +397,119 @@ __global__ void __launch_bounds__(kThreads) k_row_bwd(ProbArgs a, int j0, int nb
 }
 
 // ---------------------------------------------------------------------------
+// ML line search.  For a search direction (dO, dP) the far field along the line
+// is FT((P + a dP)(O + a dO)) = A + a B + a^2 C with A = FT(P O),
+// B = FT(dP O + P dO), C = FT(dP dO).  k_row_fwd_ls writes the row transforms of
+// the three waves of every mode (3K lines per frame row: A modes, B modes, C
+// modes) and k_col_ls finishes the column transforms and reduces
+//   L'(0)  = sum (1 - I_o/I_c) dI,  L''(0) = sum [(1 - I_o/I_c) d2I + (I_o/I_c^2) dI^2]
+// with dI = 2 sum_k Re(conj(A) B), d2I = 2 sum_k (|B|^2 + 2 Re(conj(A) C)), in FP64.
+// grid (N / L, frames in batch); L rows (columns) of 3K lines per block.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_row_fwd_ls(ProbArgs a, int j0, int L) {
+    constexpr int P = line_pitch<N>();
+    extern __shared__ __align__(16) float2 sm[];
+    float2* tw = sm;
+    float2* buf = sm + N;
+    const int K = a.K, K3 = 3 * a.K;
+    const int y0 = blockIdx.x * L;
+    const int b = blockIdx.y;
+    const int2 p = a.pos[j0 + b];
+    load_twiddles<N>(tw);
+    const int nel = 3 * L * N;  // one mode at a time: lines (part, row)
+    for (int k = 0; k < K; ++k) {
+        for (int e = threadIdx.x; e < nel; e += kThreads) {
+            const int x = e % N;
+            const int line = e / N;
+            const int part = line / L, r = line - part * L;
+            const int y = y0 + r;
+            const size_t pidx = ((size_t)k * N + y) * N + x;
+            const size_t oidx = (size_t)(p.x + y) * a.Wo + (p.y + x);
+            const float2 pr = a.probe[pidx], ob = a.obj[oidx];
+            const float2 dp = a.dir_probe ? a.dir_probe[pidx] : make_float2(0.f, 0.f);
+            const float2 dob = a.dir_obj ? a.dir_obj[oidx] : make_float2(0.f, 0.f);
+            float2 v;
+            if (part == 0)
+                v = cmul(pr, ob);
+            else if (part == 1)
+                v = cadd(cmul(dp, ob), cmul(pr, dob));
+            else
+                v = cmul(dp, dob);
+            buf[line * P + x] = v;
+        }
+        __syncthreads();
+        fft_lines<N, -1, kThreads, max_lines<N>()>(buf, 3 * L, tw);
+        for (int e = threadIdx.x; e < nel; e += kThreads) {
+            const int x = e % N;
+            const int line = e / N;
+            const int part = line / L, r = line - part * L;
+            a.spec[(((size_t)b * K3 + part * K + k) * N + y0 + r) * N + x] = buf[line * P + x];
+        }
+        __syncthreads();
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_col_ls(ProbArgs a, int j0, int C) {
+    constexpr int P = line_pitch<N>();
+    extern __shared__ __align__(16) float2 sm[];
+    __shared__ double red_s[kThreads / 32];
+    float2* tw = sm;
+    float2* buf = sm + N;                        // [3][C] lines of one mode
+    float* acc = (float*)(buf + 3 * C * P);      // [3][N * C]: I_c, dI, d2I summed over modes
+    const int K = a.K, K3 = 3 * a.K;
+    const int x0 = blockIdx.x * C;
+    const int b = blockIdx.y;
+    const int j = j0 + b;
+    load_twiddles<N>(tw);
+    for (int e = threadIdx.x; e < 3 * N * C; e += kThreads) acc[e] = 0.f;
+    const int nel = 3 * N * C;
+    for (int k = 0; k < K; ++k) {
+        for (int e = threadIdx.x; e < nel; e += kThreads) {
+            const int c = e % C;
+            const int t = e / C;
+            const int n = t % N, part = t / N;
+            buf[(part * C + c) * P + n] = a.spec[(((size_t)b * K3 + part * K + k) * N + n) * N + x0 + c];
+        }
+        __syncthreads();
+        fft_lines<N, -1, kThreads, max_lines<N>()>(buf, 3 * C, tw);
+        for (int e = threadIdx.x; e < N * C; e += kThreads) {
+            const int c = e % C, n = e / C;
+            const float2 A = buf[c * P + n];
+            const float2 B = buf[(C + c) * P + n];
+            const float2 Cc = buf[(2 * C + c) * P + n];
+            acc[e] += cnorm(A);
+            acc[N * C + e] += 2.f * (A.x * B.x + A.y * B.y);
+            acc[2 * N * C + e] += 2.f * (cnorm(B) + 2.f * (A.x * Cc.x + A.y * Cc.y));
+        }
+        __syncthreads();
+    }
+    constexpr float invN2 = 1.0f / float(N * N);
+    double l1 = 0.0, l2 = 0.0;
+    const float* io_row = a.iobs + (size_t)j * N * N;
+    for (int e = threadIdx.x; e < N * C; e += kThreads) {
+        const int c = e % C, n = e / C;
+        if (a.mask[n * N + x0 + c]) continue;
+        const float ic = acc[e] * invN2, di = acc[N * C + e] * invN2, d2i = acc[2 * N * C + e] * invN2;
+        const float io = fmaxf(io_row[n * N + x0 + c], 0.f);
+        const float icf = fmaxf(ic, 1e-30f);
+        const double w1 = 1.0 - (double)io / (double)icf;
+        const double w2 = (double)io / ((double)icf * (double)icf);
+        l1 += w1 * (double)di;
+        l2 += w1 * (double)d2i + w2 * (double)di * (double)di;
+    }
+    const double t1 = block_sum_double<kThreads>(l1, red_s);
+    __syncthreads();
+    const double t2 = block_sum_double<kThreads>(l2, red_s);
+    if (threadIdx.x == 0) {
+        double* out = a.ls_part + 2 * ((size_t)j * gridDim.x + blockIdx.x);
+        out[0] = t1;
+        out[1] = t2;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Normalisation (Psi2ObjProbe second half) and reductions.
 // ---------------------------------------------------------------------------
 // Object tiles of the gather: kObjTile x kObjTile pixels, one block each.
@@ -379,6 +526,23 @@ __global__ void k_normalise(ProbArgs a, float alpha_obj, float alpha_probe, int 
 __global__ void k_llk_reduce(ProbArgs a, int nparts_per_frame, double* out);
 __global__ void k_cycle_end(Ctl* ctl, ProbArgs a, int p, int nparts_per_frame, int last_problem);
 __global__ void k_set_ctl(Ctl* ctl, double* llk_out, int nprob);
+
+// ML conjugate-gradient vector steps.  cg[0..2] receive <G,G>, <G,Gp>, <Gp,Gp>
+// (Re sum conj(a) b over object and probe), cg[3..4] the line-search L'(0), L''(0).
+struct CgArgs {
+    float2* g_obj;
+    float2* g_probe;
+    float2* gp_obj;   // previous gradient
+    float2* gp_probe;
+    float2* d_obj;    // search direction
+    float2* d_probe;
+    size_t n_obj, n_probe;
+    double* cg;       // [8] device scalars
+};
+__global__ void k_cg_dots(CgArgs c);
+__global__ void k_cg_direction(CgArgs c);
+__global__ void k_cg_step(CgArgs c, float2* obj, float2* probe);
+__global__ void k_ls_reduce(const double* part, size_t nparts, double* out);
 
 // ---------------------------------------------------------------------------
 // Plain orthonormal 2D FFT of frames in place (FT / IFT operators).
@@ -427,7 +591,10 @@ struct KernelSet {
     void (*col)(const ProbArgs&, int j0, int nb, int mode, cudaStream_t);
     void (*row_bwd)(const ProbArgs&, int j0, int nb, int G, int mode, int upd_obj, int upd_probe, cudaStream_t);
     void (*fft2)(float2* data, int nframes, int dir, cudaStream_t);
+    void (*row_fwd_ls)(const ProbArgs&, int j0, int nb, int unused, cudaStream_t);
+    void (*col_ls)(const ProbArgs&, int j0, int nb, int unused, cudaStream_t);
     int max_lines;  // lines per block of the shared-memory kernels
+    int ls_lines;   // rows / columns per block of the line-search kernels
     int reg_lines;  // lines per block of the register kernels (0: none for this N)
     int R, M;
 };
@@ -488,6 +655,26 @@ void launch_row_bwd(const ProbArgs& a, int j0, int nb, int G, int mode, int upd_
     dim3 grid(N / a.L3, G);
     k_row_bwd<N><<<grid, kThreads, smem_row_bwd_t<N>(a.K, a.L3), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
 }
+// Lines per block of the line-search kernels: 3 waves x L rows (columns) <= max_lines.
+template <int N>
+constexpr int ls_lines() {
+    int L = 1;
+    while (3 * L * 2 <= max_lines<N>() && N % (L * 2) == 0) L *= 2;
+    return L;
+}
+template <int N>
+void launch_row_fwd_ls(const ProbArgs& a, int j0, int nb, int, cudaStream_t s) {
+    constexpr int L = ls_lines<N>();
+    dim3 grid(N / L, nb);
+    k_row_fwd_ls<N><<<grid, kThreads, sizeof(float2) * (N + (size_t)3 * L * line_pitch<N>()), s>>>(a, j0, L);
+}
+template <int N>
+void launch_col_ls(const ProbArgs& a, int j0, int nb, int, cudaStream_t s) {
+    constexpr int C = ls_lines<N>();
+    dim3 grid(N / C, nb);
+    const size_t sm = sizeof(float2) * (N + (size_t)3 * C * line_pitch<N>()) + sizeof(float) * 3 * (size_t)N * C;
+    k_col_ls<N><<<grid, kThreads, sm, s>>>(a, j0, C);
+}
 template <int N>
 void launch_fft2(float2* data, int nframes, int dir, cudaStream_t s) {
     constexpr int ml = max_lines<N>();
@@ -515,6 +702,8 @@ cudaError_t set_attrs_t() {
     if ((e = cudaFuncSetAttribute(k_fft_rows<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_fft_cols<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_fft_cols<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_fwd_ls<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_ls<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if constexpr (has_reg<N>()) {
         if ((e = set_attrs_r<N>())) return e;
     }
@@ -529,7 +718,10 @@ const KernelSet* make_kernel_set() {
                                  &launch_col<N>,
                                  &launch_row_bwd<N>,
                                  &launch_fft2<N>,
+                                 &launch_row_fwd_ls<N>,
+                                 &launch_col_ls<N>,
                                  max_lines<N>(),
+                                 ls_lines<N>(),
                                  rl,
                                  Plan<N>::R,
                                  Plan<N>::M};

@@ -80,9 +80,10 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_r(
             for (int n2 = 0; n2 < R; ++n2) v[n2] = cmul(__ldg(pr + M * n2), ob[M * n2]);
             if (mode == X_DM) {
                 const float2* ps = a.psi + ((size_t)j * N + y) * N + n1;
+                const uint64_t ef = policy_evict_first();
 #pragma unroll
                 for (int n2 = 0; n2 < R; ++n2) {
-                    const float2 q = __ldcs(ps + M * n2);
+                    const float2 q = ld_hint(ps + M * n2, ef);
                     v[n2] = make_float2(2.f * v[n2].x - q.x, 2.f * v[n2].y - q.y);
                 }
             }
@@ -105,8 +106,9 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_r(
             for (int n1 = 0; n1 < M; ++n1) u[n1] = src[n1];
             Dft<M, -1>::run(u);
             float2* dst = a.spec + ((size_t)b * N + y0 + line) * N + k2;
+            const uint64_t el = policy_evict_last();
 #pragma unroll
-            for (int k1 = 0; k1 < M; ++k1) dst[R * k1] = u[k1];
+            for (int k1 = 0; k1 < M; ++k1) st_hint(dst + R * k1, u[k1], el);
         }
     }
 }
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_col_r(Prob
         constexpr int CH = C * 4 / 16;  // 16-byte chunks per row of intensities
         for (int e = threadIdx.x; e < N * CH; e += kThreads) {
             const int row = e / CH, q = e - row * CH;
-            cp_async16(io_s + row * C + 4 * q, io_g + (size_t)row * N + 4 * q);
+            cp_async16_hint(io_s + row * C + 4 * q, io_g + (size_t)row * N + 4 * q, policy_evict_first());
         }
         if constexpr (C >= 16) {
             constexpr int MC = C / 16;  // 16-byte chunks per row of mask
@@ -160,8 +162,9 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_col_r(Prob
         if (w < C * M) {
             const int n1 = w / C, c = w - n1 * C;
             float2 v[R];
+            const uint64_t el = policy_evict_last();
 #pragma unroll
-            for (int n2 = 0; n2 < R; ++n2) v[n2] = spec[(size_t)(n1 + M * n2) * N + c];
+            for (int n2 = 0; n2 < R; ++n2) v[n2] = ld_hint(spec + (size_t)(n1 + M * n2) * N + c, el);
             Dft<R, -1>::run(v);
             float2* o = buf + c * P + n1;
             o[0] = v[0];
@@ -236,8 +239,9 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_col_r(Prob
 #pragma unroll
             for (int n = 0; n < R; ++n) v[n] = src[n];
             Dft<R, +1>::run(v);
+            const uint64_t el = policy_evict_last();
 #pragma unroll
-            for (int k1 = 0; k1 < R; ++k1) spec[(size_t)(kk + M * k1) * N + c] = v[k1];
+            for (int k1 = 0; k1 < R; ++k1) st_hint(spec + (size_t)(kk + M * k1) * N + c, v[k1], el);
         }
     }
 }
@@ -274,7 +278,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
     // after the update that reads it, so the two are refilled at different points.
     auto prefetch_spec = [&](int b) {
         const float2* src = a.spec + ((size_t)b * N + y0) * N;
-        for (int e = threadIdx.x; e < L * N / 2; e += kThreads) cp_async16(stage + 2 * e, src + 2 * e);
+        const uint64_t ef = policy_evict_first();  // the stack's last read
+        for (int e = threadIdx.x; e < L * N / 2; e += kThreads) cp_async16_hint(stage + 2 * e, src + 2 * e, ef);
         cp_async_commit();
     };
     auto prefetch_obj = [&](int b) {
@@ -360,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
                         }
                     } else {
                         wv = cadd(cmul(prv, obv), u[k1]);
-                        ps[R * k1] = wv;
+                        __stcs(ps + R * k1, wv);
                     }
                     if (acc_p) {
                         const float2 t = cconjmul(obv, wv);

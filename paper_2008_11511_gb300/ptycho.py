@@ -164,6 +164,31 @@ class Ptycho:
                       _stream_ptr(self.device))
         return out[0], go, gp
 
+    def ml(self, ncycles: int, update_obj: bool = True, update_probe: bool = False, restart: bool = False,
+           llk: torch.Tensor | None = None) -> torch.Tensor:
+        """``ncycles`` maximum-likelihood conjugate-gradient steps (the ML operator;
+        by default the object only, as the paper's ML defaults).  Returns the LLK
+        before each step (float64 CUDA tensor).  ``restart`` forgets the previous
+        direction."""
+        f = self._flags(update_obj, update_probe, True)
+        if restart:
+            f |= _lib.PTX_ML_RESTART
+        out = llk if llk is not None else torch.empty(max(ncycles, 1), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            _lib.call("ptx_ml_cycles", self._handle(), int(ncycles), f, ctypes.c_void_p(out.data_ptr()),
+                      _stream_ptr(self.device))
+        return out[:ncycles]
+
+    def line_coeffs(self, d_obj: torch.Tensor | None, d_probe: torch.Tensor | None) -> torch.Tensor:
+        """(L'(0), L''(0)) of the LLK along the direction (d_obj, d_probe)."""
+        out = torch.empty(2, dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            _lib.call("ptx_ml_line_coeffs", self._handle(),
+                      ctypes.c_void_p(d_obj.data_ptr() if d_obj is not None else None),
+                      ctypes.c_void_p(d_probe.data_ptr() if d_probe is not None else None),
+                      ctypes.c_void_p(out.data_ptr()), _stream_ptr(self.device))
+        return out
+
     def normalise(self, update_obj: bool = True, update_probe: bool = True, stages: int | None = None):
         """Second half of Psi2ObjProbe after cycles run with ``normalise=False``:
         the probe from its accumulator, then the object gathered from Psi' with

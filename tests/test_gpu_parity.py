@@ -550,3 +550,39 @@ def test_full_size_dm256_cycle_in_bench_configuration():
     _compare_cycle_state(s, pb, o, p, TOL1, psi_ref=psi)
     assert abs(llk[0] - l) / abs(l) < TOL1
     pb.close()
+
+
+
+# ------------------------------------------------------------------ ML conjugate gradient
+
+@pytest.mark.parametrize("cfg,J", [("ml32fd", 16), ("ml256", 60)])
+def test_ml_line_coeffs_parity(cfg, J):
+    s, obj, probe = warm(cfg, J=J, n_ap=3)
+    pb = gpu_problem(s, with_psi=False, obj=obj, probe=probe)
+    _, go, gp = pb.ml_grad()
+    d_o = (-go).contiguous()
+    d_p = (-0.1 * gp).contiguous()
+    got = pb.line_coeffs(d_o, d_p).cpu().numpy()
+    ref = oracle.ml_line_coeffs(obj, probe, d_o.cpu().numpy(), d_p.cpu().numpy(), data_of(s))
+    np.testing.assert_allclose(got, ref, rtol=1e-4)
+    pb.close()
+
+
+@pytest.mark.parametrize("cfg,J,both", [("ml32fd", 16, False), ("ml256", 60, False), ("ml256", 60, True)])
+def test_ml_cg_parity(cfg, J, both):
+    """ML CG steps on the GPU against the FP64 oracle CG (object only, as the
+    paper's ML defaults, and object + probe)."""
+    s, obj, probe = warm(cfg, J=J, n_ap=3)
+    pb = gpu_problem(s, with_psi=False, obj=obj, probe=probe)
+    llk = pb.ml(1, update_probe=both, restart=True).cpu().numpy()
+    o1, p1, l1 = oracle.ml_cg(obj, probe, data_of(s), 1, update_probe=both)
+    check_close("obj after 1 CG step", pb.obj.cpu().numpy(), o1, TOL1)
+    check_close("probe after 1 CG step", pb.probe.cpu().numpy(), p1, TOL1)
+    assert abs(llk[0] - l1[0]) < TOL1 * abs(l1[0])
+    more = pb.ml(4, update_probe=both).cpu().numpy()
+    o5, p5, l5 = oracle.ml_cg(obj, probe, data_of(s), 5, update_probe=both)
+    check_close("obj after 5 CG steps", pb.obj.cpu().numpy(), o5, TOL20)
+    check_close("probe after 5 CG steps", pb.probe.cpu().numpy(), p5, TOL20)
+    np.testing.assert_allclose(np.concatenate([llk, more]), l5, rtol=TOL20)
+    assert all(b < a for a, b in zip(l5[:-1], l5[1:]))
+    pb.close()
