@@ -239,6 +239,8 @@ def run_ours(args):
         pb.set_param("lanes", args.lanes)
     if args.batch_frames:
         pb.set_param("batch_frames", args.batch_frames)
+    if args.tma is not None:
+        pb.set_param("tma", args.tma)
     stream = torch.cuda.current_stream(dev)
     llk_buf = torch.empty(max(args.steps, args.warmup, 1), dtype=torch.float64, device=dev)
 
@@ -372,6 +374,8 @@ def main():
                     help="use only the first FRAMES frames of the workload (small cases for profiling)")
     ap.add_argument("--lanes", type=int, default=0,
                     help="batches in flight per cycle (library default when 0)")
+    ap.add_argument("--tma", type=int, choices=(0, 1), default=None,
+                    help="column pass staged by tensor copies (1) or the register column pass (0, the library default)")
     ap.add_argument("--batch-frames", type=int, default=0,
                     help="upper bound on frames per batch (library default when 0)")
     ap.add_argument("--timing-only", action="store_true",

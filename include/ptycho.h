@@ -43,7 +43,8 @@ typedef enum {
     PTX_ERR_UNSUPPORTED = 2,   /* frame size N not in the supported set, K > PTX_MAX_MODES */
     PTX_ERR_OUT_OF_BOUNDS = 3, /* a position puts its patch outside the object */
     PTX_ERR_CUDA = 4,          /* a CUDA runtime call failed (text in ptx_last_error) */
-    PTX_ERR_TIMEOUT = 5,       /* reserved: a bounded device-side wait gave up */
+    PTX_ERR_TIMEOUT = 5,       /* a bounded device-side wait (tensor-copy arrival) of an earlier call
+                                  gave up; that call's results are invalid; reported once */
     PTX_ERR_NOT_READY = 6      /* scratch too small or handle in an unusable state */
 } ptx_status;
 
@@ -194,7 +195,10 @@ ptx_status ptx_accumulators(ptx_handle* h, int32_t p, void** obj_acc, size_t* ob
 /* Set a scalar parameter: "alpha_obj" or "alpha_probe" (inertia factors of the
  * normalisation, default 0.01 each, must be >= 0); "lanes" (batches in flight per
  * cycle, 1..4, default 2); "batch_frames" (upper bound on frames per batch, 0 =
- * as many as the work stack holds). */
+ * as many as the work stack holds); "tma" (0, default: the register column pass;
+ * 1: the AP / DM column pass of one-mode problems with N = 256 takes its inputs
+ * by 2D tensor copies (cp.async.bulk.tensor) in a persistent grid of two CTAs
+ * per SM).  Both give the same results up to FP32 rounding order. */
 ptx_status ptx_set_param(ptx_handle* h, const char* name, double value);
 
 /* In-place orthonormal 2D FFT of `nframes` N x N complex64 frames (the FT

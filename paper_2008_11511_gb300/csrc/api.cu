@@ -1,6 +1,8 @@
 // libptycho C ABI: argument checks, scratch layout, batch scheduling and
 // CUDA-graph replay of the cycle.  The operations themselves are the kernels of
 // kernels.cuh; this file only validates, lays out memory and enqueues.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -111,6 +113,7 @@ constexpr int kMaxLanes = 4;
 struct Layout {
     size_t pos, mask, acc_obj, acc_probe, llk_part, maxbits, tile_ids, tile_ptr, tile_frames;
     size_t cg_obj, cg_probe, ls_part, cg;  // ML conjugate-gradient state
+    size_t mbits;                          // per-thread mask bits of the register column pass
     size_t end;
 };
 
@@ -126,20 +129,24 @@ struct ProbHost {
     Layout lay{};
     ProbArgs args{};
     TileLists tiles{};
+    // tensor maps of the intensities and the mask for the tensor-copy column pass (valid if tma_io)
+    CUtensorMap tm_io{};
+    CUtensorMap tm_mask{};
+    bool tma_io = false;
 };
 
 // Per-tile frame lists of the object gather (host, from the positions).
 void build_tiles(ProbHost& h, const int32_t* positions) {
     const ptx_problem& p = h.p;
-    const int T = kObjTile;
-    const int ntx = (p.Wo + T - 1) / T, nty = (p.Ho + T - 1) / T;
+    const int TW = kObjTileW, TH = kObjTileH;
+    const int ntx = (p.Wo + TW - 1) / TW, nty = (p.Ho + TH - 1) / TH;
     std::vector<int> count((size_t)ntx * nty, 0);
     auto span = [&](int j, int& ty0, int& ty1, int& tx0, int& tx1) {
         const int r = positions[2 * j], c = positions[2 * j + 1];
-        ty0 = r / T;
-        ty1 = (r + p.N - 1) / T;
-        tx0 = c / T;
-        tx1 = (c + p.N - 1) / T;
+        ty0 = r / TH;
+        ty1 = (r + p.N - 1) / TH;
+        tx0 = c / TW;
+        tx1 = (c + p.N - 1) / TW;
     };
     for (int j = 0; j < p.J; ++j) {
         int ty0, ty1, tx0, tx1;
@@ -267,6 +274,8 @@ size_t layout_problem(ProbHost& h) {
     o = align_up(o + 2 * sizeof(double) * (size_t)p.J * (p.N / h.ks->ls_lines));
     h.lay.cg = o;
     o = align_up(o + 8 * sizeof(double));
+    h.lay.mbits = o;
+    if (use_reg_kernels(h.ks, p.K)) o = align_up(o + sizeof(uint32_t) * (size_t)(p.N / h.ks->reg_lines) * kThreads);
     h.lay.end = o;
     return o;
 }
@@ -275,12 +284,49 @@ struct GraphKey {
     std::vector<int> algos;
     uint32_t flags;
     int lanes;
+    int tma;
     bool operator<(const GraphKey& o) const {
         if (flags != o.flags) return flags < o.flags;
         if (lanes != o.lanes) return lanes < o.lanes;
+        if (tma != o.tma) return tma < o.tma;
         return algos < o.algos;
     }
 };
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Row-major [h][w] array of `es`-byte elements (8: complex64 moved as 64-bit
+// words, 4: float32, 1: bytes), copied in boxes of bh rows x bw elements.
+bool encode_2d(CUtensorMap* m, int es, const void* base, uint64_t w, uint64_t h, uint32_t bw, uint32_t bh) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const CUtensorMapDataType dt = es == 8   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                   : es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                             : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    cuuint64_t dims[2] = {w, h};
+    cuuint64_t strides[1] = {w * es};
+    cuuint32_t box[2] = {bw, bh};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, dt, 2, (void*)base, dims,
+               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 }  // namespace
 
@@ -297,6 +343,10 @@ struct ptx_handle {
     // batch lanes: extra streams and fork / join events (lane 0 is the call's stream)
     int lanes = kDefaultLanes;
     int batch_cap = 0;  // ptx_set_param "batch_frames"
+    int tma = 0;        // ptx_set_param "tma": column pass fed by tensor copies where available
+    // flag in mapped pinned host memory that a device wait sets when it gives up
+    int* err_host = nullptr;
+    int* err_dev = nullptr;
     size_t spec_bytes = 0;
     cudaStream_t lane_stream[kMaxLanes] = {};
     cudaEvent_t fork_ev = nullptr;
@@ -309,6 +359,28 @@ struct ptx_handle {
 };
 
 namespace {
+
+// Mask bits of the register column pass: entry [xb][t] holds, for thread t of
+// column block xb, bit (i M + k1) = mask at row k2 + R k1, column xb C + c of its
+// pass-2 item i (w = t + 256 i, k2 = w / C, c = w % C), C = lines per block.
+std::vector<uint32_t> mask_bits(const KernelSet* ks, int N, const uint8_t* mask) {
+    const int C = ks->reg_lines, R = ks->R, M = ks->M, XB = N / C;
+    const int I2 = (C * R + kThreads - 1) / kThreads;
+    std::vector<uint32_t> t((size_t)XB * kThreads, 0u);
+    for (int xb = 0; xb < XB; ++xb)
+        for (int th = 0; th < kThreads; ++th) {
+            uint32_t bits = 0u;
+            for (int i = 0; i < I2; ++i) {
+                const int w = th + i * kThreads;
+                if (w >= C * R) continue;
+                const int k2 = w / C, c = w % C;
+                for (int k1 = 0; k1 < M; ++k1)
+                    if (mask[(size_t)(k2 + R * k1) * N + xb * C + c]) bits |= 1u << (i * M + k1);
+            }
+            t[(size_t)xb * kThreads + th] = bits;
+        }
+    return t;
+}
 
 ptx_status compute_layout(std::vector<ProbHost>& probs, size_t* spec_off, size_t* ctl_off, size_t* total) {
     size_t o = 0;
@@ -330,6 +402,7 @@ ptx_status compute_layout(std::vector<ProbHost>& probs, size_t* spec_off, size_t
         h.lay.cg_probe += o;
         h.lay.ls_part += o;
         h.lay.cg += o;
+        h.lay.mbits += o;
         h.lay.end += o;
         o += sz;
         size_t s = (size_t)h.B * kDefaultLanes * h.p.K * h.p.N * h.p.N * sizeof(float2);
@@ -370,6 +443,8 @@ void fill_args(ptx_handle* h, ProbHost& ph) {
     a.dir_obj = nullptr;
     a.dir_probe = nullptr;
     a.ls_part = (double*)(h->scratch + ph.lay.ls_part);
+    a.err_flag = h->err_dev;
+    a.mbits = (const uint32_t*)(h->scratch + ph.lay.mbits);
     ph.tiles.tile_ids = (const int*)(h->scratch + ph.lay.tile_ids);
     ph.tiles.tile_ptr = (const int*)(h->scratch + ph.lay.tile_ptr);
     ph.tiles.tile_frames = (const int*)(h->scratch + ph.lay.tile_frames);
@@ -498,7 +573,13 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
             }
             {
                 ProfScope ps(h, PTX_KERNEL_COL, ls);
-                ks->col(al, j0, nb, COL_PROJECT, ls);
+                CUtensorMap tm_spec;
+                const int grid = (h->tma && ph.tma_io && ks->col_tma) ? ks->col_tma_grid() : 0;
+                if (grid > 0 && encode_2d(&tm_spec, 8, al.spec, ph.p.N, (uint64_t)ph.B * ph.p.N,
+                                          (uint32_t)ks->reg_lines, (uint32_t)ph.p.N))
+                    ks->col_tma(&tm_spec, &ph.tm_io, &ph.tm_mask, al, j0, nb, grid, ls);
+                else
+                    ks->col(al, j0, nb, COL_PROJECT, ls);
             }
             {
                 ProfScope ps(h, PTX_KERNEL_ROW_BWD, ls);
@@ -528,7 +609,7 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
 }
 
 ptx_status get_graph(ptx_handle* h, const std::vector<int>& algos, uint32_t flags, cudaGraphExec_t* out) {
-    GraphKey key{algos, flags, h->lanes};
+    GraphKey key{algos, flags, h->lanes, h->tma};
     auto it = h->graphs.find(key);
     if (it != h->graphs.end()) {
         *out = it->second;
@@ -590,6 +671,10 @@ ptx_status run_cycles(ptx_handle* h, const std::vector<int>& algos, int ncycles,
             return fail(PTX_ERR_INVALID_ARG, "problem %zu: AP and DM cycles need the psi array", i);
     ptx_status st = check_device(h);
     if (st != PTX_OK) return st;
+    if (h->err_host && *(volatile int*)h->err_host) {
+        *(volatile int*)h->err_host = 0;
+        return fail(PTX_ERR_TIMEOUT, "a bounded device wait of an earlier call gave up (its results are invalid)");
+    }
     if (ncycles == 0) return PTX_OK;
     cudaStream_t s = (cudaStream_t)stream;
     k_set_ctl<<<1, 1, 0, s>>>(h->ctl, llk_dev, (int)h->probs.size());
@@ -660,8 +745,23 @@ ptx_status ptx_create(ptx_handle** out, const ptx_problem* probs, int32_t nprob,
     h->spec_bytes = total - spec_off;
     h->ctl = (Ctl*)(h->scratch + ctl_off);
     cudaGetDevice(&h->device);
+    if (cudaHostAlloc((void**)&h->err_host, sizeof(int), cudaHostAllocMapped) == cudaSuccess) {
+        *h->err_host = 0;
+        if (cudaHostGetDevicePointer((void**)&h->err_dev, h->err_host, 0) != cudaSuccess) h->err_dev = nullptr;
+    } else {
+        h->err_host = nullptr;
+    }
+    cudaGetLastError();
+    for (ProbHost& ph : h->probs) {
+        const KernelSet* ks = kernel_set(ph.p.N);
+        const uint32_t C = (uint32_t)ks->reg_lines, N = (uint32_t)ph.p.N;
+        ph.tma_io = ph.p.K == 1 && ks->col_tma && ks->col_tma_grid() > 0 &&
+                    encode_2d(&ph.tm_io, 4, ph.p.iobs, N, (uint64_t)ph.p.J * N, C, N) &&
+                    encode_2d(&ph.tm_mask, 1, h->scratch + ph.lay.mask, N, N, C, N);
+    }
     cudaStream_t s = (cudaStream_t)stream;
     // zero everything the library owns, then copy positions and mask
+    std::vector<std::vector<uint32_t>> mbits_host(h->probs.size());
     e = cudaMemsetAsync(h->scratch, 0, spec_off, s);
     for (size_t i = 0; e == cudaSuccess && i < h->probs.size(); ++i) {
         ProbHost& ph = h->probs[i];
@@ -672,6 +772,12 @@ ptx_status ptx_create(ptx_handle** out, const ptx_problem* probs, int32_t nprob,
         if (ph.p.mask) {
             e = cudaMemcpyAsync(h->scratch + ph.lay.mask, ph.p.mask, (size_t)ph.p.N * ph.p.N, cudaMemcpyHostToDevice, s);
             if (e != cudaSuccess) break;
+            if (use_reg_kernels(ph.ks, ph.p.K)) {
+                mbits_host[i] = mask_bits(ph.ks, ph.p.N, ph.p.mask);
+                e = cudaMemcpyAsync(h->scratch + ph.lay.mbits, mbits_host[i].data(), sizeof(uint32_t) * mbits_host[i].size(),
+                                    cudaMemcpyHostToDevice, s);
+                if (e != cudaSuccess) break;
+            }
         }
         const std::vector<int>* lists[3] = {&ph.tile_ids, &ph.tile_ptr, &ph.tile_frames};
         const size_t offs[3] = {ph.lay.tile_ids, ph.lay.tile_ptr, ph.lay.tile_frames};
@@ -915,6 +1021,9 @@ ptx_status ptx_set_param(ptx_handle* h, const char* name, double value) {
         if (value < 1 || value > kMaxLanes || value != (int)value)
             return fail(PTX_ERR_INVALID_ARG, "lanes must be an integer in 1..%d", kMaxLanes);
         h->lanes = (int)value;
+    } else if (!strcmp(name, "tma")) {
+        if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "tma must be 0 or 1");
+        h->tma = (int)value;
     } else if (!strcmp(name, "batch_frames")) {
         if (value != (int)value || value > 32768)
             return fail(PTX_ERR_INVALID_ARG, "batch_frames must be an integer in 0..32768");
@@ -981,6 +1090,7 @@ void ptx_destroy(ptx_handle* h) {
     }
     for (cudaEvent_t e : h->prob_ev) cudaEventDestroy(e);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->err_host) cudaFreeHost(h->err_host);
     delete h;
 }
 

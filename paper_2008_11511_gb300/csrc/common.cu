@@ -18,13 +18,14 @@ __device__ __forceinline__ float warp_max(float v) {
 // over the frames whose patch contains r, in ascending j.  Each pixel is
 // owned by one thread, so the accumulator is written without atomics.
 __global__ void __launch_bounds__(256) k_obj_gather(ProbArgs a, TileLists tl) {
-    constexpr int T = kObjTile;
-    constexpr int Q = T * T / 256;  // pixels per thread (rows lane-major)
+    constexpr int TW = kObjTileW, TH = kObjTileH;
+    constexpr int RS = 256 / TW;          // rows covered by the block's threads at once
+    constexpr int Q = TW * TH / 256;      // pixels per thread: rows wy + RS q of column x
     const int t = blockIdx.x;
     const int tid = tl.tile_ids[t];
     const int ty = tid / tl.ntx, tx = tid - ty * tl.ntx;
-    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
-    const int x = tx * T + lane;
+    const int wy = threadIdx.x / TW;
+    const int x = tx * TW + threadIdx.x % TW;
     const int N = a.N, K = a.K;
     float2 n[Q];
     float d[Q];
@@ -34,7 +35,7 @@ __global__ void __launch_bounds__(256) k_obj_gather(ProbArgs a, TileLists tl) {
         d[q] = 0.f;
     }
     const int f0 = tl.tile_ptr[t], f1 = tl.tile_ptr[t + 1];
-    const int y0 = ty * T + wy;
+    const int y0 = ty * TH + wy;
     // F frames per step: all their loads are issued before any is used, so each
     // thread keeps up to 2 F Q loads in flight (the loop is latency-bound otherwise)
     constexpr int F = 4;
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(256) k_obj_gather(ProbArgs a, TileLists tl) {
                 const int px = x - p.y;
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
-                    const int py = y0 + 8 * q - p.x;
+                    const int py = y0 + RS * q - p.x;
                     ok[u][q] = fi < f1 && px >= 0 && px < N && py >= 0 && py < N;
                     const size_t off = ok[u][q] ? ((size_t)k * N + py) * N + px : 0;
                     pr[u][q] = ok[u][q] ? __ldg(a.probe + off) : make_float2(0.f, 0.f);
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(256) k_obj_gather(ProbArgs a, TileLists tl) {
     if (x < a.Wo) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const int y = ty * T + wy + 8 * q;
+            const int y = y0 + RS * q;
             if (y < a.Ho) a.acc_obj[(size_t)y * a.Wo + x] = make_float4(n[q].x, n[q].y, d[q], 0.f);
         }
     }

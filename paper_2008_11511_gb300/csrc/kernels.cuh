@@ -49,6 +49,8 @@ struct ProbArgs {
     const float2* dir_probe;  // [K][N][N] or null
     double* ls_part;        // [J][ncolblk][2] line-search partial sums
     int L1, C2, L3;         // rows per row_fwd block, columns per col block, rows per row_bwd block
+    int* err_flag;          // host-mapped flag, set when a bounded device wait gives up (or null)
+    const uint32_t* mbits;  // [N / C][256] mask bits per thread of the register column pass
 };
 
 struct Ctl {
@@ -512,8 +514,15 @@ __global__ void __launch_bounds__(kThreads) k_col_ls(ProbArgs a, int j0, int C) 
 // ---------------------------------------------------------------------------
 // Normalisation (Psi2ObjProbe second half) and reductions.
 // ---------------------------------------------------------------------------
-// Object tiles of the gather: kObjTile x kObjTile pixels, one block each.
-constexpr int kObjTile = 32;
+// Object tiles of the gather: kObjTileW x kObjTileH pixels, one block each.
+// Wide tiles make every frame's share of a tile a few long row segments
+// (kObjTileW * 8 bytes each), which HBM serves more efficiently than short ones.
+#ifndef PTX_OBJ_TILE_W
+#define PTX_OBJ_TILE_W 32
+#endif
+constexpr int kObjTileW = PTX_OBJ_TILE_W;
+constexpr int kObjTileH = 1024 / kObjTileW;
+static_assert(kObjTileW % 32 == 0 && kObjTileW <= 256 && kObjTileH * kObjTileW == 1024, "1024-pixel tiles, 32-wide multiples");
 struct TileLists {
     const int* tile_ids;     // [ntiles] tile index ty * ntx + tx of each active tile
     const int* tile_ptr;     // [ntiles + 1] CSR offsets into tile_frames
@@ -597,6 +606,10 @@ struct KernelSet {
     int ls_lines;   // rows / columns per block of the line-search kernels
     int reg_lines;  // lines per block of the register kernels (0: none for this N)
     int R, M;
+    // column pass fed by tensor copies (K = 1; null where N has none) and its persistent grid
+    void (*col_tma)(const void* tm_spec, const void* tm_io, const void* tm_mask, const ProbArgs&, int j0, int nb,
+                    int grid, cudaStream_t);
+    int (*col_tma_grid)();
 };
 
 const KernelSet* kernel_set(int N);
@@ -614,10 +627,12 @@ size_t smem_row_bwd_t(int K, int L) {
 
 }  // namespace ptx
 #include "kernels_reg.cuh"
+#include "kernels_tma.cuh"
 namespace ptx {
 
 template <int N>
 constexpr bool has_reg() { return Plan<N>::M > 1; }
+
 
 template <int N>
 void launch_row_fwd(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s) {
@@ -724,7 +739,9 @@ const KernelSet* make_kernel_set() {
                                  ls_lines<N>(),
                                  rl,
                                  Plan<N>::R,
-                                 Plan<N>::M};
+                                 Plan<N>::M,
+                                 ColTma<N>::kOk ? &launch_col_tma<N> : nullptr,
+                                 &col_tma_grid<N>};
     return &ks;
 }
 

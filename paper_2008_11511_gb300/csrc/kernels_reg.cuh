@@ -38,6 +38,8 @@ struct RegShape {
     // blocks per SM the register budget is sized for: large codelets (24, 32
     // points) need more registers per thread
     static constexpr int MinBlocks = (R > M ? R : M) >= 24 ? 2 : 5;
+    // the column pass also holds its pixels' intensities in registers
+    static constexpr int ColMinBlocks = (R > M ? R : M) >= 24 ? 2 : 4;
     static_assert(M > 1, "register kernels need two passes");
     static_assert(N % L == 0, "lines per block must divide N");
 };
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_r(
 // grid (N / L, frames in batch); block handles columns [x0, x0 + L).
 // ---------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_col_r(ProbArgs a, int j0, int mode) {
+__global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(ProbArgs a, int j0, int mode) {
     using S = RegShape<N>;
     constexpr int R = S::R, M = S::M, C = S::L, P = S::P;
     constexpr int I1b = (C * M + kThreads - 1) / kThreads;  // inverse pass-2 items (M per column)
@@ -132,27 +134,33 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_col_r(Prob
     const int b = blockIdx.y;
     const int j = j0 + b;
     float2* spec = a.spec + (size_t)b * N * N + x0;
-    // the block's intensities and mask, copied to shared memory (cp.async) while
-    // the forward transform runs; C = 16 columns are 64 bytes of I and 16 of mask per row
-    float* io_s = (float*)(buf + C * P);          // [N][C]
-    uint8_t* mk_s = (uint8_t*)(io_s + N * C);     // [N][C]
-    {
-        const float* io_g = a.iobs + (size_t)j * N * N + x0;
-        constexpr int CH = C * 4 / 16;  // 16-byte chunks per row of intensities
-        for (int e = threadIdx.x; e < N * CH; e += kThreads) {
-            const int row = e / CH, q = e - row * CH;
-            cp_async16_hint(io_s + row * C + 4 * q, io_g + (size_t)row * N + 4 * q, policy_evict_first());
+    // intensities of this thread's pass-2 pixels (rows k2 + R k1 of column c),
+    // loaded into registers while the forward transform runs, and their mask bits
+    float io_r[S::I2][M];
+#pragma unroll
+    for (int i = 0; i < S::I2; ++i) {
+        const int w = threadIdx.x + i * kThreads;
+        if (w < C * R) {
+            const int k2 = w / C, c = w - k2 * C;
+            const float* ib = a.iobs + (size_t)j * N * N + (size_t)k2 * N + x0 + c;
+#pragma unroll
+            for (int k1 = 0; k1 < M; ++k1) io_r[i][k1] = __ldcs(ib + (size_t)R * k1 * N);
         }
-        if constexpr (C >= 16) {
-            constexpr int MC = C / 16;  // 16-byte chunks per row of mask
-            for (int e = threadIdx.x; e < N * MC; e += kThreads) {
-                const int row = e / MC, q = e - row * MC;
-                cp_async16(mk_s + row * C + 16 * q, a.mask + row * N + x0 + 16 * q);
+    }
+    uint32_t mbits = 0u;
+    if (a.mbits) {
+        mbits = a.mbits[blockIdx.x * kThreads + threadIdx.x];
+    } else {  // callers without the table (the allocation-free entry point) read the mask bytes
+#pragma unroll
+        for (int i = 0; i < S::I2; ++i) {
+            const int w = threadIdx.x + i * kThreads;
+            if (w < C * R) {
+                const int k2 = w / C, c = w - k2 * C;
+#pragma unroll
+                for (int k1 = 0; k1 < M; ++k1)
+                    mbits |= (a.mask[(size_t)(k2 + R * k1) * N + x0 + c] != 0) ? (1u << (i * M + k1)) : 0u;
             }
-        } else {
-            for (int row = threadIdx.x; row < N; row += kThreads) cp_async8(mk_s + row * C, a.mask + row * N + x0);
         }
-        cp_async_commit();
     }
     __syncthreads();
     // forward pass 1: thread (c, n1) holds rows n1 + M n2 of column c
@@ -185,7 +193,6 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_col_r(Prob
             for (int n1 = 0; n1 < M; ++n1) u[i][n1] = src[n1];
         }
     }
-    cp_async_wait_all();
     __syncthreads();
     constexpr float invN2 = 1.0f / float(N * N);
     KahanF llk;
@@ -197,10 +204,9 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_col_r(Prob
             Dft<M, -1>::run(u[i]);
 #pragma unroll
             for (int k1 = 0; k1 < M; ++k1) {
-                const int row = k2 + R * k1;
                 const float ic = cnorm(u[i][k1]) * invN2;
-                const float io = io_s[row * C + c];
-                const bool masked = mk_s[row * C + c] != 0;
+                const float io = io_r[i][k1];
+                const bool masked = (mbits >> (i * M + k1)) & 1u;
                 if (!masked) llk.add(llk_term_fast(ic, io));
                 float f;
                 if (masked) {
@@ -431,7 +437,7 @@ size_t smem_row_fwd_r() { return sizeof(float2) * (N + (size_t)RegShape<N>::L * 
 template <int N>
 size_t smem_col_r() {
     using S = RegShape<N>;
-    return sizeof(float2) * (N + (size_t)S::L * S::P) + (size_t)N * S::L * (sizeof(float) + 1);
+    return sizeof(float2) * (N + (size_t)S::L * S::P);
 }
 template <int N>
 size_t smem_row_bwd_r() {

@@ -530,6 +530,34 @@ def test_several_frames_per_block_all_sizes(N, J):
     pb.close()
 
 
+@pytest.mark.parametrize("tma", [0, 1])
+@pytest.mark.parametrize("lanes,batch", [(1, 0), (2, 0), (2, 37)])
+def test_dm256_column_pass_variants(tma, lanes, batch):
+    """The 256x256 column pass with and without tensor-copy staging, in one and
+    two lanes and with a batch size (37 frames) that leaves ragged batches and a
+    partial last wave of the persistent grid: three DM cycles and one AP cycle
+    against the oracle."""
+    s, o0, p0 = warm("dm256", J=150, Ho=640, Wo=640)
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    pb.set_param("tma", tma)
+    pb.set_param("lanes", lanes)
+    pb.set_param("batch_frames", batch)
+    llk = pb.dm(3, init_psi=True).cpu().numpy()
+    o, p, psi, llk_ref = oracle.cycles("DM", o0, p0, data_of(s), 3)
+    _compare_cycle_state(s, pb, o, p, TOL1 * 3, psi_ref=psi)
+    np.testing.assert_allclose(llk, llk_ref, rtol=TOL1 * 3)
+    pb.close()
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    pb.set_param("tma", tma)
+    pb.set_param("lanes", lanes)
+    pb.set_param("batch_frames", batch)
+    l1 = pb.ap(1).cpu().numpy()
+    o, p, l = oracle.ap_cycle(o0, p0, data_of(s))
+    _compare_cycle_state(s, pb, o, p, TOL1)
+    assert abs(l1[0] - l) / abs(l) < TOL1
+    pb.close()
+
+
 def test_full_size_dm256_cycle_in_bench_configuration():
     """The headline workload at full size — 4000 frames of 256x256, 2048x2048 object,
     2 % mask — in bench.py's launch configuration (CUDA graph, two batch lanes):
