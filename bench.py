@@ -241,6 +241,8 @@ def run_ours(args):
         pb.set_param("batch_frames", args.batch_frames)
     if args.tma is not None:
         pb.set_param("tma", args.tma)
+    if args.tma_gather is not None:
+        pb.set_param("tma_gather", args.tma_gather)
     stream = torch.cuda.current_stream(dev)
     llk_buf = torch.empty(max(args.steps, args.warmup, 1), dtype=torch.float64, device=dev)
 
@@ -376,6 +378,8 @@ def main():
                     help="batches in flight per cycle (library default when 0)")
     ap.add_argument("--tma", type=int, choices=(0, 1), default=None,
                     help="column pass staged by tensor copies (1) or the register column pass (0, the library default)")
+    ap.add_argument("--tma-gather", type=int, choices=(0, 1), default=None,
+                    help="object gather fed by tensor copies (1, the library default) or the plain gather (0)")
     ap.add_argument("--batch-frames", type=int, default=0,
                     help="upper bound on frames per batch (library default when 0)")
     ap.add_argument("--timing-only", action="store_true",

