@@ -1,4 +1,4 @@
-"""FP64 CPU oracle for the far-field ptychography projection cycle.
+"""FP64 CPU oracle for the ptychography projection cycle (far and near field).
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
@@ -41,6 +41,13 @@ Readings of points the paper leaves open (each is listed in the design doc):
   scan.)
 * The per-cycle LLK is that of the wave being projected (Phi for AP, 2 Phi - Psi
   for DM); ``llk`` gives the exact L(O, P).
+* Near field (PropagateNearField; the paper names the operator and the near /
+  far field flag but gives no formula): paraxial Fresnel propagation in
+  Fourier space, IFT(FT(x) exp(-i pi lambda z q^2)), q = k / (N pixel) the
+  signed spatial frequency, parametrised by c = lambda z / pixel^2; back
+  propagation uses the conjugate transfer.  The near-field amplitude projection
+  is PropagateNearField^-1 ApplyAmplitude PropagateNearField (the paper's
+  PropagateApplyAmplitude), with intensities and mask in detector pixels.
 """
 from __future__ import annotations
 
@@ -65,20 +72,25 @@ def _workers():
 
 @dataclass
 class Data:
-    """PtychoData (paper Section 4): observed intensities, positions, mask."""
+    """PtychoData (paper Section 4): observed intensities, positions, mask and
+    the near / far field flag.  ``nearfield`` = 0 is the far field (the
+    detector sees FT(Psi), intensities in FFT order); ``nearfield`` = c > 0 is
+    the near field with propagation factor c = lambda z / pixel^2 (the detector
+    sees PropagateNearField(Psi), intensities in real-space order)."""
 
-    iobs: np.ndarray       # float64 (J, N, N), FFT order
+    iobs: np.ndarray       # float64 (J, N, N)
     positions: np.ndarray  # int64 (J, 2) top-left (row, col)
     mask: np.ndarray       # bool (N, N), True = bad pixel (free)
+    nearfield: float = 0.0
 
     @staticmethod
-    def make(iobs, positions, mask=None):
+    def make(iobs, positions, mask=None, nearfield=0.0):
         iobs = np.asarray(iobs, dtype=np.float64)
         N = iobs.shape[-1]
         if mask is None:
             mask = np.zeros((N, N), dtype=bool)
         return Data(iobs=iobs, positions=np.asarray(positions, dtype=np.int64),
-                    mask=np.asarray(mask).astype(bool))
+                    mask=np.asarray(mask).astype(bool), nearfield=float(nearfield))
 
     @property
     def J(self):
@@ -87,6 +99,14 @@ class Data:
     @property
     def N(self):
         return self.iobs.shape[-1]
+
+    def to_detector(self, x):
+        """The wave at the detector: FT (far field) or PropagateNearField forward."""
+        return ft(x) if self.nearfield == 0 else propagate_near_field(x, self.nearfield, +1)
+
+    def from_detector(self, y):
+        """Inverse (and adjoint) of ``to_detector``."""
+        return ift(y) if self.nearfield == 0 else propagate_near_field(y, self.nearfield, -1)
 
 
 # --------------------------------------------------------------------------
@@ -101,6 +121,25 @@ def ft(x):
 def ift(x):
     """IFT: inverse of ``ft`` (its adjoint, as ``ft`` is unitary)."""
     return scipy.fft.ifft2(x, axes=(-2, -1), norm="ortho", workers=_workers())
+
+
+def near_field_transfer(N, c):
+    """Fresnel (paraxial) transfer function on the N x N frequency grid in FFT
+    order: h[ky, kx] = exp(-i pi c (ky^2 + kx^2) / N^2), k the signed integer
+    frequency (k - N for k >= N / 2) and c = lambda z / pixel^2 (a plane wave of
+    spatial frequency q = k / (N pixel) gains the phase -pi lambda z q^2)."""
+    k = np.fft.fftfreq(N) * N
+    q2 = k[:, None] ** 2 + k[None, :] ** 2
+    return np.exp(-1j * np.pi * c * q2 / N ** 2)
+
+
+def propagate_near_field(x, c, direction=+1):
+    """PropagateNearField: IFT(FT(x) h) over the last two axes; direction -1
+    propagates back (conj(h), the inverse and adjoint, as |h| = 1)."""
+    h = near_field_transfer(x.shape[-1], c)
+    if direction < 0:
+        h = np.conj(h)
+    return ift(ft(x) * h)
 
 
 def obj_probe_to_psi(obj, probe, positions):
@@ -227,7 +266,9 @@ def ap_cycle(obj, probe, data: Data, alpha_obj=1e-2, alpha_probe=1e-2,
              update_obj=True, update_probe=True):
     """One Alternating Projections cycle (AP, Marchesini et al. 2013):
     Psi_j = IFT(ApplyAmplitude(FT(Phi_j))), Phi = ObjProbe2Psi(O, P), then
-    Psi2ObjProbe.  Returns (obj, probe, llk of FT(Phi))."""
+    Psi2ObjProbe.  In the near field FT / IFT are the forward and backward
+    PropagateNearField (the paper's PropagateApplyAmplitude operator).
+    Returns (obj, probe, llk of the detector wave of Phi)."""
     obj = np.asarray(obj, dtype=np.complex128)
     probe = np.asarray(probe, dtype=np.complex128)
     psi = np.empty((data.J,) + probe.shape, dtype=np.complex128)
@@ -235,9 +276,9 @@ def ap_cycle(obj, probe, data: Data, alpha_obj=1e-2, alpha_probe=1e-2,
     for lo, hi in _stacks(data.J):
         pos = data.positions[lo:hi]
         phi = obj_probe_to_psi(obj, probe, pos)
-        phi_hat = ft(phi)
+        phi_hat = data.to_detector(phi)
         llk += llk_poisson(calc_intensity(phi_hat), data.iobs[lo:hi], data.mask)
-        psi[lo:hi] = ift(apply_amplitude(phi_hat, data.iobs[lo:hi], data.mask))
+        psi[lo:hi] = data.from_detector(apply_amplitude(phi_hat, data.iobs[lo:hi], data.mask))
     obj, probe = overlap_update(obj, probe, psi, data.positions, alpha_obj, alpha_probe, update_obj, update_probe)
     return obj, probe, llk
 
@@ -246,7 +287,8 @@ def dm_cycle(obj, probe, psi, data: Data, alpha_obj=1e-2, alpha_probe=1e-2,
              update_obj=True, update_probe=True, init_psi=False):
     """One Difference Map cycle (beta = 1; Elser 2007, Thibault et al. 2008):
     Phi = ObjProbe2Psi(O, P); X = 2 Phi - Psi;
-    Psi <- Psi + IFT(ApplyAmplitude(FT(X))) - Phi; then Psi2ObjProbe from the new Psi.
+    Psi <- Psi + IFT(ApplyAmplitude(FT(X))) - Phi; then Psi2ObjProbe from the new Psi
+    (near field: PropagateNearField forward / back in place of FT / IFT).
     ``init_psi`` sets Psi = Phi first.  Returns (obj, probe, psi, llk of FT(X))."""
     obj = np.asarray(obj, dtype=np.complex128)
     probe = np.asarray(probe, dtype=np.complex128)
@@ -262,9 +304,9 @@ def dm_cycle(obj, probe, psi, data: Data, alpha_obj=1e-2, alpha_probe=1e-2,
         if init_psi:
             psi[lo:hi] = phi
         x = 2.0 * phi - psi[lo:hi]
-        x_hat = ft(x)
+        x_hat = data.to_detector(x)
         llk += llk_poisson(calc_intensity(x_hat), data.iobs[lo:hi], data.mask)
-        x_proj = ift(apply_amplitude(x_hat, data.iobs[lo:hi], data.mask))
+        x_proj = data.from_detector(apply_amplitude(x_hat, data.iobs[lo:hi], data.mask))
         psi[lo:hi] = psi[lo:hi] + x_proj - phi
     obj, probe = overlap_update(obj, probe, psi, data.positions, alpha_obj, alpha_probe, update_obj, update_probe)
     return obj, probe, psi, llk
@@ -276,7 +318,7 @@ def llk(obj, probe, data: Data):
     probe = np.asarray(probe, dtype=np.complex128)
     total = 0.0
     for lo, hi in _stacks(data.J):
-        phi_hat = ft(obj_probe_to_psi(obj, probe, data.positions[lo:hi]))
+        phi_hat = data.to_detector(obj_probe_to_psi(obj, probe, data.positions[lo:hi]))
         total += llk_poisson(calc_intensity(phi_hat), data.iobs[lo:hi], data.mask)
     return total
 
@@ -292,6 +334,8 @@ def ml_grad(obj, probe, data: Data):
       G_Pk(x)      = sum_j  conj(O(r_j + x)) IFT[w_j FT(Phi_jk)](x)
       w_j = 2 (1 - I_o / I_c) on unmasked pixels, 0 on masked ones.
 
+    In the near field FT / IFT are PropagateNearField forward / back (the
+    adjoint of a unitary propagator is its inverse).
     Returns (llk deviance, G_O, G_P)."""
     obj = np.asarray(obj, dtype=np.complex128)
     probe = np.asarray(probe, dtype=np.complex128)
@@ -301,12 +345,12 @@ def ml_grad(obj, probe, data: Data):
     total = 0.0
     for lo, hi in _stacks(data.J):
         pos = data.positions[lo:hi]
-        phi_hat = ft(obj_probe_to_psi(obj, probe, pos))
+        phi_hat = data.to_detector(obj_probe_to_psi(obj, probe, pos))
         ic = calc_intensity(phi_hat)
         io = np.maximum(data.iobs[lo:hi], 0.0)
         total += llk_poisson(ic, data.iobs[lo:hi], data.mask)
         w = np.where(data.mask, 0.0, 2.0 * (1.0 - io / np.maximum(ic, ICALC_FLOOR)))
-        back = ift(phi_hat * w[:, None])
+        back = data.from_detector(phi_hat * w[:, None])
         for i, (r, c) in enumerate(pos):
             patch = obj[r:r + N, c:c + N]
             g_o[r:r + N, c:c + N] += (np.conj(probe) * back[i]).sum(0)
@@ -332,9 +376,9 @@ def ml_line_coeffs(obj, probe, d_obj, d_probe, data: Data):
     l1 = l2 = 0.0
     for lo, hi in _stacks(data.J):
         pos = data.positions[lo:hi]
-        A = ft(obj_probe_to_psi(obj, probe, pos))
-        B = ft(obj_probe_to_psi(obj, d_probe, pos) + obj_probe_to_psi(d_obj, probe, pos))
-        C = ft(obj_probe_to_psi(d_obj, d_probe, pos))
+        A = data.to_detector(obj_probe_to_psi(obj, probe, pos))
+        B = data.to_detector(obj_probe_to_psi(obj, d_probe, pos) + obj_probe_to_psi(d_obj, probe, pos))
+        C = data.to_detector(obj_probe_to_psi(d_obj, d_probe, pos))
         ic = calc_intensity(A)
         di = 2.0 * (np.conj(A) * B).real.sum(axis=-3)
         d2i = 2.0 * ((B.real ** 2 + B.imag ** 2) + 2.0 * (np.conj(A) * C).real).sum(axis=-3)
@@ -404,16 +448,17 @@ def cycles(algorithm, obj, probe, data: Data, n, psi=None, init_psi=True, **kw):
 # or one object pixel at a time.
 # --------------------------------------------------------------------------
 
-def dm_frame_update(obj, probe, psi_j, iobs_j, pos_j, mask, init_psi=False):
+def dm_frame_update(obj, probe, psi_j, iobs_j, pos_j, mask, init_psi=False, nearfield=0.0):
     """New Psi_j and the LLK of frame j for one DM step (the frame's part of
     ``dm_cycle``).  Returns (psi_new_j, llk_j)."""
     obj = np.asarray(obj, dtype=np.complex128)
     probe = np.asarray(probe, dtype=np.complex128)
+    d = Data.make(np.asarray(iobs_j, np.float64)[None], np.asarray([pos_j]), mask, nearfield)
     phi = obj_probe_to_psi(obj, probe, np.asarray([pos_j]))[0]
     psi_j = phi if init_psi else np.asarray(psi_j, dtype=np.complex128)
-    x_hat = ft(2.0 * phi - psi_j)
-    l = llk_poisson(calc_intensity(x_hat), np.asarray(iobs_j, np.float64), mask)
-    return psi_j + ift(apply_amplitude(x_hat, np.asarray(iobs_j, np.float64), mask)) - phi, l
+    x_hat = d.to_detector(2.0 * phi - psi_j)
+    l = llk_poisson(calc_intensity(x_hat), d.iobs[0], d.mask)
+    return psi_j + d.from_detector(apply_amplitude(x_hat, d.iobs[0], d.mask)) - phi, l
 
 
 def frames_llk(obj, probe, data: Data, frames):
@@ -421,7 +466,7 @@ def frames_llk(obj, probe, data: Data, frames):
     obj = np.asarray(obj, dtype=np.complex128)
     probe = np.asarray(probe, dtype=np.complex128)
     frames = np.asarray(frames)
-    phi_hat = ft(obj_probe_to_psi(obj, probe, data.positions[frames]))
+    phi_hat = data.to_detector(obj_probe_to_psi(obj, probe, data.positions[frames]))
     return llk_poisson(calc_intensity(phi_hat), data.iobs[frames], data.mask)
 
 

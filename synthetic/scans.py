@@ -44,7 +44,7 @@ class Scan:
     Ho: int
     Wo: int
     positions: np.ndarray  # int32 (J, 2): (row, col) top-left corners
-    iobs: np.ndarray  # float32 (J, N, N), FFT order
+    iobs: np.ndarray  # float32 (J, N, N): FFT order (far field) or detector pixels (near field)
     mask: np.ndarray  # uint8 (N, N), 1 = masked, FFT order
     obj_true: np.ndarray  # complex128 (Ho, Wo)
     probe_true: np.ndarray  # complex128 (K, N, N), scaled to the photon count
@@ -55,6 +55,7 @@ class Scan:
     step_px: float  # achieved mean nearest-neighbour step of the spiral
     algorithm: str = "AP"
     cycles: int = 20
+    nearfield: float = 0.0  # 0: far field; c = lambda z / pixel^2 > 0: near field
     meta: dict = field(default_factory=dict)
 
 
@@ -177,16 +178,24 @@ def _workers():
         return os.cpu_count() or 1
 
 
-def _frame_intensities(obj, probe, positions, lo, hi):
-    """Noise-free model intensities sum_k |FT(P_k O[r_j])|^2 for frames lo..hi-1."""
+def _frame_intensities(obj, probe, positions, lo, hi, nearfield=0.0):
+    """Noise-free detector intensities for frames lo..hi-1: sum_k |FT(P_k O[r_j])|^2
+    in the far field; in the near field sum_k of |the wave after a Fresnel
+    propagation over lambda z = nearfield * pixel^2|^2, the propagation being
+    done in Fourier space with the paraxial transfer exp(-i pi lambda z q^2)."""
     N = probe.shape[-1]
     n = hi - lo
     out = np.zeros((n, N, N), dtype=np.float64)
+    if nearfield:
+        k = np.fft.fftfreq(N) * N
+        transfer = np.exp(-1j * np.pi * nearfield * (k[:, None] ** 2 + k[None, :] ** 2) / N ** 2)
     for i in range(n):
         r, c = positions[lo + i]
         patch = obj[r:r + N, c:c + N]
         w = probe * patch[None]
         f = scipy.fft.fft2(w, norm="ortho", workers=_workers())
+        if nearfield:
+            f = scipy.fft.ifft2(f * transfer, norm="ortho", workers=_workers())
         out[i] = (f.real ** 2 + f.imag ** 2).sum(0)
     return out
 
@@ -195,7 +204,8 @@ def make_scan(name: str, N: int, J: int, Ho: int, Wo: int, *, K: int = 1, seed: 
               photons: float, step: float, probe: str = "disk", probe_radius: float | None = None,
               phase_coef: float | None = None, mode_powers=None, mask_fraction: float = 0.0,
               noise: bool = True, probe0_blur: float = 2.0, algorithm: str = "AP",
-              cycles: int = 20, chunk: int = 256) -> Scan:
+              cycles: int = 20, chunk: int = 256, nearfield: float = 0.0,
+              diffuser_phase: float = 0.0) -> Scan:
     """Draw one seeded scan.  The probe is scaled so that the mean total model
     intensity per frame equals ``photons`` before Poisson sampling; hence the
     noise-free intensities equal the model of (obj_true, probe_true) exactly."""
@@ -210,6 +220,10 @@ def make_scan(name: str, N: int, J: int, Ho: int, Wo: int, *, K: int = 1, seed: 
         phase_coef = 0.24 / probe_radius
     if probe == "disk":
         P = disk_probe(N, probe_radius, phase_coef)[None]
+        if diffuser_phase:
+            # a diffuser in the beam: smooth random phase of about +-diffuser_phase rad
+            d = scipy.ndimage.gaussian_filter(rng.standard_normal((N, N)), 4.0, mode="wrap")
+            P = P * np.exp(1j * diffuser_phase * d / max(np.abs(d).max(), 1e-300))
         if K > 1:
             raise ValueError("disk probe is single-mode; use probe='hg' for K > 1")
     elif probe == "hg":
@@ -219,14 +233,14 @@ def make_scan(name: str, N: int, J: int, Ho: int, Wo: int, *, K: int = 1, seed: 
     positions, nn = fermat_spiral(J, step, Ho, Wo, N)
     # photon scaling from a sample of frames (all of them when J is small)
     sample = np.linspace(0, J - 1, num=min(J, 64)).astype(np.int64)
-    tot = np.array([_frame_intensities(obj, P, positions[i:i + 1], 0, 1)[0].sum() for i in sample])
+    tot = np.array([_frame_intensities(obj, P, positions[i:i + 1], 0, 1, nearfield)[0].sum() for i in sample])
     P = P * math.sqrt(photons / tot.mean())
     mask = detector_gap_mask(N, mask_fraction)
     iobs = np.empty((J, N, N), dtype=np.float32)
     chunk_seeds = s_noise.spawn((J + chunk - 1) // chunk)
     for ci, lo in enumerate(range(0, J, chunk)):
         hi = min(J, lo + chunk)
-        lam = _frame_intensities(obj, P, positions, lo, hi)
+        lam = _frame_intensities(obj, P, positions, lo, hi, nearfield)
         if noise:
             crng = np.random.default_rng(chunk_seeds[ci])
             iobs[lo:hi] = crng.poisson(lam).astype(np.float32)
@@ -237,7 +251,8 @@ def make_scan(name: str, N: int, J: int, Ho: int, Wo: int, *, K: int = 1, seed: 
     probe0 = _blur_complex(P, probe0_blur).astype(np.complex64)
     return Scan(name=name, N=N, K=K, J=J, Ho=Ho, Wo=Wo, positions=positions, iobs=iobs,
                 mask=mask, obj_true=obj, probe_true=P, obj0=obj0, probe0=probe0,
-                photons=photons, seed=seed, step_px=nn, algorithm=algorithm, cycles=cycles)
+                photons=photons, seed=seed, step_px=nn, algorithm=algorithm, cycles=cycles,
+                nearfield=nearfield)
 
 
 # Workload recipes.  Each stands in for one of the paper's workload shapes
@@ -255,6 +270,11 @@ CONFIGS = {
     # finite-difference copy: 32^2 frames, 16 positions
     "ml32fd": dict(N=32, J=16, Ho=64, Wo=64, K=1, seed=4, photons=1e5, step=6.0,
                    probe_radius=6.0, mask_fraction=0.0, algorithm="ML", cycles=50),
+    # near field (Table 1's near-field row, 1 probe): 256^2 frames of a diffuser-modulated
+    # beam, Fresnel propagation factor lambda z / pixel^2 = 200, 1e8 photons per frame
+    "nf256": dict(N=256, J=64, Ho=640, Wo=640, K=1, seed=6, photons=1e8, step=30.0,
+                  probe_radius=90.0, phase_coef=0.0, diffuser_phase=2.0, mask_fraction=0.02,
+                  nearfield=200.0, algorithm="DM", cycles=100),
     # large multi-mode DM: 3 Hermite-Gauss modes 512^2, 6000^2 object, 10000 positions, 1e7 photons
     "modes512": dict(N=512, J=10000, Ho=6000, Wo=6000, K=3, seed=5, photons=1e7, step=60.0,
                      probe="hg", probe_radius=51.2, mode_powers=[0.7, 0.2, 0.1],

@@ -549,3 +549,101 @@ def test_ml_cg_decreases_llk_and_takes_the_model_step():
     assert rel(o1, obj - a * go) < 1e-12 and rel(p1, probe) == 0.0
     o2, p2, l2s = orc.ml_cg(obj, probe, data, 3, update_obj=True, update_probe=True)
     assert l2s[-1] < l2s[0]
+
+
+# ---------------------------------------------------------------- near field
+
+def test_near_field_propagates_a_gaussian_beam_like_fresnel():
+    """A Gaussian exp(-r^2 / (2 s^2)) after a paraxial propagation over lambda z is
+    exp(-r^2 / (2 s^2 (1 + i b))) / (1 + i b), b = lambda z / (2 pi s^2) (s in
+    pixels, lambda z = c pixel^2): the closed form pins the sign and the scale of
+    the transfer function.  The beam stays far from the frame edges, so the
+    periodic discrete propagation matches the continuous one."""
+    N, sig = 128, 4.0
+    y = np.arange(N) - N // 2
+    r2 = y[:, None] ** 2 + y[None, :] ** 2
+    u0 = np.exp(-r2 / (2 * sig ** 2))
+    for c in (10.0, 60.0, 150.0):
+        b = c / (2 * np.pi * sig ** 2)
+        expect = np.exp(-r2 / (2 * sig ** 2 * (1 + 1j * b))) / (1 + 1j * b)
+        got = orc.propagate_near_field(u0, c, +1)
+        assert rel(got, expect) < 1e-8, c
+        # back propagation: the conjugate closed form
+        assert rel(orc.propagate_near_field(u0, c, -1), np.conj(expect)) < 1e-8, c
+
+
+def test_near_field_propagation_is_unitary_and_reversible():
+    rng = np.random.default_rng(40)
+    x = crandn(rng, 3, 48, 48)
+    for c in (0.0, 7.5, 300.0):
+        y = orc.propagate_near_field(x, c, +1)
+        assert abs(np.linalg.norm(y) - np.linalg.norm(x)) < 1e-12 * np.linalg.norm(x)
+        assert rel(orc.propagate_near_field(y, c, -1), x) < 1e-13
+    assert rel(orc.propagate_near_field(x, 0.0, +1), x) < 1e-14
+    # direct transfer values: h = exp(-i pi c (ky^2 + kx^2) / N^2), k signed
+    h = orc.near_field_transfer(8, 3.0)
+    assert abs(h[0, 0] - 1) < 1e-15
+    assert abs(h[1, 2] - np.exp(-1j * np.pi * 3.0 * 5 / 64)) < 1e-15
+    assert abs(h[7, 6] - np.exp(-1j * np.pi * 3.0 * (1 + 4) / 64)) < 1e-15
+    assert abs(h[4, 0] - np.exp(-1j * np.pi * 3.0 * 16 / 64)) < 1e-15
+
+
+def test_near_field_at_zero_distance_projects_in_real_space():
+    """With lambda z = 0 the detector sees the exit wave itself: one near-field AP
+    step replaces |Phi| by sqrt(I) pixel by pixel (checked here without any
+    transform), masked pixels unchanged."""
+    rng = np.random.default_rng(41)
+    N = 16
+    obj = crandn(rng, 30, 30)
+    probe = crandn(rng, 1, N, N)
+    pos = np.array([[0, 0], [5, 9], [14, 3]])
+    iobs = rng.uniform(0.5, 4.0, size=(3, N, N))
+    mask = np.zeros((N, N), bool)
+    mask[2, 5] = True
+    data = orc.Data.make(iobs, pos, mask, nearfield=1e-300)
+    phi = np.stack([probe[0] * obj[r:r + N, c:c + N] for r, c in pos])
+    expect = np.where(mask, phi, np.sqrt(iobs) * np.exp(1j * np.angle(phi)))
+    got = data.from_detector(orc.apply_amplitude(data.to_detector(phi[:, None]), data.iobs, data.mask))[:, 0]
+    assert rel(got, expect) < 1e-12
+
+
+def _near_field_problem(noise=False):
+    s = make_scan("nf32", N=32, J=12, Ho=80, Wo=80, seed=43, photons=1e6, step=8.0,
+                  probe_radius=11.0, phase_coef=0.0, diffuser_phase=1.5, mask_fraction=0.02,
+                  nearfield=12.0, noise=noise)
+    return s, orc.Data.make(s.iobs, s.positions, s.mask, nearfield=s.nearfield)
+
+
+def test_near_field_fixed_point_ap_and_dm():
+    """Noise-free near-field intensities of the true object and probe: one AP and
+    one DM cycle leave both unchanged and the LLK is zero (up to the float32
+    storage of the intensities)."""
+    s, data = _near_field_problem()
+    o, p = s.obj_true, s.probe_true
+    assert 0 <= orc.llk(o, p, data) < 1e-9 * data.iobs.sum()
+    o1, p1, l1 = orc.ap_cycle(o, p, data)
+    assert rel(p1, p) < 1e-6 and rel(o1[orc.object_denominator(p, s.positions, o.shape) > 0],
+                                      o[orc.object_denominator(p, s.positions, o.shape) > 0]) < 1e-6
+    psi0 = orc.obj_probe_to_psi(o, p, s.positions)
+    _, p2, psi2, _ = orc.dm_cycle(o, p, psi0, data)
+    assert rel(p2, p) < 1e-6 and rel(psi2, psi0) < 1e-6
+    # and the same scan read as far field is not a fixed point
+    far = orc.Data.make(s.iobs, s.positions, s.mask)
+    assert orc.llk(o, p, far) > 1e-3 * data.iobs.sum()
+
+
+def test_near_field_ml_grad_directional_finite_differences():
+    s, data = _near_field_problem(noise=True)
+    rng = np.random.default_rng(44)
+    obj = s.obj_true * (1 + 0.05 * crandn(rng, s.Ho, s.Wo))
+    probe = s.probe_true * (1 + 0.05 * crandn(rng, *s.probe_true.shape))
+    L, go, gp = orc.ml_grad(obj, probe, data)
+    assert abs(L - orc.llk(obj, probe, data)) < 1e-9 * abs(L)
+    do = crandn(rng, *obj.shape)
+    dp = crandn(rng, *probe.shape)
+    ho = 1e-6 * np.sqrt(np.mean(np.abs(obj) ** 2))
+    hp = 1e-6 * np.sqrt(np.mean(np.abs(probe) ** 2))
+    fd_o = richardson_fd(lambda t: orc.llk(obj + t * do, probe, data), ho)
+    fd_p = richardson_fd(lambda t: orc.llk(obj, probe + t * dp, data), hp)
+    assert abs(fd_o - float(np.real(np.vdot(go, do)))) < 1e-7 * max(abs(fd_o), 1.0)
+    assert abs(fd_p - float(np.real(np.vdot(gp, dp)))) < 1e-7 * max(abs(fd_p), 1.0)
