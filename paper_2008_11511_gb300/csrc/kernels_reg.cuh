@@ -319,6 +319,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
             dp_s[e] = 0.f;
         }
     }
+    // the block's probe rows are the same for all its frames: this thread's
+    // pass-2 pixels stay in registers (one-mode sizes with register sums)
+    constexpr bool kRegProbe = kRegAcc;
+    float2 pr_r[kRegProbe ? S::I2 : 1][kRegProbe ? M : 1];
+    if constexpr (kRegProbe) {
+#pragma unroll
+        for (int i = 0; i < S::I2; ++i) {
+            const int w = threadIdx.x + i * kThreads;
+            if (w < L * R) {
+                const int line = w / R, k2 = w - line * R;
+                const float2* pr = a.probe + (size_t)(y0 + line) * N + k2;
+#pragma unroll
+                for (int k1 = 0; k1 < M; ++k1) pr_r[i][k1] = __ldg(pr + R * k1);
+            }
+        }
+    }
     __syncthreads();
     for (int b = blockIdx.y; b < nb; b += gridDim.y) {
         const int j = j0 + b;
@@ -360,7 +376,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
                 float2* ps = (mode != BWD_GRAD) ? a.psi + ((size_t)j * N + y) * N + k2 : nullptr;
 #pragma unroll
                 for (int k1 = 0; k1 < M; ++k1) {
-                    const float2 prv = __ldg(pr + R * k1);
+                    float2 prv;
+                    if constexpr (kRegProbe)
+                        prv = pr_r[i][k1];
+                    else
+                        prv = __ldg(pr + R * k1);
                     const float2 obv = ob[R * k1];
                     float2 wv;
                     if (mode == BWD_GRAD) {
