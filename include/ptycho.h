@@ -81,6 +81,13 @@ typedef struct {
     void* psi;              /* device complex64 [J][K][N][N] exit-wave stack Psi (the Ptycho
                                object's Psi array), needed by the AP and DM cycles; may be NULL
                                for LLK and ML */
+    double nearfield;       /* 0: far field (the detector sees FT(Psi); iobs and mask in FFT
+                               order).  c > 0: near field (PropagateNearField, paper Section 4
+                               and the operator table): the detector sees IFT(FT(Psi) h),
+                               h = exp(-i pi c (ky^2 + kx^2) / N^2) with signed frequencies,
+                               c = lambda z / pixel^2; iobs and mask in detector pixels.  Near
+                               field needs K = 1 and N >= 32 (PTX_ERR_UNSUPPORTED otherwise) and
+                               serves the AP / DM cycles and ptx_llk, not the ML calls. */
 } ptx_problem;
 
 /* Device scratch needed by ptx_create for these problems, in bytes.  The caller

@@ -71,6 +71,7 @@ class Problem(ctypes.Structure):
         ("iobs", ctypes.c_void_p),
         ("mask", ctypes.c_void_p),
         ("psi", ctypes.c_void_p),
+        ("nearfield", ctypes.c_double),
     ]
 
 

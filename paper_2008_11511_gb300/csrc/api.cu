@@ -115,6 +115,7 @@ struct Layout {
     size_t pos, mask, acc_obj, acc_probe, llk_part, maxbits, tile_ids, tile_ptr, tile_frames;
     size_t cg_obj, cg_probe, ls_part, cg;  // ML conjugate-gradient state
     size_t mbits;                          // per-thread mask bits of the register column pass
+    size_t nf_t;                           // near-field transfer factors t[k] (complex64, N)
     size_t end;
 };
 
@@ -207,6 +208,11 @@ ptx_status check_problem(const ptx_problem& p, int idx) {
         return fail(PTX_ERR_INVALID_ARG, "problem %d: obj, probe, positions and iobs must be non-null", idx);
     if ((uintptr_t)p.iobs % 16 || (uintptr_t)p.obj % 8 || (uintptr_t)p.probe % 16 || (uintptr_t)p.psi % 16)
         return fail(PTX_ERR_INVALID_ARG, "problem %d: iobs, probe and psi must be 16-byte aligned, obj 8-byte", idx);
+    if (!(p.nearfield >= 0.0) || !std::isfinite(p.nearfield))
+        return fail(PTX_ERR_INVALID_ARG, "problem %d: nearfield must be finite and >= 0", idx);
+    if (p.nearfield > 0.0 && (p.K != 1 || p.N < 32))
+        return fail(PTX_ERR_UNSUPPORTED, "problem %d: the near field needs K = 1 and N >= 32 (K=%d, N=%d)", idx, p.K,
+                    p.N);
     for (int j = 0; j < p.J; ++j) {
         const int r = p.positions[2 * j], c = p.positions[2 * j + 1];
         if (r < 0 || c < 0 || r > p.Ho - p.N || c > p.Wo - p.N)
@@ -281,6 +287,8 @@ size_t layout_problem(ProbHost& h) {
     o = align_up(o + 8 * sizeof(double));
     h.lay.mbits = o;
     if (use_reg_kernels(h.ks, p.K)) o = align_up(o + sizeof(uint32_t) * (size_t)(p.N / h.ks->reg_lines) * kThreads);
+    h.lay.nf_t = o;
+    if (p.nearfield > 0.0) o = align_up(o + sizeof(float2) * (size_t)p.N);
     h.lay.end = o;
     return o;
 }
@@ -423,6 +431,7 @@ ptx_status compute_layout(std::vector<ProbHost>& probs, size_t* spec_off, size_t
         h.lay.ls_part += o;
         h.lay.cg += o;
         h.lay.mbits += o;
+        h.lay.nf_t += o;
         h.lay.end += o;
         o += sz;
         size_t s = (size_t)h.B * kDefaultLanes * h.p.K * h.p.N * h.p.N * sizeof(float2);
@@ -465,6 +474,7 @@ void fill_args(ptx_handle* h, ProbHost& ph) {
     a.ls_part = (double*)(h->scratch + ph.lay.ls_part);
     a.err_flag = h->err_dev;
     a.mbits = (const uint32_t*)(h->scratch + ph.lay.mbits);
+    a.nf_t = ph.p.nearfield > 0.0 ? (const float2*)(h->scratch + ph.lay.nf_t) : nullptr;
     ph.tiles.tile_ids = (const int*)(h->scratch + ph.lay.tile_ids);
     ph.tiles.tile_ptr = (const int*)(h->scratch + ph.lay.tile_ptr);
     ph.tiles.tile_frames = (const int*)(h->scratch + ph.lay.tile_frames);
@@ -597,7 +607,21 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
                 ProfScope ps(h, PTX_KERNEL_ROW_FWD, ls);
                 ks->row_fwd(al, j0, nb, fwd_mode, ls);
             }
-            {
+            if (ph.p.nearfield > 0.0) {
+                // propagate, project at the detector, propagate back
+                {
+                    ProfScope ps(h, PTX_KERNEL_COL, ls);
+                    ks->col_nf(al, nb, +1, ls);
+                }
+                {
+                    ProfScope ps(h, PTX_KERNEL_COL, ls);
+                    ks->row_proj(al, j0, nb, 0, ls);
+                }
+                {
+                    ProfScope ps(h, PTX_KERNEL_COL, ls);
+                    ks->col_nf(al, nb, -1, ls);
+                }
+            } else {
                 ProfScope ps(h, PTX_KERNEL_COL, ls);
                 CUtensorMap tm_spec;
                 const int grid = (h->tma && ph.tma_io && ks->col_tma) ? ks->col_tma_grid() : 0;
@@ -791,6 +815,7 @@ ptx_status ptx_create(ptx_handle** out, const ptx_problem* probs, int32_t nprob,
     cudaStream_t s = (cudaStream_t)stream;
     // zero everything the library owns, then copy positions and mask
     std::vector<std::vector<uint32_t>> mbits_host(h->probs.size());
+    std::vector<std::vector<float>> nf_host(h->probs.size());
     e = cudaMemsetAsync(h->scratch, 0, spec_off, s);
     for (size_t i = 0; e == cudaSuccess && i < h->probs.size(); ++i) {
         ProbHost& ph = h->probs[i];
@@ -807,6 +832,20 @@ ptx_status ptx_create(ptx_handle** out, const ptx_problem* probs, int32_t nprob,
                                     cudaMemcpyHostToDevice, s);
                 if (e != cudaSuccess) break;
             }
+        }
+        if (ph.p.nearfield > 0.0) {
+            // t[k] = exp(-i pi c k^2 / N^2), k signed, in FP64 then rounded: h[ky][kx] = t[ky] t[kx]
+            const int N = ph.p.N;
+            nf_host[i].resize(2 * (size_t)N);
+            for (int k = 0; k < N; ++k) {
+                const double ks = k < (N + 1) / 2 ? k : k - N;
+                const double ph_ = -M_PI * ph.p.nearfield * ks * ks / ((double)N * N);
+                nf_host[i][2 * k] = (float)std::cos(ph_);
+                nf_host[i][2 * k + 1] = (float)std::sin(ph_);
+            }
+            e = cudaMemcpyAsync(h->scratch + ph.lay.nf_t, nf_host[i].data(), sizeof(float) * nf_host[i].size(),
+                                cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) break;
         }
         const std::vector<int>* lists[3] = {&ph.tile_ids, &ph.tile_ptr, &ph.tile_frames};
         const size_t offs[3] = {ph.lay.tile_ids, ph.lay.tile_ptr, ph.lay.tile_frames};
@@ -855,7 +894,12 @@ ptx_status ptx_llk(ptx_handle* h, double* llk_dev, void* stream) {
         for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
             const int nb = std::min(ph.B, ph.p.J - j0);
             ph.ks->row_fwd(ph.args, j0, nb, X_PHI, s);
-            ph.ks->col(ph.args, j0, nb, COL_LLK, s);
+            if (ph.p.nearfield > 0.0) {
+                ph.ks->col_nf(ph.args, nb, +1, s);
+                ph.ks->row_proj(ph.args, j0, nb, 1, s);
+            } else {
+                ph.ks->col(ph.args, j0, nb, COL_LLK, s);
+            }
         }
         k_llk_reduce<<<1, 1024, 0, s>>>(ph.args, ph.p.N / ph.C2, llk_dev + pi);
     }
@@ -869,6 +913,8 @@ ptx_status ptx_ml_grad(ptx_handle* h, void* grad_obj, void* grad_probe, double* 
     if (h->probs.size() != 1) return fail(PTX_ERR_INVALID_ARG, "ptx_ml_grad needs a single-problem handle");
     ptx_status st = check_device(h);
     if (st != PTX_OK) return st;
+    for (const ProbHost& q : h->probs)
+        if (q.p.nearfield > 0.0) return fail(PTX_ERR_UNSUPPORTED, "%s: the near field serves AP, DM and the LLK only", "ptx_ml_grad");
     cudaStream_t s = (cudaStream_t)stream;
     ProbHost& ph = h->probs[0];
     ProbArgs a = ph.args;
@@ -963,6 +1009,8 @@ ptx_status ptx_ml_line_coeffs(ptx_handle* h, const void* d_obj, const void* d_pr
     if (h->probs.size() != 1) return fail(PTX_ERR_INVALID_ARG, "ML needs a single-problem handle");
     ptx_status st = check_device(h);
     if (st != PTX_OK) return st;
+    for (const ProbHost& q : h->probs)
+        if (q.p.nearfield > 0.0) return fail(PTX_ERR_UNSUPPORTED, "%s: the near field serves AP, DM and the LLK only", "ptx_ml_line_coeffs");
     return enqueue_line_coeffs(h, h->probs[0], (const float2*)d_obj, (const float2*)d_probe, coeffs_dev,
                                (cudaStream_t)stream);
 }
@@ -975,6 +1023,8 @@ ptx_status ptx_ml_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, double*
     if (flags & ~known) return fail(PTX_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags & ~known);
     ptx_status st = check_device(h);
     if (st != PTX_OK) return st;
+    for (const ProbHost& q : h->probs)
+        if (q.p.nearfield > 0.0) return fail(PTX_ERR_UNSUPPORTED, "%s: the near field serves AP, DM and the LLK only", "ptx_ml_cycles");
     cudaStream_t s = (cudaStream_t)stream;
     ProbHost& ph = h->probs[0];
     CgArgs c = cg_args(h, ph);

@@ -51,6 +51,7 @@ struct ProbArgs {
     int L1, C2, L3;         // rows per row_fwd block, columns per col block, rows per row_bwd block
     int* err_flag;          // host-mapped flag, set when a bounded device wait gives up (or null)
     const uint32_t* mbits;  // [N / C][256] mask bits per thread of the register column pass
+    const float2* nf_t;     // [N] near-field transfer factors t[k] (h[ky][kx] = t[ky] t[kx]) or null
 };
 
 constexpr int kCycleEndBlocks = 64;  // blocks of the cycle's LLK reduction
@@ -617,6 +618,9 @@ struct KernelSet {
     void (*col_tma)(const void* tm_spec, const void* tm_io, const void* tm_mask, const ProbArgs&, int j0, int nb,
                     int grid, cudaStream_t);
     int (*col_tma_grid)();
+    // near-field passes (K = 1, N with two-pass transforms)
+    void (*col_nf)(const ProbArgs&, int nb, int dir, cudaStream_t);
+    void (*row_proj)(const ProbArgs&, int j0, int nb, int llk_only, cudaStream_t);
 };
 
 const KernelSet* kernel_set(int N);
@@ -635,6 +639,7 @@ size_t smem_row_bwd_t(int K, int L) {
 }  // namespace ptx
 #include "kernels_reg.cuh"
 #include "kernels_tma.cuh"
+#include "kernels_nf.cuh"
 namespace ptx {
 
 template <int N>
@@ -728,6 +733,7 @@ cudaError_t set_attrs_t() {
     if ((e = cudaFuncSetAttribute(k_col_ls<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if constexpr (has_reg<N>()) {
         if ((e = set_attrs_r<N>())) return e;
+        if ((e = set_attrs_nf<N>())) return e;
     }
     return cudaSuccess;
 }
@@ -748,7 +754,9 @@ const KernelSet* make_kernel_set() {
                                  Plan<N>::R,
                                  Plan<N>::M,
                                  ColTma<N>::kOk ? &launch_col_tma<N> : nullptr,
-                                 &col_tma_grid<N>};
+                                 &col_tma_grid<N>,
+                                 &launch_col_nf<N>,
+                                 &launch_row_proj<N>};
     return &ks;
 }
 

@@ -42,10 +42,12 @@ class Ptycho:
     psi:       complex64 (J, K, N, N) CUDA tensor, the exit-wave stack used by
                the AP and DM cycles; allocated when ``with_psi`` is set and none
                is given (LLK and gradient alone do not need it)
+    nearfield: 0 for the far field; c = lambda z / pixel^2 > 0 for the near field
+               (PropagateNearField; iobs and mask then in detector pixels)
     """
 
     def __init__(self, obj: torch.Tensor, probe: torch.Tensor, iobs: torch.Tensor, positions, mask=None,
-                 psi: torch.Tensor | None = None, with_psi: bool = True):
+                 psi: torch.Tensor | None = None, with_psi: bool = True, nearfield: float = 0.0):
         _require_cuda(obj, "obj", torch.complex64)
         _require_cuda(probe, "probe", torch.complex64)
         _require_cuda(iobs, "iobs", torch.float32)
@@ -72,7 +74,8 @@ class Ptycho:
         self._prob = Problem(N=N, K=K, J=J, Ho=self.Ho, Wo=self.Wo, obj=obj.data_ptr(), probe=probe.data_ptr(),
                              positions=pos.ctypes.data, iobs=iobs.data_ptr(),
                              mask=(m.ctypes.data if m is not None else None),
-                             psi=(psi.data_ptr() if psi is not None else None))
+                             psi=(psi.data_ptr() if psi is not None else None), nearfield=float(nearfield))
+        self.nearfield = float(nearfield)
         nbytes = ctypes.c_size_t(0)
         _lib.call("ptx_workspace_bytes", ctypes.byref(self._prob), 1, ctypes.byref(nbytes))
         with torch.cuda.device(self.device):
@@ -249,7 +252,8 @@ class PtychoBatch:
             keep += [pos, m]
             arr[i] = Problem(N=N, K=K, J=J, Ho=obj.shape[0], Wo=obj.shape[1], obj=obj.data_ptr(),
                              probe=probe.data_ptr(), positions=pos.ctypes.data, iobs=iobs.data_ptr(),
-                             mask=(m.ctypes.data if m is not None else None), psi=psi.data_ptr())
+                             mask=(m.ctypes.data if m is not None else None), psi=psi.data_ptr(),
+                             nearfield=float(d.get("nearfield", 0.0)))
             self.items.append(dict(obj=obj, probe=probe, iobs=iobs, psi=psi, positions=pos, mask=m))
         self.device = dev
         self.nprob = len(problems)
