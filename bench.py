@@ -243,6 +243,8 @@ def run_ours(args):
         pb.set_param("tma", args.tma)
     if args.tma_gather is not None:
         pb.set_param("tma_gather", args.tma_gather)
+    if args.tc:
+        pb.set_param("tc", 1)
     stream = torch.cuda.current_stream(dev)
     llk_buf = torch.empty(max(args.steps, args.warmup, 1), dtype=torch.float64, device=dev)
 
@@ -355,7 +357,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "desc": workload_desc(s), "form": "fp32 (plain)",
+                "config": {"workload": WORKLOAD, "desc": workload_desc(s), "form": ("tf32 hi+lo tensor-core DFT stages in the column pass, fp32 elsewhere" if args.tc else "fp32 (plain)"),
                            "parallelism": f"replicas x{ws}",
                            "l2": "inputs larger than L2 (Psi 2.1 GB + I 1.05 GB per replica); no flush"},
                 "roofline": roof, "roofline_cycle": roof_cycle, "kernels": kstats,
@@ -386,6 +388,8 @@ def main():
                     help="column pass staged by tensor copies (1) or the register column pass (0, the library default)")
     ap.add_argument("--tma-gather", type=int, choices=(0, 1), default=None,
                     help="object gather fed by tensor copies (1, the library default) or the plain gather (0)")
+    ap.add_argument("--tc", action="store_true",
+                    help="the split-precision form: column-pass DFT stages on the tensor cores (TF32 hi + lo)")
     ap.add_argument("--batch-frames", type=int, default=0,
                     help="upper bound on frames per batch (library default when 0)")
     ap.add_argument("--timing-only", action="store_true",

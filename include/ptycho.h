@@ -57,9 +57,10 @@ typedef enum {
 
 #define PTX_MAX_MODES 8
 
-/* Supported frame sizes N (N x N frames): products of 2 and 3 that the
- * kernels are built for. */
-#define PTX_SUPPORTED_SIZES {8, 12, 16, 32, 64, 128, 192, 256, 384, 512}
+/* Supported frame sizes N (N x N frames) the kernels are built for: products
+ * of 2 and 3, and of 2 with 5 or 7 (the paper's FFT libraries accept prime
+ * factors up to 7, Table 1 caption; 400^2 frames in Fig. 7). */
+#define PTX_SUPPORTED_SIZES {8, 12, 16, 32, 64, 80, 128, 160, 192, 224, 256, 384, 400, 448, 512}
 
 /* One ptychography problem (the paper's PtychoData plus the current Ptycho
  * object and probe, Section 4). */
@@ -208,8 +209,11 @@ ptx_status ptx_accumulators(ptx_handle* h, int32_t p, void** obj_acc, size_t* ob
  * per SM).  "tma_gather" (1, default: the object numerator / denominator of
  * frames with N >= 64 is gathered from boxes of Psi' and P brought into shared
  * memory by 3D tensor copies through a four-stage mbarrier ring; 0: the plain
- * gather).  Each pair of variants gives the same results up to FP32 rounding
- * order. */
+ * gather).  "tc" (0, default; 1: the AP / DM column pass of one-mode problems
+ * with N = 256 runs its four 16-point DFT stages on the tensor cores:
+ * tcgen05.mma kind::tf32 with hi + lo split operands and FP32 accumulation in
+ * TMEM, relative error about 2^-21 per product instead of FP32's 2^-24).
+ * Each pair of variants gives the same results up to rounding. */
 ptx_status ptx_set_param(ptx_handle* h, const char* name, double value);
 
 /* In-place orthonormal 2D FFT of `nframes` N x N complex64 frames (the FT

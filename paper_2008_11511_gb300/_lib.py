@@ -32,7 +32,7 @@ PTX_ML_RESTART = 0x20
 PTX_MAX_MODES = 8
 PTX_ALGO_AP = 0
 PTX_ALGO_DM = 1
-SUPPORTED_SIZES = (8, 12, 16, 32, 64, 128, 192, 256, 384, 512)
+SUPPORTED_SIZES = (8, 12, 16, 32, 64, 80, 128, 160, 192, 224, 256, 384, 400, 448, 512)
 
 # Every symbol include/ptycho.h declares.
 EXPORTS = (

@@ -27,6 +27,11 @@ const KernelSet* kernel_set_192();
 const KernelSet* kernel_set_256();
 const KernelSet* kernel_set_384();
 const KernelSet* kernel_set_512();
+const KernelSet* kernel_set_80();
+const KernelSet* kernel_set_160();
+const KernelSet* kernel_set_224();
+const KernelSet* kernel_set_400();
+const KernelSet* kernel_set_448();
 cudaError_t set_attrs_8();
 cudaError_t set_attrs_12();
 cudaError_t set_attrs_16();
@@ -37,6 +42,11 @@ cudaError_t set_attrs_192();
 cudaError_t set_attrs_256();
 cudaError_t set_attrs_384();
 cudaError_t set_attrs_512();
+cudaError_t set_attrs_80();
+cudaError_t set_attrs_160();
+cudaError_t set_attrs_224();
+cudaError_t set_attrs_400();
+cudaError_t set_attrs_448();
 
 const KernelSet* kernel_set(int N) {
     switch (N) {
@@ -50,6 +60,11 @@ const KernelSet* kernel_set(int N) {
         case 256: return kernel_set_256();
         case 384: return kernel_set_384();
         case 512: return kernel_set_512();
+        case 80: return kernel_set_80();
+        case 160: return kernel_set_160();
+        case 224: return kernel_set_224();
+        case 400: return kernel_set_400();
+        case 448: return kernel_set_448();
         default: return nullptr;
     }
 }
@@ -63,7 +78,8 @@ static cudaError_t ensure_attributes() {
     if (dev < 32 && (done_mask >> dev) & 1) return cudaSuccess;
     cudaError_t (*fns[])() = {set_attrs_8,   set_attrs_12,  set_attrs_16,  set_attrs_32,  set_attrs_64,
                               set_attrs_128, set_attrs_192, set_attrs_256, set_attrs_384, set_attrs_512,
-                              set_attrs_gather_tma};
+                              set_attrs_80,  set_attrs_160, set_attrs_224, set_attrs_400, set_attrs_448,
+                              set_attrs_gather_tma, set_attrs_tc};
     for (auto f : fns)
         if ((e = f()) != cudaSuccess) return e;
     if (dev < 32) done_mask |= 1 << dev;
@@ -372,6 +388,7 @@ struct ptx_handle {
     int batch_cap = 0;  // ptx_set_param "batch_frames"
     int tma = 0;        // ptx_set_param "tma": column pass fed by tensor copies where available
     int tma_gather = 1; // ptx_set_param "tma_gather": object gather fed by tensor copies where available
+    int tc = 0;         // ptx_set_param "tc": column pass with the DFT stages on the tensor cores (N = 256, K = 1)
     // flag in mapped pinned host memory that a device wait sets when it gives up
     int* err_host = nullptr;
     int* err_dev = nullptr;
@@ -621,6 +638,9 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
                     ProfScope ps(h, PTX_KERNEL_COL, ls);
                     ks->col_nf(al, nb, -1, ls);
                 }
+            } else if (h->tc && ph.p.N == 256 && ph.p.K == 1) {
+                ProfScope ps(h, PTX_KERNEL_COL, ls);
+                launch_col_tc(al, j0, nb, ls);
             } else {
                 ProfScope ps(h, PTX_KERNEL_COL, ls);
                 CUtensorMap tm_spec;
@@ -659,7 +679,7 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
 }
 
 ptx_status get_graph(ptx_handle* h, const std::vector<int>& algos, uint32_t flags, cudaGraphExec_t* out) {
-    GraphKey key{algos, flags, h->lanes, h->tma | (h->tma_gather << 1)};
+    GraphKey key{algos, flags, h->lanes, h->tma | (h->tma_gather << 1) | (h->tc << 2)};
     auto it = h->graphs.find(key);
     if (it != h->graphs.end()) {
         *out = it->second;
@@ -1103,6 +1123,9 @@ ptx_status ptx_set_param(ptx_handle* h, const char* name, double value) {
     } else if (!strcmp(name, "tma")) {
         if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "tma must be 0 or 1");
         h->tma = (int)value;
+    } else if (!strcmp(name, "tc")) {
+        if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "tc must be 0 or 1");
+        h->tc = (int)value;
     } else if (!strcmp(name, "tma_gather")) {
         if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "tma_gather must be 0 or 1");
         h->tma_gather = (int)value;

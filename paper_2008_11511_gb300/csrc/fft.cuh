@@ -188,7 +188,61 @@ struct DftComposite {
     }
 };
 
+// Prime R (5, 7): the DFT written out, out[k] = v[0] + sum_{n>0} v[n] w^(n k),
+// pairing n and R - n so that each pair costs one complex sum and one
+// difference: out[k] = v0 + sum_{n<=R/2} [(v_n + v_{R-n}) cos(2 pi n k / R)
+// + i DIR (v_n - v_{R-n}) sin(2 pi n k / R)].
+template <int R, int DIR>
+struct DftPrime {
+    __device__ __forceinline__ static void run(float2* v) {
+        constexpr int H = R / 2;
+        float2 sp[H], sm[H];
+#pragma unroll
+        for (int n = 1; n <= H; ++n) {
+            sp[n - 1] = cadd(v[n], v[R - n]);
+            sm[n - 1] = csub(v[n], v[R - n]);
+        }
+        float2 out[R];
+        float2 dc = v[0];
+#pragma unroll
+        for (int n = 0; n < H; ++n) dc = cadd(dc, sp[n]);
+        out[0] = dc;
+        apply<1>(v[0], sp, sm, out);
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = out[k];
+    }
+    template <int K>
+    __device__ __forceinline__ static void apply(float2 v0, const float2* sp, const float2* sm, float2* out) {
+        if constexpr (K <= R / 2) {
+            constexpr int H = R / 2;
+            float2 re = v0, im = make_float2(0.f, 0.f);
+            term<K, 1>(sp, sm, re, im);
+            // out[K] = re + i DIR im, out[R - K] = re - i DIR im
+            const float2 t = mul_i<DIR>(im);
+            out[K] = cadd(re, t);
+            out[R - K] = csub(re, t);
+            (void)H;
+            apply<K + 1>(v0, sp, sm, out);
+        }
+    }
+    template <int K, int N1>
+    __device__ __forceinline__ static void term(const float2* sp, const float2* sm, float2& re, float2& im) {
+        if constexpr (N1 <= R / 2) {
+            constexpr float c = (float)tw_cos(N1 * K, R);
+            constexpr float s = (float)tw_sin(N1 * K, R);
+            re = make_float2(fmaf(sp[N1 - 1].x, c, re.x), fmaf(sp[N1 - 1].y, c, re.y));
+            im = make_float2(fmaf(sm[N1 - 1].x, s, im.x), fmaf(sm[N1 - 1].y, s, im.y));
+            term<K, N1 + 1>(sp, sm, re, im);
+        }
+    }
+};
+template <int DIR> struct Dft<5, DIR> : DftPrime<5, DIR> {};
+template <int DIR> struct Dft<7, DIR> : DftPrime<7, DIR> {};
 template <int DIR> struct Dft<6, DIR> : DftComposite<3, 2, DIR> {};
+template <int DIR> struct Dft<10, DIR> : DftComposite<5, 2, DIR> {};
+template <int DIR> struct Dft<14, DIR> : DftComposite<7, 2, DIR> {};
+template <int DIR> struct Dft<20, DIR> : DftComposite<5, 4, DIR> {};
+template <int DIR> struct Dft<28, DIR> : DftComposite<7, 4, DIR> {};
 template <int DIR> struct Dft<8, DIR> : DftComposite<4, 2, DIR> {};
 template <int DIR> struct Dft<12, DIR> : DftComposite<4, 3, DIR> {};
 template <int DIR> struct Dft<16, DIR> : DftComposite<4, 4, DIR> {};
@@ -211,6 +265,12 @@ template <> struct Plan<192> { static constexpr int R = 16, M = 12; };
 template <> struct Plan<256> { static constexpr int R = 16, M = 16; };
 template <> struct Plan<384> { static constexpr int R = 16, M = 24; };
 template <> struct Plan<512> { static constexpr int R = 16, M = 32; };
+// sizes with factors 5 and 7 (the paper's FFT libraries accept radix up to 7)
+template <> struct Plan<80>  { static constexpr int R = 10, M = 8;  };
+template <> struct Plan<160> { static constexpr int R = 16, M = 10; };
+template <> struct Plan<224> { static constexpr int R = 16, M = 14; };
+template <> struct Plan<400> { static constexpr int R = 20, M = 20; };
+template <> struct Plan<448> { static constexpr int R = 16, M = 28; };
 
 // Line pitch (in complex elements) in shared memory: room for the padded
 // intermediate layout, and odd so that column-major accesses are conflict-free.

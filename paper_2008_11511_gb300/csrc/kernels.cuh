@@ -534,6 +534,10 @@ struct TileLists {
     int ntx;                 // tiles per object row
 };
 __global__ void k_obj_gather(ProbArgs a, TileLists tl, int fuse_max);
+// Column pass with the 16-point DFT stages on the tensor cores (tcgen05, TF32
+// hi + lo split; N = 256, one mode), the split-precision form of k_col_r<256>.
+void launch_col_tc(const ProbArgs& a, int j0, int nb, cudaStream_t s);
+cudaError_t set_attrs_tc();
 // The same gather fed by 3D tensor copies (32 x 32 tiles, N >= 64).
 void launch_obj_gather_tma(const void* tm_psi, const void* tm_probe, const ProbArgs& a, const TileLists& tl,
                            int ntiles, int fuse_max, cudaStream_t s);

@@ -21,7 +21,7 @@ namespace ptx {
 // row passes, columns for the column pass).
 template <int N>
 __host__ __device__ constexpr int reg_lines() {
-    return N >= 512 ? 8 : (N == 384 ? 8 : (N == 192 ? 16 : (4096 / N > N ? N : 4096 / N)));
+    return N >= 384 ? 8 : ((N == 192 || N == 80 || N == 160 || N == 224) ? 16 : (4096 / N > N ? N : 4096 / N));
 }
 // Shared-memory pitch of a line: room for both padded intermediate layouts
 // (R (M+1) and M (R+1) elements), odd.
@@ -37,9 +37,9 @@ struct RegShape {
     static constexpr int I2 = (L * R + kThreads - 1) / kThreads;  // pass-2 items per thread
     // blocks per SM the register budget is sized for: large codelets (24, 32
     // points) need more registers per thread
-    static constexpr int MinBlocks = (R > M ? R : M) >= 24 ? 2 : 5;
+    static constexpr int MinBlocks = (R > M ? R : M) >= 20 ? 2 : 5;
     // the column pass also holds its pixels' intensities in registers
-    static constexpr int ColMinBlocks = (R > M ? R : M) >= 24 ? 2 : 4;
+    static constexpr int ColMinBlocks = (R > M ? R : M) >= 20 ? 2 : 4;
     static_assert(M > 1, "register kernels need two passes");
     static_assert(N % L == 0, "lines per block must divide N");
 };

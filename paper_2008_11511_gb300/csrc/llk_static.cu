@@ -44,6 +44,11 @@ cudaError_t set_attrs_192();
 cudaError_t set_attrs_256();
 cudaError_t set_attrs_384();
 cudaError_t set_attrs_512();
+cudaError_t set_attrs_80();
+cudaError_t set_attrs_160();
+cudaError_t set_attrs_224();
+cudaError_t set_attrs_400();
+cudaError_t set_attrs_448();
 }  // namespace ptx
 
 namespace {
@@ -87,7 +92,8 @@ ptx_status setup_device(int dev, unsigned char** out) {
     if (e != cudaSuccess) return fail(PTX_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
     cudaError_t (*attrs[])() = {ptx::set_attrs_8,   ptx::set_attrs_12,  ptx::set_attrs_16,  ptx::set_attrs_32,
                                 ptx::set_attrs_64,  ptx::set_attrs_128, ptx::set_attrs_192, ptx::set_attrs_256,
-                                ptx::set_attrs_384, ptx::set_attrs_512};
+                                ptx::set_attrs_384, ptx::set_attrs_512, ptx::set_attrs_80,  ptx::set_attrs_160,
+                                ptx::set_attrs_224, ptx::set_attrs_400, ptx::set_attrs_448};
     for (auto f : attrs)
         if ((e = f()) != cudaSuccess) return fail(PTX_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
     if ((e = cudaMemset((char*)ptr + kMaskOff, 0, kMaskBytes)) != cudaSuccess ||

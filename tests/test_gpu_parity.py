@@ -91,7 +91,7 @@ def warm(cfg, J=None, n_ap=1, **over):
 
 # ------------------------------------------------------------------ FT / IFT
 
-@pytest.mark.parametrize("N", [8, 12, 16, 32, 64, 128, 192, 256, 384, 512])
+@pytest.mark.parametrize("N", [8, 12, 16, 32, 64, 80, 128, 160, 192, 224, 256, 384, 400, 448, 512])
 def test_fft2_matches_oracle(N):
     from paper_2008_11511_gb300 import fft2
     rng = np.random.default_rng(N)
@@ -105,7 +105,7 @@ def test_fft2_matches_oracle(N):
     check_close(f"IFT(FT) N={N}", X.cpu().numpy(), x, 3e-6)
 
 
-@pytest.mark.parametrize("N", [32, 192, 256])
+@pytest.mark.parametrize("N", [32, 80, 192, 224, 256, 400])
 def test_fft2_special_inputs(N):
     from paper_2008_11511_gb300 import fft2
     d = np.zeros((3, N, N), np.complex64)
@@ -314,7 +314,7 @@ def test_zero_extra_mode_equals_single_mode():
 
 # ------------------------------------------------------------------ edge cases
 
-@pytest.mark.parametrize("N", [32, 192, 384])
+@pytest.mark.parametrize("N", [32, 80, 160, 192, 224, 384, 400, 448])
 def test_other_frame_sizes_ap(N):
     s = make_scan(f"n{N}", N=N, J=12, Ho=N + 40, Wo=N + 24, seed=N, photons=1e5, step=N / 12,
                   probe_radius=N * 0.18, mask_fraction=0.02)
@@ -505,7 +505,8 @@ def test_configured_start_is_at_the_float32_floor(cfg, J):
     pb.close()
 
 
-@pytest.mark.parametrize("N,J", [(64, 700), (128, 300), (192, 200), (384, 60), (512, 40)])
+@pytest.mark.parametrize("N,J", [(64, 700), (80, 600), (128, 300), (160, 300), (192, 200), (224, 160), (384, 60),
+                                 (400, 50), (448, 40), (512, 40)])
 def test_several_frames_per_block_all_sizes(N, J):
     """Enough frames that every inverse-row block handles several frames (its
     staged rows are refilled between frames), for each register-kernel size:
@@ -530,16 +531,18 @@ def test_several_frames_per_block_all_sizes(N, J):
     pb.close()
 
 
-@pytest.mark.parametrize("tma", [0, 1])
+@pytest.mark.parametrize("form", ["register", "tma", "tc"])
 @pytest.mark.parametrize("lanes,batch", [(1, 0), (2, 0), (2, 37)])
-def test_dm256_column_pass_variants(tma, lanes, batch):
-    """The 256x256 column pass with and without tensor-copy staging, in one and
+def test_dm256_column_pass_variants(form, lanes, batch):
+    """The 256x256 column pass in its three forms — FP32 registers, FP32 fed by
+    tensor copies, DFT stages on the tensor cores (TF32 hi + lo) — in one and
     two lanes and with a batch size (37 frames) that leaves ragged batches and a
     partial last wave of the persistent grid: three DM cycles and one AP cycle
-    against the oracle."""
+    against the oracle, at the FP32 tolerance."""
     s, o0, p0 = warm("dm256", J=150, Ho=640, Wo=640)
     pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
-    pb.set_param("tma", tma)
+    pb.set_param("tma", int(form == "tma"))
+    pb.set_param("tc", int(form == "tc"))
     pb.set_param("lanes", lanes)
     pb.set_param("batch_frames", batch)
     llk = pb.dm(3, init_psi=True).cpu().numpy()
@@ -548,7 +551,8 @@ def test_dm256_column_pass_variants(tma, lanes, batch):
     np.testing.assert_allclose(llk, llk_ref, rtol=TOL1 * 3)
     pb.close()
     pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
-    pb.set_param("tma", tma)
+    pb.set_param("tma", int(form == "tma"))
+    pb.set_param("tc", int(form == "tc"))
     pb.set_param("lanes", lanes)
     pb.set_param("batch_frames", batch)
     l1 = pb.ap(1).cpu().numpy()
