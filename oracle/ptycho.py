@@ -41,6 +41,12 @@ Readings of points the paper leaves open (each is listed in the design doc):
   scan.)
 * The per-cycle LLK is that of the wave being projected (Phi for AP, 2 Phi - Psi
   for DM); ``llk`` gives the exact L(O, P).
+* Incoherent background (the Ptycho object's background, optimised in AP;
+  the paper cites Marchesini et al. 2013 without a formula): one N x N array B
+  >= 0 added to every frame's model intensity (LLK, projection, gradient);
+  the projection scales it like a mode, and ``ap_cycle_background`` replaces B
+  by the mean over frames of the scaled backgrounds.  B = 0 stays 0 (the update
+  is multiplicative), so a reconstruction starts it at a positive guess.
 * Near field (PropagateNearField; the paper names the operator and the near /
   far field flag but gives no formula): paraxial Fresnel propagation in
   Fourier space, IFT(FT(x) exp(-i pi lambda z q^2)), q = k / (N pixel) the
@@ -82,15 +88,22 @@ class Data:
     positions: np.ndarray  # int64 (J, 2) top-left (row, col)
     mask: np.ndarray       # bool (N, N), True = bad pixel (free)
     nearfield: float = 0.0
+    background: np.ndarray | None = None  # float64 (N, N) incoherent background, or None
 
     @staticmethod
-    def make(iobs, positions, mask=None, nearfield=0.0):
+    def make(iobs, positions, mask=None, nearfield=0.0, background=None):
         iobs = np.asarray(iobs, dtype=np.float64)
         N = iobs.shape[-1]
         if mask is None:
             mask = np.zeros((N, N), dtype=bool)
+        bg = None if background is None else np.asarray(background, dtype=np.float64).reshape(N, N)
         return Data(iobs=iobs, positions=np.asarray(positions, dtype=np.int64),
-                    mask=np.asarray(mask).astype(bool), nearfield=float(nearfield))
+                    mask=np.asarray(mask).astype(bool), nearfield=float(nearfield), background=bg)
+
+    @property
+    def bg(self):
+        """The incoherent background added to every frame's model intensity (0 if none)."""
+        return 0.0 if self.background is None else self.background
 
     @property
     def J(self):
@@ -156,13 +169,16 @@ def calc_intensity(psi_hat):
     return (psi_hat.real ** 2 + psi_hat.imag ** 2).sum(axis=-3)
 
 
-def apply_amplitude(psi_hat, iobs, mask):
+def apply_amplitude(psi_hat, iobs, mask, background=0.0):
     """ApplyAmplitude: in Fourier space replace the modulus by the observed
     amplitude, with one common factor for all modes; masked pixels unchanged.
+    An incoherent background B is one more incoherent component of the model
+    intensity (Marchesini et al. 2013's augmented projection): the factor is
+    sqrt(I_obs) / sqrt(sum_k |Psi_k|^2 + B).
 
     psi_hat: (..., K, N, N); iobs: (..., N, N); mask: (N, N) bool.
     """
-    ic = calc_intensity(psi_hat)
+    ic = calc_intensity(psi_hat) + background
     s = np.sqrt(np.maximum(iobs, 0.0)) / np.maximum(np.sqrt(ic), AMP_FLOOR)
     s = np.where(mask, 1.0, s)
     return psi_hat * s[..., None, :, :]
@@ -277,10 +293,40 @@ def ap_cycle(obj, probe, data: Data, alpha_obj=1e-2, alpha_probe=1e-2,
         pos = data.positions[lo:hi]
         phi = obj_probe_to_psi(obj, probe, pos)
         phi_hat = data.to_detector(phi)
-        llk += llk_poisson(calc_intensity(phi_hat), data.iobs[lo:hi], data.mask)
-        psi[lo:hi] = data.from_detector(apply_amplitude(phi_hat, data.iobs[lo:hi], data.mask))
+        llk += llk_poisson(calc_intensity(phi_hat) + data.bg, data.iobs[lo:hi], data.mask)
+        psi[lo:hi] = data.from_detector(apply_amplitude(phi_hat, data.iobs[lo:hi], data.mask, data.bg))
     obj, probe = overlap_update(obj, probe, psi, data.positions, alpha_obj, alpha_probe, update_obj, update_probe)
     return obj, probe, llk
+
+
+def ap_cycle_background(obj, probe, background, data: Data, alpha_obj=1e-2, alpha_probe=1e-2,
+                        update_obj=True, update_probe=True):
+    """AP cycle with the incoherent background optimisation (paper Section 4:
+    "incoherent background optimisation (AP)", Marchesini et al. 2013).  The
+    background B is an incoherent component of every frame's model intensity,
+    I_c + B; the augmented amplitude projection scales it with the frames' modes
+    (B_j' = s_j^2 B, s_j = sqrt(I_o,j / (I_c,j + B))), and the new background is
+    their least-squares common value, the mean over frames:
+        B <- B * (1 / J) sum_j I_o,j / (I_c,j + B)     (unmasked pixels; masked keep B).
+    The waves are projected with the current B; O, P are updated from them as in
+    ``ap_cycle``.  Returns (obj, probe, background, llk)."""
+    background = np.asarray(background, dtype=np.float64)
+    d = Data(iobs=data.iobs, positions=data.positions, mask=data.mask, nearfield=data.nearfield, background=background)
+    obj = np.asarray(obj, dtype=np.complex128)
+    probe = np.asarray(probe, dtype=np.complex128)
+    psi = np.empty((d.J,) + probe.shape, dtype=np.complex128)
+    llk = 0.0
+    ratio = np.zeros_like(background)
+    for lo, hi in _stacks(d.J):
+        phi = obj_probe_to_psi(obj, probe, d.positions[lo:hi])
+        phi_hat = d.to_detector(phi)
+        ic = calc_intensity(phi_hat) + background
+        llk += llk_poisson(ic, d.iobs[lo:hi], d.mask)
+        ratio += (np.maximum(d.iobs[lo:hi], 0.0) / np.maximum(ic, ICALC_FLOOR)).sum(axis=0)
+        psi[lo:hi] = d.from_detector(apply_amplitude(phi_hat, d.iobs[lo:hi], d.mask, background))
+    new_bg = np.where(d.mask, background, background * ratio / d.J)
+    obj, probe = overlap_update(obj, probe, psi, d.positions, alpha_obj, alpha_probe, update_obj, update_probe)
+    return obj, probe, new_bg, llk
 
 
 def dm_cycle(obj, probe, psi, data: Data, alpha_obj=1e-2, alpha_probe=1e-2,
@@ -305,8 +351,8 @@ def dm_cycle(obj, probe, psi, data: Data, alpha_obj=1e-2, alpha_probe=1e-2,
             psi[lo:hi] = phi
         x = 2.0 * phi - psi[lo:hi]
         x_hat = data.to_detector(x)
-        llk += llk_poisson(calc_intensity(x_hat), data.iobs[lo:hi], data.mask)
-        x_proj = data.from_detector(apply_amplitude(x_hat, data.iobs[lo:hi], data.mask))
+        llk += llk_poisson(calc_intensity(x_hat) + data.bg, data.iobs[lo:hi], data.mask)
+        x_proj = data.from_detector(apply_amplitude(x_hat, data.iobs[lo:hi], data.mask, data.bg))
         psi[lo:hi] = psi[lo:hi] + x_proj - phi
     obj, probe = overlap_update(obj, probe, psi, data.positions, alpha_obj, alpha_probe, update_obj, update_probe)
     return obj, probe, psi, llk
@@ -319,7 +365,7 @@ def llk(obj, probe, data: Data):
     total = 0.0
     for lo, hi in _stacks(data.J):
         phi_hat = data.to_detector(obj_probe_to_psi(obj, probe, data.positions[lo:hi]))
-        total += llk_poisson(calc_intensity(phi_hat), data.iobs[lo:hi], data.mask)
+        total += llk_poisson(calc_intensity(phi_hat) + data.bg, data.iobs[lo:hi], data.mask)
     return total
 
 
@@ -346,7 +392,7 @@ def ml_grad(obj, probe, data: Data):
     for lo, hi in _stacks(data.J):
         pos = data.positions[lo:hi]
         phi_hat = data.to_detector(obj_probe_to_psi(obj, probe, pos))
-        ic = calc_intensity(phi_hat)
+        ic = calc_intensity(phi_hat) + data.bg
         io = np.maximum(data.iobs[lo:hi], 0.0)
         total += llk_poisson(ic, data.iobs[lo:hi], data.mask)
         w = np.where(data.mask, 0.0, 2.0 * (1.0 - io / np.maximum(ic, ICALC_FLOOR)))
@@ -379,7 +425,7 @@ def ml_line_coeffs(obj, probe, d_obj, d_probe, data: Data):
         A = data.to_detector(obj_probe_to_psi(obj, probe, pos))
         B = data.to_detector(obj_probe_to_psi(obj, d_probe, pos) + obj_probe_to_psi(d_obj, probe, pos))
         C = data.to_detector(obj_probe_to_psi(d_obj, d_probe, pos))
-        ic = calc_intensity(A)
+        ic = calc_intensity(A) + data.bg
         di = 2.0 * (np.conj(A) * B).real.sum(axis=-3)
         d2i = 2.0 * ((B.real ** 2 + B.imag ** 2) + 2.0 * (np.conj(A) * C).real).sum(axis=-3)
         io = np.maximum(data.iobs[lo:hi], 0.0)
@@ -467,7 +513,7 @@ def frames_llk(obj, probe, data: Data, frames):
     probe = np.asarray(probe, dtype=np.complex128)
     frames = np.asarray(frames)
     phi_hat = data.to_detector(obj_probe_to_psi(obj, probe, data.positions[frames]))
-    return llk_poisson(calc_intensity(phi_hat), data.iobs[frames], data.mask)
+    return llk_poisson(calc_intensity(phi_hat) + data.bg, data.iobs[frames], data.mask)
 
 
 def object_denominator(probe, positions, shape_obj):

@@ -647,3 +647,77 @@ def test_near_field_ml_grad_directional_finite_differences():
     fd_p = richardson_fd(lambda t: orc.llk(obj, probe + t * dp, data), hp)
     assert abs(fd_o - float(np.real(np.vdot(go, do)))) < 1e-7 * max(abs(fd_o), 1.0)
     assert abs(fd_p - float(np.real(np.vdot(gp, dp)))) < 1e-7 * max(abs(fd_p), 1.0)
+
+
+# ---------------------------------------------------------------- incoherent background
+
+def _background_problem(bg_level=3.0, noise=False):
+    """Far-field data whose intensities carry a known smooth background B_true
+    (model: |FT(P O)|^2 + B_true, computed here with numpy, not the oracle)."""
+    s = make_scan("bg32", N=32, J=16, Ho=64, Wo=64, seed=61, photons=1e5, step=6.0,
+                  probe_radius=6.0, mask_fraction=0.0, noise=False)
+    yy, xx = np.mgrid[0:32, 0:32]
+    b_true = bg_level * (1.0 + 0.5 * np.cos(2 * np.pi * yy / 32) * np.cos(2 * np.pi * xx / 32))
+    iobs = noise_free_intensity(s.obj_true, s.probe_true, s.positions) + b_true[None]
+    if noise:
+        iobs = np.random.default_rng(62).poisson(iobs).astype(np.float64)
+    return s, iobs, b_true
+
+
+def test_background_llk_is_poisson_with_the_added_rate():
+    """With a background the LLK terms are the Poisson deviance at rate I_c + B
+    (checked against scipy.stats)."""
+    s, iobs, b = _background_problem(noise=True)
+    data = orc.Data.make(iobs, s.positions, None, background=0.7 * b)
+    rng = np.random.default_rng(63)
+    obj = s.obj_true * (1 + 0.03 * crandn(rng, s.Ho, s.Wo))
+    ic = noise_free_intensity(obj, s.probe_true, s.positions) + 0.7 * b[None]
+    ref = float(-(scipy.stats.poisson.logpmf(iobs, ic) - scipy.stats.poisson.logpmf(iobs, iobs)).sum())
+    assert abs(orc.llk(obj, s.probe_true, data) - ref) < 1e-9 * abs(ref)
+
+
+def test_background_fixed_point_and_zero_llk():
+    """Noise-free data with the true background: the background AP cycle leaves
+    O, P and B unchanged and the LLK is zero."""
+    s, iobs, b = _background_problem()
+    data = orc.Data.make(iobs, s.positions, None)
+    o1, p1, b1, l1 = orc.ap_cycle_background(s.obj_true, s.probe_true, b, data)
+    assert abs(l1) < 1e-10 * iobs.sum()
+    assert rel(b1, b) < 1e-12 and rel(p1, s.probe_true) < 1e-10
+    ill = orc.object_denominator(s.probe_true, s.positions, s.obj_true.shape) > 0
+    assert rel(o1[ill], s.obj_true[ill]) < 1e-10
+
+
+def test_background_update_is_an_em_step_towards_the_true_background():
+    """With O and P held at the truth the background update is the EM step of
+    a Poisson mixture (component B in I_c + B): from a guess twice too high or
+    four times too low the LLK never increases, and where the background
+    dominates the model (I_c < B_true) B reaches B_true; everywhere it moves
+    towards it."""
+    s, iobs, b = _background_problem(bg_level=40.0)
+    data = orc.Data.make(iobs, s.positions, None)
+    ic_max = noise_free_intensity(s.obj_true, s.probe_true, s.positions).max(axis=0)
+    dark = ic_max < b
+    assert dark.sum() > 50
+    for b0 in (2.0 * b, 0.25 * b):
+        bg, llks = b0, []
+        for _ in range(150):
+            _, _, bg, l = orc.ap_cycle_background(s.obj_true, s.probe_true, bg, data,
+                                                  update_obj=False, update_probe=False)
+            llks.append(l)
+        assert all(b2 <= b1 * (1 + 1e-12) for b1, b2 in zip(llks[:-1], llks[1:]))
+        assert rel(bg[dark], b[dark]) < 1e-3, rel(bg[dark], b[dark])
+        assert rel(bg, b) < 0.5 * rel(b0, b)
+
+
+def test_background_gradient_finite_differences():
+    s, iobs, b = _background_problem(noise=True)
+    data = orc.Data.make(iobs, s.positions, None, background=b)
+    rng = np.random.default_rng(64)
+    obj = s.obj_true * (1 + 0.05 * crandn(rng, s.Ho, s.Wo))
+    probe = s.probe_true.copy()
+    L, go, gp = orc.ml_grad(obj, probe, data)
+    do = crandn(rng, *obj.shape)
+    ho = 1e-6 * np.sqrt(np.mean(np.abs(obj) ** 2))
+    fd = richardson_fd(lambda t: orc.llk(obj + t * do, probe, data), ho)
+    assert abs(fd - float(np.real(np.vdot(go, do)))) < 1e-7 * max(abs(fd), 1.0)
