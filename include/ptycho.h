@@ -54,6 +54,7 @@ typedef enum {
 #define PTX_DM_INIT_PSI  0x4u  /* DM only: set Psi = P . O[r_j] before the first cycle */
 #define PTX_NO_NORMALISE 0x8u  /* accumulate N_O, D_O, N_P, D_P but do not normalise (data-parallel split) */
 #define PTX_NO_GRAPH     0x10u /* enqueue kernels directly instead of replaying a captured CUDA graph */
+#define PTX_UPDATE_BACKGROUND 0x40u /* AP only: update the incoherent background of the problems that have one */
 
 #define PTX_MAX_MODES 8
 
@@ -89,6 +90,12 @@ typedef struct {
                                c = lambda z / pixel^2; iobs and mask in detector pixels.  Near
                                field needs K = 1 and N >= 32 (PTX_ERR_UNSUPPORTED otherwise) and
                                serves the AP / DM cycles and ptx_llk, not the ML calls. */
+    float* background;      /* device float32 [N][N] incoherent background B >= 0 (paper Section 4,
+                               the Ptycho object's background), in the layout of iobs, or NULL.
+                               When given, every frame's model intensity is I_c + B (LLK,
+                               projection, gradient, line search) and AP cycles with
+                               PTX_UPDATE_BACKGROUND replace B by B (1/J) sum_j I_o / (I_c + B)
+                               on unmasked pixels (the update is multiplicative: start B > 0). */
 } ptx_problem;
 
 /* Device scratch needed by ptx_create for these problems, in bytes.  The caller

@@ -1,4 +1,4 @@
-"""FP64 CPU oracle of the far-field ptychography cycle (AP, DM, LLK, ML gradient).
+"""FP64 CPU oracle of the ptychography cycle (AP, DM, LLK, ML gradient; far and near field).
 
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and
 the CPU-baseline legs of ``bench.py``, never by the product package.  It shares

@@ -539,6 +539,7 @@ __all__ = [
     "llk_poisson", "psi_to_probe_sums", "psi_to_obj_sums", "psi_to_obj_probe_sums", "inertia_update",
     "normalise", "overlap_update", "ap_cycle", "dm_cycle", "llk", "ml_grad",
     "cycles", "dm_frame_update", "frames_llk", "object_denominator", "frames_covering", "ml_line_coeffs", "ml_cg",
+    "ap_cycle_background", "near_field_transfer", "propagate_near_field",
     "ICALC_FLOOR", "AMP_FLOOR", "STACK",
 ]
 

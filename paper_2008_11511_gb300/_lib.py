@@ -29,6 +29,7 @@ PTX_DM_INIT_PSI = 0x4
 PTX_NO_NORMALISE = 0x8
 PTX_NO_GRAPH = 0x10
 PTX_ML_RESTART = 0x20
+PTX_UPDATE_BACKGROUND = 0x40
 PTX_MAX_MODES = 8
 PTX_ALGO_AP = 0
 PTX_ALGO_DM = 1
@@ -72,6 +73,7 @@ class Problem(ctypes.Structure):
         ("mask", ctypes.c_void_p),
         ("psi", ctypes.c_void_p),
         ("nearfield", ctypes.c_double),
+        ("background", ctypes.c_void_p),
     ]
 
 

@@ -132,6 +132,7 @@ struct Layout {
     size_t cg_obj, cg_probe, ls_part, cg;  // ML conjugate-gradient state
     size_t mbits;                          // per-thread mask bits of the register column pass
     size_t nf_t;                           // near-field transfer factors t[k] (complex64, N)
+    size_t bg_acc;                         // background update sums (float, N x N)
     size_t end;
 };
 
@@ -305,6 +306,8 @@ size_t layout_problem(ProbHost& h) {
     if (use_reg_kernels(h.ks, p.K)) o = align_up(o + sizeof(uint32_t) * (size_t)(p.N / h.ks->reg_lines) * kThreads);
     h.lay.nf_t = o;
     if (p.nearfield > 0.0) o = align_up(o + sizeof(float2) * (size_t)p.N);
+    h.lay.bg_acc = o;
+    if (p.background) o = align_up(o + sizeof(float) * (size_t)p.N * p.N);
     h.lay.end = o;
     return o;
 }
@@ -449,6 +452,7 @@ ptx_status compute_layout(std::vector<ProbHost>& probs, size_t* spec_off, size_t
         h.lay.cg += o;
         h.lay.mbits += o;
         h.lay.nf_t += o;
+        h.lay.bg_acc += o;
         h.lay.end += o;
         o += sz;
         size_t s = (size_t)h.B * kDefaultLanes * h.p.K * h.p.N * h.p.N * sizeof(float2);
@@ -492,6 +496,8 @@ void fill_args(ptx_handle* h, ProbHost& ph) {
     a.err_flag = h->err_dev;
     a.mbits = (const uint32_t*)(h->scratch + ph.lay.mbits);
     a.nf_t = ph.p.nearfield > 0.0 ? (const float2*)(h->scratch + ph.lay.nf_t) : nullptr;
+    a.bg = ph.p.background;
+    a.bg_acc = nullptr;  // set only for the column passes of AP cycles that update the background
     ph.tiles.tile_ids = (const int*)(h->scratch + ph.lay.tile_ids);
     ph.tiles.tile_ptr = (const int*)(h->scratch + ph.lay.tile_ptr);
     ph.tiles.tile_frames = (const int*)(h->scratch + ph.lay.tile_frames);
@@ -608,6 +614,7 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
         const ProbArgs& a = ph.args;
         const KernelSet* ks = ph.ks;
         const int algo = algos[pi];
+        const bool upd_bg = (flags & PTX_UPDATE_BACKGROUND) && algo == ALGO_AP && ph.p.background;
         const int fwd_mode = (algo == ALGO_DM && !init) ? X_DM : X_PHI;
         const int bwd_mode = (algo == ALGO_DM) ? BWD_DM : BWD_AP;
         bool used[kMaxLanes] = {};
@@ -620,6 +627,7 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
             cudaStream_t ls = lanes == 1 ? s : h->lane_stream[lane];
             ProbArgs al = a;
             al.spec = a.spec + lane * slice;
+            if (upd_bg) al.bg_acc = (float*)(h->scratch + ph.lay.bg_acc);
             {
                 ProfScope ps(h, PTX_KERNEL_ROW_FWD, ls);
                 ks->row_fwd(al, j0, nb, fwd_mode, ls);
@@ -638,13 +646,13 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
                     ProfScope ps(h, PTX_KERNEL_COL, ls);
                     ks->col_nf(al, nb, -1, ls);
                 }
-            } else if (h->tc && ph.p.N == 256 && ph.p.K == 1) {
+            } else if (h->tc && ph.p.N == 256 && ph.p.K == 1 && !ph.p.background) {
                 ProfScope ps(h, PTX_KERNEL_COL, ls);
                 launch_col_tc(al, j0, nb, ls);
             } else {
                 ProfScope ps(h, PTX_KERNEL_COL, ls);
                 CUtensorMap tm_spec;
-                const int grid = (h->tma && ph.tma_io && ks->col_tma) ? ks->col_tma_grid() : 0;
+                const int grid = (h->tma && ph.tma_io && ks->col_tma && !ph.p.background) ? ks->col_tma_grid() : 0;
                 if (grid > 0 && encode_2d(&tm_spec, 8, al.spec, ph.p.N, (uint64_t)ph.B * ph.p.N,
                                           (uint32_t)ks->reg_lines, (uint32_t)ph.p.N))
                     ks->col_tma(&tm_spec, &ph.tm_io, &ph.tm_mask, al, j0, nb, grid, ls);
@@ -663,6 +671,9 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
                     cudaEventRecord(ev, h->lane_stream[l]);
                     cudaStreamWaitEvent(s, ev, 0);
                 }
+        if (upd_bg) k_bg_update<<<2 * 152, 256, 0, s>>>(ph.p.background, (float*)(h->scratch + ph.lay.bg_acc),
+                                                        (const uint8_t*)(h->scratch + ph.lay.mask), ph.p.N * ph.p.N,
+                                                        1.0f / (float)ph.p.J);
         if (!(flags & PTX_NO_NORMALISE))
             enqueue_stages(h, ph, (upd_p ? STAGE_PROBE : 0) | (upd_o ? STAGE_OBJ_GATHER | STAGE_OBJ_NORMALISE : 0), s);
         ProfScope ps(h, PTX_KERNEL_CYCLE_END, s);
@@ -731,11 +742,16 @@ ptx_status run_cycles(ptx_handle* h, const std::vector<int>& algos, int ncycles,
                       void* stream) {
     if (!h) return fail(PTX_ERR_INVALID_ARG, "null handle");
     if (ncycles < 0) return fail(PTX_ERR_INVALID_ARG, "ncycles=%d must be >= 0", ncycles);
-    const uint32_t known = PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_DM_INIT_PSI | PTX_NO_NORMALISE | PTX_NO_GRAPH;
+    const uint32_t known =
+        PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_DM_INIT_PSI | PTX_NO_NORMALISE | PTX_NO_GRAPH | PTX_UPDATE_BACKGROUND;
     if (flags & ~known) return fail(PTX_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags & ~known);
     if ((int)algos.size() != (int)h->probs.size()) return fail(PTX_ERR_INVALID_ARG, "one algorithm per problem");
     for (int a : algos)
         if (a != ALGO_AP && a != ALGO_DM) return fail(PTX_ERR_INVALID_ARG, "algorithm %d is neither AP nor DM", a);
+    if (flags & PTX_UPDATE_BACKGROUND)
+        for (size_t i = 0; i < algos.size(); ++i)
+            if (algos[i] != ALGO_AP && h->probs[i].p.background)
+                return fail(PTX_ERR_INVALID_ARG, "problem %zu: the background is updated in AP cycles only", i);
     for (size_t i = 0; i < h->probs.size(); ++i)
         if (!h->probs[i].p.psi)
             return fail(PTX_ERR_INVALID_ARG, "problem %zu: AP and DM cycles need the psi array", i);
@@ -749,7 +765,7 @@ ptx_status run_cycles(ptx_handle* h, const std::vector<int>& algos, int ncycles,
     cudaStream_t s = (cudaStream_t)stream;
     k_set_ctl<<<1, 1, 0, s>>>(h->ctl, llk_dev, (int)h->probs.size());
     const bool graph = !(flags & PTX_NO_GRAPH) && !h->profiling;
-    const uint32_t base = flags & (PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_NO_NORMALISE);
+    const uint32_t base = flags & (PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_NO_NORMALISE | PTX_UPDATE_BACKGROUND);
     for (int c = 0; c < ncycles; ++c) {
         uint32_t f = base;
         if (c == 0 && (flags & PTX_DM_INIT_PSI)) f |= PTX_DM_INIT_PSI;

@@ -192,6 +192,15 @@ __global__ void k_cycle_end(Ctl* ctl, ProbArgs a, int p, int nparts_per_frame, i
     }
 }
 
+// Background update of an AP cycle: B <- B * (1/J) sum_j I_o / (I_c + B) on
+// unmasked pixels, then the sums are cleared for the next cycle.
+__global__ void k_bg_update(float* bg, float* acc, const uint8_t* mask, int n, float inv_j) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!mask[i]) bg[i] *= acc[i] * inv_j;
+        acc[i] = 0.f;
+    }
+}
+
 __global__ void k_set_ctl(Ctl* ctl, double* llk_out, int nprob) {
     ctl->llk_out = llk_out;
     ctl->cycle = 0;

@@ -52,6 +52,8 @@ struct ProbArgs {
     int* err_flag;          // host-mapped flag, set when a bounded device wait gives up (or null)
     const uint32_t* mbits;  // [N / C][256] mask bits per thread of the register column pass
     const float2* nf_t;     // [N] near-field transfer factors t[k] (h[ky][kx] = t[ky] t[kx]) or null
+    const float* bg;        // [N][N] incoherent background added to the model intensity, or null
+    float* bg_acc;          // [N][N] sum over frames of I_o / (I_c + B) (background update), or null
 };
 
 constexpr int kCycleEndBlocks = 64;  // blocks of the cycle's LLK reduction
@@ -286,10 +288,11 @@ __global__ void __launch_bounds__(kThreads) k_col(ProbArgs a, int j0, int mode) 
         const int c = e % C, n = e / C;
         float icr = 0.f;
         for (int k = 0; k < K; ++k) icr += cnorm(buf[(k * C + c) * P + n]);
-        const float ic = icr * invN2;
+        const float ic = icr * invN2 + (a.bg ? a.bg[n * N + x0 + c] : 0.f);
         const float io = io_row[n * N + x0 + c];
         const bool masked = a.mask[n * N + x0 + c] != 0;
         if (!masked) llk.add(llk_term(ic, io));
+        if (a.bg_acc && !masked) atomicAdd(a.bg_acc + n * N + x0 + c, fmaxf(io, 0.f) / fmaxf(ic, 1e-30f));
         if (mode != COL_LLK) {
             float f;
             if (masked) {
@@ -497,7 +500,8 @@ __global__ void __launch_bounds__(kThreads) k_col_ls(ProbArgs a, int j0, int C) 
     for (int e = threadIdx.x; e < N * C; e += kThreads) {
         const int c = e % C, n = e / C;
         if (a.mask[n * N + x0 + c]) continue;
-        const float ic = acc[e] * invN2, di = acc[N * C + e] * invN2, d2i = acc[2 * N * C + e] * invN2;
+        const float ic = acc[e] * invN2 + (a.bg ? a.bg[n * N + x0 + c] : 0.f);
+        const float di = acc[N * C + e] * invN2, d2i = acc[2 * N * C + e] * invN2;
         const float io = fmaxf(io_row[n * N + x0 + c], 0.f);
         const float icf = fmaxf(ic, 1e-30f);
         const double w1 = 1.0 - (double)io / (double)icf;
@@ -543,6 +547,7 @@ void launch_obj_gather_tma(const void* tm_psi, const void* tm_probe, const ProbA
                            int ntiles, int fuse_max, cudaStream_t s);
 cudaError_t set_attrs_gather_tma();
 __global__ void k_den_max(ProbArgs a, int upd_obj, int upd_probe);
+__global__ void k_bg_update(float* bg, float* acc, const uint8_t* mask, int n, float inv_j);
 __global__ void k_normalise(ProbArgs a, float alpha_obj, float alpha_probe, int upd_obj, int upd_probe);
 __global__ void k_llk_reduce(ProbArgs a, int nparts_per_frame, double* out);
 __global__ void k_cycle_end(Ctl* ctl, ProbArgs a, int p, int nparts_per_frame, int last_problem);

@@ -168,9 +168,14 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_row_pro
             const uint8_t* mk_row = a.mask + (size_t)y * N + k2;
 #pragma unroll
             for (int k1 = 0; k1 < M; ++k1) {
-                const float ic = cnorm(u[i][k1]);
+                float ic = cnorm(u[i][k1]);
                 const float io = __ldcs(io_row + R * k1);
                 const bool masked = mk_row[R * k1] != 0;
+                if (a.bg) {  // incoherent background in the detector plane
+                    const int pix = y * N + k2 + R * k1;
+                    ic += __ldg(a.bg + pix);
+                    if (a.bg_acc && !masked) atomicAdd(a.bg_acc + pix, fmaxf(io, 0.f) / fmaxf(ic, 1e-30f));
+                }
                 if (!masked) llk.add(llk_term_fast(ic, io));
                 const float f = masked ? 0.f : amp_ratio(io, ic) - 1.0f;
                 u[i][k1] = cscale(u[i][k1], f);

@@ -204,9 +204,14 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(P
             Dft<M, -1>::run(u[i]);
 #pragma unroll
             for (int k1 = 0; k1 < M; ++k1) {
-                const float ic = cnorm(u[i][k1]) * invN2;
+                float ic = cnorm(u[i][k1]) * invN2;
                 const float io = io_r[i][k1];
                 const bool masked = (mbits >> (i * M + k1)) & 1u;
+                if (a.bg) {  // incoherent background: one more component of the model intensity
+                    const int pix = (k2 + R * k1) * N + x0 + c;
+                    ic += __ldg(a.bg + pix);
+                    if (a.bg_acc && !masked) atomicAdd(a.bg_acc + pix, fmaxf(io, 0.f) / fmaxf(ic, 1e-30f));
+                }
                 if (!masked) llk.add(llk_term_fast(ic, io));
                 float f;
                 if (masked) {

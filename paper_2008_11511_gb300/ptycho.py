@@ -14,7 +14,8 @@ import torch
 
 from . import _lib
 from ._lib import (PTX_DM_INIT_PSI, PTX_NO_GRAPH, PTX_NO_NORMALISE, PTX_STAGE_OBJ_GATHER, PTX_STAGE_OBJ_NORMALISE,
-                   PTX_STAGE_PROBE, PTX_UPDATE_OBJ, PTX_UPDATE_PROBE, SUPPORTED_SIZES, Problem, PtychoError)
+                   PTX_STAGE_PROBE, PTX_UPDATE_BACKGROUND, PTX_UPDATE_OBJ, PTX_UPDATE_PROBE, SUPPORTED_SIZES, Problem,
+                   PtychoError)
 
 
 def _stream_ptr(device) -> ctypes.c_void_p:
@@ -44,10 +45,14 @@ class Ptycho:
                is given (LLK and gradient alone do not need it)
     nearfield: 0 for the far field; c = lambda z / pixel^2 > 0 for the near field
                (PropagateNearField; iobs and mask then in detector pixels)
+    background: optional float32 (N, N) CUDA tensor, the incoherent background
+               added to every frame's model intensity (updated in place by
+               ``ap(..., update_background=True)``)
     """
 
     def __init__(self, obj: torch.Tensor, probe: torch.Tensor, iobs: torch.Tensor, positions, mask=None,
-                 psi: torch.Tensor | None = None, with_psi: bool = True, nearfield: float = 0.0):
+                 psi: torch.Tensor | None = None, with_psi: bool = True, nearfield: float = 0.0,
+                 background: torch.Tensor | None = None):
         _require_cuda(obj, "obj", torch.complex64)
         _require_cuda(probe, "probe", torch.complex64)
         _require_cuda(iobs, "iobs", torch.float32)
@@ -68,14 +73,20 @@ class Ptycho:
         m = None
         if mask is not None:
             m = np.ascontiguousarray(np.asarray(mask).astype(np.uint8).reshape(N, N))
+        if background is not None:
+            _require_cuda(background, "background", torch.float32)
+            if tuple(background.shape) != (N, N):
+                raise ValueError("background must be (N, N)")
         self.obj, self.probe, self.iobs, self.psi = obj, probe, iobs, psi
         self.N, self.K, self.J = N, K, J
         self.Ho, self.Wo = obj.shape
         self._prob = Problem(N=N, K=K, J=J, Ho=self.Ho, Wo=self.Wo, obj=obj.data_ptr(), probe=probe.data_ptr(),
                              positions=pos.ctypes.data, iobs=iobs.data_ptr(),
                              mask=(m.ctypes.data if m is not None else None),
-                             psi=(psi.data_ptr() if psi is not None else None), nearfield=float(nearfield))
+                             psi=(psi.data_ptr() if psi is not None else None), nearfield=float(nearfield),
+                             background=(background.data_ptr() if background is not None else None))
         self.nearfield = float(nearfield)
+        self.background = background
         nbytes = ctypes.c_size_t(0)
         _lib.call("ptx_workspace_bytes", ctypes.byref(self._prob), 1, ctypes.byref(nbytes))
         with torch.cuda.device(self.device):
@@ -122,15 +133,20 @@ class Ptycho:
         return f
 
     def ap(self, ncycles: int, update_obj: bool = True, update_probe: bool = True, graph: bool = True,
-           normalise: bool = True, llk: torch.Tensor | None = None) -> torch.Tensor:
+           normalise: bool = True, llk: torch.Tensor | None = None, update_background: bool = False) -> torch.Tensor:
         """``ncycles`` alternating-projection cycles; returns the per-cycle LLK
-        (float64 CUDA tensor of length ncycles)."""
+        (float64 CUDA tensor of length ncycles).  ``update_background`` also
+        optimises the incoherent background given at construction."""
         if self.psi is None:
             raise ValueError("AP needs the exit-wave stack: create Ptycho with with_psi=True")
+        f = self._flags(update_obj, update_probe, graph, normalise)
+        if update_background:
+            if self.background is None:
+                raise ValueError("update_background needs a background: create Ptycho with background=...")
+            f |= PTX_UPDATE_BACKGROUND
         out = llk if llk is not None else torch.empty(max(ncycles, 1), dtype=torch.float64, device=self.device)
         with torch.cuda.device(self.device):
-            _lib.call("ptx_ap_cycles", self._handle(), int(ncycles),
-                      self._flags(update_obj, update_probe, graph, normalise),
+            _lib.call("ptx_ap_cycles", self._handle(), int(ncycles), f,
                       ctypes.c_void_p(out.data_ptr()), _stream_ptr(self.device))
         return out[:ncycles]
 
