@@ -47,6 +47,13 @@ Readings of points the paper leaves open (each is listed in the design doc):
   the projection scales it like a mode, and ``ap_cycle_background`` replaces B
   by the mean over frames of the scaled backgrounds.  B = 0 stays 0 (the update
   is multiplicative), so a reconstruction starts it at a positive guess.
+* Position refinement (Psi2PosShift; the paper cites Odstrcil et al. 2018 and
+  adds a filter against weak object gradients, without formulas): per frame
+  the first-order least-squares shift between Phi_j and the projected Psi_j,
+  object gradient by central differences; frames whose gradient norm is below
+  a fraction of the mean over frames keep their position.  Positions stay
+  integer in the cycle; the caller accumulates the shifts and moves a frame
+  when its accumulated shift rounds to a new pixel.
 * Near field (PropagateNearField; the paper names the operator and the near /
   far field flag but gives no formula): paraxial Fresnel propagation in
   Fourier space, IFT(FT(x) exp(-i pi lambda z q^2)), q = k / (N pixel) the
@@ -329,6 +336,57 @@ def ap_cycle_background(obj, probe, background, data: Data, alpha_obj=1e-2, alph
     return obj, probe, new_bg, llk
 
 
+def object_gradient(obj):
+    """(dO/dy, dO/dx) of the object by central differences, one-sided on the
+    object's first and last row / column."""
+    gy = np.empty_like(obj)
+    gx = np.empty_like(obj)
+    gy[1:-1] = 0.5 * (obj[2:] - obj[:-2])
+    gy[0] = obj[1] - obj[0]
+    gy[-1] = obj[-1] - obj[-2]
+    gx[:, 1:-1] = 0.5 * (obj[:, 2:] - obj[:, :-2])
+    gx[:, 0] = obj[:, 1] - obj[:, 0]
+    gx[:, -1] = obj[:, -1] - obj[:, -2]
+    return gy, gx
+
+
+def position_shifts(obj, probe, psi, positions, filter_ratio=0.1):
+    """Position refinement (Psi2PosShift; paper Section 4, after Odstrcil et al.
+    2018): for frame j the shift d = (d_y, d_x) that moves the model exit wave
+    Phi_j = P O[r_j] towards the projected wave Psi_j in the least-squares
+    sense, to first order in the shift: with chi = Psi_j - Phi_j and
+    G_a = P dO/da (a = y, x) on the patch, summed over modes and pixels,
+        [<G_y,G_y> <G_y,G_x>] [d_y]   [<G_y,chi>]
+        [<G_x,G_y> <G_x,G_x>] [d_x] = [<G_x,chi>],   <u,v> = sum Re(conj(u) v).
+    The paper adds a filter against shifting where the object gradient is
+    weak: a frame whose gradient norm <G_y,G_y> + <G_x,G_x> is below
+    ``filter_ratio`` times the mean over frames keeps its position (shift 0),
+    as does a frame whose 2 x 2 system is singular.
+    Returns float64 (J, 2) shifts (row, col) in pixels."""
+    obj = np.asarray(obj, dtype=np.complex128)
+    probe = np.asarray(probe, dtype=np.complex128)
+    K, N, _ = probe.shape
+    gy, gx = object_gradient(obj)
+    J = len(positions)
+    out = np.zeros((J, 2))
+    norm = np.zeros(J)
+    systems = []
+    dot = lambda u, v: float((np.conj(u) * v).real.sum())
+    for j, (r, c) in enumerate(positions):
+        sl = (slice(r, r + N), slice(c, c + N))
+        chi = psi[j] - probe * obj[sl][None]
+        g_y = probe * gy[sl][None]
+        g_x = probe * gx[sl][None]
+        a = np.array([[dot(g_y, g_y), dot(g_y, g_x)], [dot(g_x, g_y), dot(g_x, g_x)]])
+        systems.append((a, np.array([dot(g_y, chi), dot(g_x, chi)])))
+        norm[j] = a[0, 0] + a[1, 1]
+    for j, (a, b) in enumerate(systems):
+        det = a[0, 0] * a[1, 1] - a[0, 1] * a[1, 0]
+        if norm[j] >= filter_ratio * norm.mean() and det > 1e-12 * norm[j] ** 2:
+            out[j] = np.linalg.solve(a, b)
+    return out
+
+
 def dm_cycle(obj, probe, psi, data: Data, alpha_obj=1e-2, alpha_probe=1e-2,
              update_obj=True, update_probe=True, init_psi=False):
     """One Difference Map cycle (beta = 1; Elser 2007, Thibault et al. 2008):
@@ -539,7 +597,7 @@ __all__ = [
     "llk_poisson", "psi_to_probe_sums", "psi_to_obj_sums", "psi_to_obj_probe_sums", "inertia_update",
     "normalise", "overlap_update", "ap_cycle", "dm_cycle", "llk", "ml_grad",
     "cycles", "dm_frame_update", "frames_llk", "object_denominator", "frames_covering", "ml_line_coeffs", "ml_cg",
-    "ap_cycle_background", "near_field_transfer", "propagate_near_field",
+    "ap_cycle_background", "near_field_transfer", "propagate_near_field", "object_gradient", "position_shifts",
     "ICALC_FLOOR", "AMP_FLOOR", "STACK",
 ]
 

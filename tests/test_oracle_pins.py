@@ -721,3 +721,65 @@ def test_background_gradient_finite_differences():
     ho = 1e-6 * np.sqrt(np.mean(np.abs(obj) ** 2))
     fd = richardson_fd(lambda t: orc.llk(obj + t * do, probe, data), ho)
     assert abs(fd - float(np.real(np.vdot(go, do)))) < 1e-7 * max(abs(fd), 1.0)
+
+
+# ---------------------------------------------------------------- position refinement
+
+def _fourier_shift(x, dy, dx):
+    """x(r + (dy, dx)) for a periodic band-limited x, by a phase ramp (numpy FFT)."""
+    H, W = x.shape
+    ky = np.fft.fftfreq(H)[:, None]
+    kx = np.fft.fftfreq(W)[None, :]
+    return np.fft.ifft2(np.fft.fft2(x) * np.exp(2j * np.pi * (ky * dy + kx * dx)))
+
+
+def _smooth_object(seed, H=96, W=96, sigma=4.0):
+    rng = np.random.default_rng(seed)
+    from scipy.ndimage import gaussian_filter
+    a = gaussian_filter(rng.standard_normal((H, W)), sigma, mode="wrap")
+    p = gaussian_filter(rng.standard_normal((H, W)), sigma, mode="wrap")
+    return (1.0 + 0.3 * a / np.abs(a).max()) * np.exp(1j * 1.5 * p / np.abs(p).max())
+
+
+def test_position_shift_recovers_a_known_subpixel_shift():
+    """Psi_j built from the object shifted by a known sub-pixel amount (exact
+    Fourier shift, computed here with numpy): the estimated shift matches it to
+    first order, scales linearly with it, and is zero for Psi = Phi."""
+    obj = _smooth_object(80)
+    N = 24
+    yy, xx = np.mgrid[0:N, 0:N] - N / 2
+    probe = np.exp(-(yy ** 2 + xx ** 2) / (2 * 6.0 ** 2))[None].astype(np.complex128)
+    pos = np.array([[20, 30], [40, 12], [55, 50], [10, 60]])
+    deltas = np.array([[0.12, -0.08], [-0.1, 0.05], [0.06, 0.11], [-0.05, -0.12]])
+    psi = np.stack([probe * _fourier_shift(obj, dy, dx)[r:r + N, c:c + N][None]
+                    for (r, c), (dy, dx) in zip(pos, deltas)])
+    d = orc.position_shifts(obj, probe, psi, pos, filter_ratio=0.0)
+    assert np.abs(d - deltas).max() < 0.1 * np.abs(deltas).max(), (d, deltas)
+    d2 = orc.position_shifts(obj, probe, np.stack([probe * _fourier_shift(obj, 2 * dy, 2 * dx)[r:r + N, c:c + N][None]
+                                                   for (r, c), (dy, dx) in zip(pos, deltas)]), pos, filter_ratio=0.0)
+    assert np.abs(d2 - 2 * d).max() < 0.1 * np.abs(d).max()
+    phi = orc.obj_probe_to_psi(obj, probe, pos)
+    assert np.abs(orc.position_shifts(obj, probe, phi, pos)).max() == 0.0
+
+
+def test_position_shift_filter_keeps_flat_regions_in_place():
+    """A frame over a flat part of the object (no gradient) is not shifted and
+    gives no NaN; frames over structure still are."""
+    obj = _smooth_object(81)
+    obj[:, :40] = 1.0  # flat left part
+    N = 24
+    probe = np.ones((1, N, N), dtype=np.complex128)
+    pos = np.array([[10, 5], [10, 60], [50, 65]])
+    psi = np.stack([probe * _fourier_shift(obj, 0.1, 0.1)[r:r + N, c:c + N][None] for r, c in pos])
+    d = orc.position_shifts(obj, probe, psi, pos, filter_ratio=0.1)
+    assert np.all(np.isfinite(d)) and np.all(d[0] == 0.0)
+    assert np.all(np.abs(d[1:]) > 0.02)
+
+
+def test_object_gradient_central_differences():
+    y = np.arange(10)[:, None] * np.ones((1, 8))
+    x = np.ones((10, 1)) * np.arange(8)[None, :]
+    o = (2.0 * y + 3j * x ** 2).astype(np.complex128)
+    gy, gx = orc.object_gradient(o)
+    assert np.allclose(gy, 2.0)
+    assert np.allclose(gx[:, 1:-1], 3j * 2 * x[:, 1:-1]) and np.allclose(gx[:, 0], 3j) and np.allclose(gx[:, -1], 3j * 13)
