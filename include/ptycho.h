@@ -239,6 +239,26 @@ ptx_status ptx_fft2(void* data, int32_t nframes, int32_t N, int32_t direction, v
 #define PTX_KERNEL_OBJ_GATHER 6 /* object numerator / denominator gathered per tile from Psi' */
 #define PTX_KERNEL_KINDS     7
 
+/* Position refinement (Psi2PosShift, paper Section 4, after Odstrcil et al.
+ * 2018).  For every frame of problem p, the first-order least-squares shift
+ * (row, col) in pixels that moves P . O[r_j] towards the projected exit wave
+ * left in psi by the last AP cycle: with chi = Psi_j - P O[r_j] and
+ * G_a = P dO/da (a = row, col; central differences of the object, one-sided on
+ * its edges) it solves [<G_y,G_y> <G_y,G_x>; <G_x,G_y> <G_x,G_x>] d =
+ * [<G_y,chi>; <G_x,chi>], <u,v> = sum over modes and pixels of Re(conj(u) v),
+ * in FP64.  A frame whose gradient norm <G_y,G_y> + <G_x,G_x> is below
+ * filter_ratio times the mean over frames (the paper's filter against weak
+ * object gradients), or whose system is singular, gets (0, 0).
+ * shifts: device float32 [J][2].  The positions themselves stay integer: the
+ * caller accumulates the shifts and moves frames with ptx_set_positions. */
+ptx_status ptx_position_shifts(ptx_handle* h, int32_t p, float filter_ratio, float* shifts, void* stream);
+
+/* Replace the scan positions of problem p (host int32 [J][2], copied; the
+ * same bounds as at create, PTX_ERR_OUT_OF_BOUNDS otherwise).  Rebuilds the
+ * object tile lists in place and drops the captured cycle graphs; waits for
+ * its copies (a host synchronisation). */
+ptx_status ptx_set_positions(ptx_handle* h, int32_t p, const int32_t* positions, void* stream);
+
 /* Per-kernel timing for measurement.  While enabled, the cycle calls launch
  * their kernels directly (no CUDA graph) and bracket every launch with CUDA
  * events recorded on the launch stream.  Enabling resets the counters. */

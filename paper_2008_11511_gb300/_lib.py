@@ -38,7 +38,7 @@ SUPPORTED_SIZES = (8, 12, 16, 32, 64, 80, 128, 160, 192, 224, 256, 384, 400, 448
 # Every symbol include/ptycho.h declares.
 EXPORTS = (
     "ptx_workspace_bytes", "ptx_create", "ptx_ap_cycles", "ptx_dm_cycles", "ptx_cycles", "ptx_llk", "ptx_ml_grad",
-    "ptx_ml_cycles", "ptx_ml_line_coeffs",
+    "ptx_ml_cycles", "ptx_ml_line_coeffs", "ptx_position_shifts", "ptx_set_positions",
     "ptx_normalise", "ptx_accumulators", "ptx_set_param", "ptx_fft2", "ptx_profile_enable", "ptx_profile_read",
     "ptx_llk_static", "ptx_last_error", "ptx_destroy",
 )

@@ -133,6 +133,7 @@ struct Layout {
     size_t mbits;                          // per-thread mask bits of the register column pass
     size_t nf_t;                           // near-field transfer factors t[k] (complex64, N)
     size_t bg_acc;                         // background update sums (float, N x N)
+    size_t pos_part;                       // position-shift partial sums (double, J x bands x 5)
     size_t end;
 };
 
@@ -287,12 +288,18 @@ size_t layout_problem(ProbHost& h) {
     o = align_up(o + sizeof(double) * (size_t)p.J * (p.N / h.C2));
     h.lay.maxbits = o;
     o = align_up(o + 2 * sizeof(unsigned));
+    // tile lists sized for any positions (ptx_set_positions rewrites them in place):
+    // every object tile, and per frame the tiles an N x N patch can meet
+    const size_t ntiles_max = (size_t)((p.Wo + kObjTileW - 1) / kObjTileW) * ((p.Ho + kObjTileH - 1) / kObjTileH);
+    const size_t per_frame = (size_t)((p.N + kObjTileH - 1) / kObjTileH + 1) * ((p.N + kObjTileW - 1) / kObjTileW + 1);
     h.lay.tile_ids = o;
-    o = align_up(o + sizeof(int) * h.tile_ids.size());
+    o = align_up(o + sizeof(int) * std::max(h.tile_ids.size(), ntiles_max));
     h.lay.tile_ptr = o;
-    o = align_up(o + sizeof(int) * h.tile_ptr.size());
+    o = align_up(o + sizeof(int) * std::max(h.tile_ptr.size(), ntiles_max + 1));
     h.lay.tile_frames = o;
-    o = align_up(o + sizeof(int) * h.tile_frames.size());
+    o = align_up(o + sizeof(int) * std::max(h.tile_frames.size(), (size_t)p.J * per_frame));
+    h.lay.pos_part = o;
+    o = align_up(o + 5 * sizeof(double) * (size_t)p.J * ((p.N + 7) / 8));
     // CG: gradient, previous gradient and direction of object and probe
     h.lay.cg_obj = o;
     o = align_up(o + 3 * sizeof(float2) * (size_t)p.Ho * p.Wo);
@@ -453,6 +460,7 @@ ptx_status compute_layout(std::vector<ProbHost>& probs, size_t* spec_off, size_t
         h.lay.mbits += o;
         h.lay.nf_t += o;
         h.lay.bg_acc += o;
+        h.lay.pos_part += o;
         h.lay.end += o;
         o += sz;
         size_t s = (size_t)h.B * kDefaultLanes * h.p.K * h.p.N * h.p.N * sizeof(float2);
@@ -1195,6 +1203,53 @@ ptx_status ptx_profile_read(ptx_handle* h, int32_t nkinds, int64_t* launches, do
             total_ms[u.first] += ms;
         }
     }
+    return PTX_OK;
+}
+
+ptx_status ptx_position_shifts(ptx_handle* h, int32_t p, float filter_ratio, float* shifts, void* stream) {
+    if (!h || !shifts) return fail(PTX_ERR_INVALID_ARG, "null handle or shifts");
+    if (p < 0 || p >= (int)h->probs.size()) return fail(PTX_ERR_INVALID_ARG, "problem %d out of range", p);
+    if (!(filter_ratio >= 0.f)) return fail(PTX_ERR_INVALID_ARG, "filter_ratio must be >= 0");
+    ProbHost& ph = h->probs[p];
+    if (!ph.p.psi) return fail(PTX_ERR_INVALID_ARG, "position shifts need the psi array of the last cycle");
+    ptx_status st = check_device(h);
+    if (st != PTX_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int bands = (ph.p.N + 7) / 8;
+    double* part = (double*)(h->scratch + ph.lay.pos_part);
+    k_pos_sums<<<dim3(bands, ph.p.J), 256, 0, s>>>(ph.args, part);
+    k_pos_solve<<<1, 1024, 0, s>>>(part, ph.p.J, bands, filter_ratio, shifts);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ptx_position_shifts launch");
+    return PTX_OK;
+}
+
+ptx_status ptx_set_positions(ptx_handle* h, int32_t p, const int32_t* positions, void* stream) {
+    if (!h || !positions) return fail(PTX_ERR_INVALID_ARG, "null handle or positions");
+    if (p < 0 || p >= (int)h->probs.size()) return fail(PTX_ERR_INVALID_ARG, "problem %d out of range", p);
+    ProbHost& ph = h->probs[p];
+    for (int j = 0; j < ph.p.J; ++j) {
+        const int r = positions[2 * j], c = positions[2 * j + 1];
+        if (r < 0 || c < 0 || r > ph.p.Ho - ph.p.N || c > ph.p.Wo - ph.p.N)
+            return fail(PTX_ERR_OUT_OF_BOUNDS, "position %d = (%d, %d) puts the %dx%d patch outside the %dx%d object", j,
+                        r, c, ph.p.N, ph.p.N, ph.p.Ho, ph.p.Wo);
+    }
+    ptx_status st = check_device(h);
+    if (st != PTX_OK) return st;
+    build_tiles(ph, positions);
+    fill_args(h, ph);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(h->scratch + ph.lay.pos, positions, sizeof(int32_t) * 2 * (size_t)ph.p.J,
+                                    cudaMemcpyHostToDevice, s);
+    const std::vector<int>* lists[3] = {&ph.tile_ids, &ph.tile_ptr, &ph.tile_frames};
+    const size_t offs[3] = {ph.lay.tile_ids, ph.lay.tile_ptr, ph.lay.tile_frames};
+    for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+        if (!lists[q]->empty())
+            e = cudaMemcpyAsync(h->scratch + offs[q], lists[q]->data(), sizeof(int) * lists[q]->size(),
+                                cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host arrays are not kept
+    if (e != cudaSuccess) return cuda_fail(e, "ptx_set_positions copy");
+    drop_graphs(h);  // captured cycles hold the old tile count
     return PTX_OK;
 }
 

@@ -548,6 +548,9 @@ void launch_obj_gather_tma(const void* tm_psi, const void* tm_probe, const ProbA
 cudaError_t set_attrs_gather_tma();
 __global__ void k_den_max(ProbArgs a, int upd_obj, int upd_probe);
 __global__ void k_bg_update(float* bg, float* acc, const uint8_t* mask, int n, float inv_j);
+// position refinement (position.cu)
+__global__ void k_pos_sums(ProbArgs a, double* part);
+__global__ void k_pos_solve(const double* part, int J, int bands, float filter_ratio, float* shifts);
 __global__ void k_normalise(ProbArgs a, float alpha_obj, float alpha_probe, int upd_obj, int upd_probe);
 __global__ void k_llk_reduce(ProbArgs a, int nparts_per_frame, double* out);
 __global__ void k_cycle_end(Ctl* ctl, ProbArgs a, int p, int nparts_per_frame, int last_problem);
@@ -672,7 +675,10 @@ void launch_col(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s) {
     if constexpr (has_reg<N>()) {
         if (a.K == 1) {
             dim3 grid(N / RegShape<N>::L, nb);
-            k_col_r<N><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, mode);
+            if (a.bg)
+                k_col_r<N, true><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, mode);
+            else
+                k_col_r<N, false><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, mode);
             return;
         }
     }

@@ -119,7 +119,9 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_r(
 // Column pass: column FFT, projection + LLK, inverse column FFT.
 // grid (N / L, frames in batch); block handles columns [x0, x0 + L).
 // ---------------------------------------------------------------------------
-template <int N>
+// kBg: the problem has an incoherent background (separate instantiation, so
+// that the common path carries none of its loads and sums).
+template <int N, bool kBg>
 __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(ProbArgs a, int j0, int mode) {
     using S = RegShape<N>;
     constexpr int R = S::R, M = S::M, C = S::L, P = S::P;
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(P
                 float ic = cnorm(u[i][k1]) * invN2;
                 const float io = io_r[i][k1];
                 const bool masked = (mbits >> (i * M + k1)) & 1u;
-                if (a.bg) {  // incoherent background: one more component of the model intensity
+                if constexpr (kBg) {  // incoherent background: one more component of the model intensity
                     const int pix = (k2 + R * k1) * N + x0 + c;
                     ic += __ldg(a.bg + pix);
                     if (a.bg_acc && !masked) atomicAdd(a.bg_acc + pix, fmaxf(io, 0.f) / fmaxf(ic, 1e-30f));
@@ -478,10 +480,12 @@ cudaError_t set_attrs_r() {
     const int mx = 200 * 1024;
     const int carve = cudaSharedmemCarveoutMaxShared;  // room for 5-6 blocks of ~37 KB per SM
     if ((e = cudaFuncSetAttribute(k_row_fwd_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-    if ((e = cudaFuncSetAttribute(k_col_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_r<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_r<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_row_bwd_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_row_fwd_r<N>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
-    if ((e = cudaFuncSetAttribute(k_col_r<N>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_r<N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_r<N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_row_bwd_r<N>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     return cudaSuccess;
 }

@@ -164,6 +164,39 @@ class Ptycho:
                       _stream_ptr(self.device))
         return out[:ncycles]
 
+    def position_shifts(self, filter_ratio: float = 0.1) -> torch.Tensor:
+        """Per-frame least-squares position shifts (row, col) in pixels from the
+        exit waves of the last AP cycle (float32 CUDA tensor (J, 2))."""
+        out = torch.empty((self.J, 2), dtype=torch.float32, device=self.device)
+        with torch.cuda.device(self.device):
+            _lib.call("ptx_position_shifts", self._handle(), 0, ctypes.c_float(filter_ratio),
+                      ctypes.c_void_p(out.data_ptr()), _stream_ptr(self.device))
+        return out
+
+    def set_positions(self, positions):
+        """Replace the integer scan positions (J, 2) (rebuilds the object tiles)."""
+        pos = np.ascontiguousarray(np.asarray(positions, dtype=np.int32).reshape(self.J, 2))
+        with torch.cuda.device(self.device):
+            _lib.call("ptx_set_positions", self._handle(), 0, ctypes.c_void_p(pos.ctypes.data),
+                      _stream_ptr(self.device))
+        self.positions = pos
+
+    def refine_positions(self, filter_ratio: float = 0.1, step: float = 1.0, max_shift: float = 2.0):
+        """One position-refinement step after an AP cycle: the per-frame shifts
+        (scaled by ``step``, clipped to ``max_shift`` px) accumulate into
+        sub-pixel positions, and frames whose rounded position changes move.
+        Returns the sub-pixel positions (float64 (J, 2))."""
+        if getattr(self, "_pos_f", None) is None:
+            self._pos_f = self.positions.astype(np.float64)
+        d = self.position_shifts(filter_ratio).cpu().numpy().astype(np.float64)
+        self._pos_f += np.clip(step * d, -max_shift, max_shift)
+        hi = np.array([self.Ho - self.N, self.Wo - self.N], dtype=np.float64)
+        self._pos_f = np.clip(self._pos_f, 0.0, hi)
+        new = np.rint(self._pos_f).astype(np.int32)
+        if np.any(new != self.positions):
+            self.set_positions(new)
+        return self._pos_f.copy()
+
     def llk(self) -> torch.Tensor:
         """Exact Poisson LLK of the current object and probe (float64 CUDA scalar tensor)."""
         out = torch.empty(1, dtype=torch.float64, device=self.device)
