@@ -235,16 +235,19 @@ def run_ours(args):
     probe = torch.tensor(s.probe0, device=dev)
     iobs = torch.tensor(s.iobs, device=dev)
     pb = Ptycho(obj, probe, iobs, s.positions, s.mask, with_psi=True)
+    params = []
     if args.lanes:
-        pb.set_param("lanes", args.lanes)
+        params.append(("lanes", args.lanes))
     if args.batch_frames:
-        pb.set_param("batch_frames", args.batch_frames)
+        params.append(("batch_frames", args.batch_frames))
     if args.tma is not None:
-        pb.set_param("tma", args.tma)
+        params.append(("tma", args.tma))
     if args.tma_gather is not None:
-        pb.set_param("tma_gather", args.tma_gather)
+        params.append(("tma_gather", args.tma_gather))
     if args.tc:
-        pb.set_param("tc", 1)
+        params.append(("tc", 1))
+    for name, val in params:
+        pb.set_param(name, val)
     stream = torch.cuda.current_stream(dev)
     llk_buf = torch.empty(max(args.steps, args.warmup, 1), dtype=torch.float64, device=dev)
 
@@ -296,23 +299,51 @@ def run_ours(args):
     for v in kstats.values():
         v["share"] = v["total_ms"] / tot_ms
 
-    # end to end through the public API with host buffers: every step copies the
-    # intensity stack in from pinned host memory and reads the cycle's LLK back
+    # end to end through the public API with host buffers: every step copies its
+    # intensity stack in from pinned host memory and reads the cycle's LLK back.
+    # The copies run on a second stream one step ahead, into the other of two
+    # device buffers; each buffer has its own handle, and both handles share the
+    # object, the probe and the exit-wave stack.
     host_iobs = torch.from_numpy(s.iobs).pin_memory()
     host_llk = torch.empty(1, dtype=torch.float64).pin_memory()
+    iobs2 = torch.empty_like(iobs)
+    pb2 = Ptycho(obj, probe, iobs2, s.positions, s.mask, psi=pb.psi)
+    for name, val in params:
+        pb2.set_param(name, val)
+    iobs2.copy_(iobs)
+    pb2.dm(1, llk=llk_buf)  # graph capture outside the timed region
+    handles, bufs = (pb, pb2), (iobs, iobs2)
+    copy_stream = torch.cuda.Stream(dev)
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    used = [torch.cuda.Event(), torch.cuda.Event()]
     e_steps = max(1, min(args.steps, 10))
     barrier(ws)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for _ in range(e_steps):
-        iobs.copy_(host_iobs, non_blocking=True)
-        l = pb.dm(1, llk=llk_buf)
+    with torch.cuda.stream(copy_stream):
+        bufs[0].copy_(host_iobs, non_blocking=True)
+        copied[0].record(copy_stream)
+    for k in range(e_steps):
+        b = k % 2
+        if k + 1 < e_steps:
+            nb = 1 - b
+            with torch.cuda.stream(copy_stream):
+                if k >= 1:
+                    copy_stream.wait_event(used[nb])
+                bufs[nb].copy_(host_iobs, non_blocking=True)
+                copied[nb].record(copy_stream)
+        stream.wait_event(copied[b])
+        l = handles[b].dm(1, llk=llk_buf)
+        used[b].record(stream)
         host_llk.copy_(l[:1], non_blocking=True)
-        stream.synchronize()
+    stream.synchronize()
+    copy_stream.synchronize()
     el = time.perf_counter() - t0
     barrier(ws)
     el = max_over_ranks(el, ws)
     e2e_value = s.J * e_steps * ws / el
+    pb2.close()
+    del iobs2
 
     # roofline: the dominant kernel by time share
     pk = peaks()
@@ -363,7 +394,8 @@ def run_ours(args):
                 "roofline": roof, "roofline_cycle": roof_cycle, "kernels": kstats,
                 "clocks": clk, "gpu_launches": gpu_launches,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(s.iobs.nbytes),
-                        "d2h_bytes_per_step": 8, "steps": e_steps},
+                        "d2h_bytes_per_step": 8, "steps": e_steps,
+                        "copies": "pinned host -> device on a second stream, one step ahead, two buffers"},
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     pb.close()
