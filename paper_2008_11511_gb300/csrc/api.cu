@@ -306,7 +306,7 @@ size_t layout_problem(ProbHost& h) {
     h.lay.cg_probe = o;
     o = align_up(o + 3 * sizeof(float2) * (size_t)p.K * p.N * p.N);
     h.lay.ls_part = o;
-    o = align_up(o + 2 * sizeof(double) * (size_t)p.J * (p.N / h.ks->ls_lines));
+    o = align_up(o + 2 * sizeof(double) * (size_t)p.J * (p.N / std::min(h.ks->ls_lines, h.ks->reg_lines > 0 ? h.ks->reg_lines : h.ks->ls_lines)));
     h.lay.cg = o;
     o = align_up(o + 8 * sizeof(double));
     h.lay.mbits = o;
@@ -1016,7 +1016,9 @@ ptx_status enqueue_line_coeffs(ptx_handle* h, ProbHost& ph, const float2* d_obj,
         ph.ks->row_fwd_ls(a, j0, nb, 0, s);
         ph.ks->col_ls(a, j0, nb, 0, s);
     }
-    k_ls_reduce<<<1, 1024, 0, s>>>(a.ls_part, (size_t)ph.p.J * (ph.p.N / ph.ks->ls_lines), out);
+    // partial pairs per frame: one per column block of the line-search column pass
+    const int ls_cols = use_reg_kernels(ph.ks, ph.p.K) ? ph.ks->reg_lines : ph.ks->ls_lines;
+    k_ls_reduce<<<1, 1024, 0, s>>>(a.ls_part, (size_t)ph.p.J * (ph.p.N / ls_cols), out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "line-search launch");
     return PTX_OK;

@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(kThreads) k_col_ls(ProbArgs a, int j0, int C) 
         __syncthreads();
     }
     constexpr float invN2 = 1.0f / float(N * N);
-    double l1 = 0.0, l2 = 0.0;
+    KahanF l1, l2;  // single-precision terms, compensated sums (as k_col_ls_r)
     const float* io_row = a.iobs + (size_t)j * N * N;
     for (int e = threadIdx.x; e < N * C; e += kThreads) {
         const int c = e % C, n = e / C;
@@ -504,14 +504,14 @@ __global__ void __launch_bounds__(kThreads) k_col_ls(ProbArgs a, int j0, int C) 
         const float di = acc[N * C + e] * invN2, d2i = acc[2 * N * C + e] * invN2;
         const float io = fmaxf(io_row[n * N + x0 + c], 0.f);
         const float icf = fmaxf(ic, 1e-30f);
-        const double w1 = 1.0 - (double)io / (double)icf;
-        const double w2 = (double)io / ((double)icf * (double)icf);
-        l1 += w1 * (double)di;
-        l2 += w1 * (double)d2i + w2 * (double)di * (double)di;
+        const float w1 = 1.f - io / icf;
+        const float q = di / icf;
+        l1.add(w1 * di);
+        l2.add(fmaf(w1, d2i, io * q * q));
     }
-    const double t1 = block_sum_double<kThreads>(l1, red_s);
+    const double t1 = block_sum_double<kThreads>(l1.value(), red_s);
     __syncthreads();
-    const double t2 = block_sum_double<kThreads>(l2, red_s);
+    const double t2 = block_sum_double<kThreads>(l2.value(), red_s);
     if (threadIdx.x == 0) {
         double* out = a.ls_part + 2 * ((size_t)j * gridDim.x + blockIdx.x);
         out[0] = t1;
@@ -706,12 +706,26 @@ constexpr int ls_lines() {
 }
 template <int N>
 void launch_row_fwd_ls(const ProbArgs& a, int j0, int nb, int, cudaStream_t s) {
+    if constexpr (has_reg<N>()) {
+        if (a.K == 1) {
+            dim3 grid(N / RegShape<N>::L, nb, (a.dir_obj && a.dir_probe) ? 3 : 2);
+            k_row_fwd_ls_r<N><<<grid, kThreads, smem_row_fwd_r<N>(), s>>>(a, j0);
+            return;
+        }
+    }
     constexpr int L = ls_lines<N>();
     dim3 grid(N / L, nb);
     k_row_fwd_ls<N><<<grid, kThreads, sizeof(float2) * (N + (size_t)3 * L * line_pitch<N>()), s>>>(a, j0, L);
 }
 template <int N>
 void launch_col_ls(const ProbArgs& a, int j0, int nb, int, cudaStream_t s) {
+    if constexpr (has_reg<N>()) {
+        if (a.K == 1) {
+            dim3 grid(N / RegShape<N>::L, nb);
+            k_col_ls_r<N><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, (a.dir_obj && a.dir_probe) ? 3 : 2);
+            return;
+        }
+    }
     constexpr int C = ls_lines<N>();
     dim3 grid(N / C, nb);
     const size_t sm = sizeof(float2) * (N + (size_t)3 * C * line_pitch<N>()) + sizeof(float) * 3 * (size_t)N * C;

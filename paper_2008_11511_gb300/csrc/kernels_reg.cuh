@@ -459,6 +459,192 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
     }
 }
 
+// ---------------------------------------------------------------------------
+// ML line search, one probe mode (the same arithmetic as k_row_fwd_ls /
+// k_col_ls, with the register-resident transforms).  For a direction (dO, dP)
+// the far field along the line is A + a B + a^2 C with A = FT(P O),
+// B = FT(dP O + P dO), C = FT(dP dO); C vanishes unless both parts of the
+// direction are given.
+//
+// Row pass: grid (N / L, frames in batch, waves), blockIdx.z = wave (0: A,
+// 1: B, 2: C); row transforms into spec[b][wave].
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_ls_r(ProbArgs a, int j0) {
+    using S = RegShape<N>;
+    constexpr int R = S::R, M = S::M, L = S::L, P = S::P;
+    extern __shared__ __align__(16) float2 sm[];
+    float2* tw = sm;
+    float2* buf = sm + N;
+    load_twiddles<N>(tw);
+    const int y0 = blockIdx.x * L;
+    const int b = blockIdx.y;
+    const int wave = blockIdx.z;
+    const int2 p = a.pos[j0 + b];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < S::I1; ++i) {
+        const int w = threadIdx.x + i * kThreads;
+        if (w < L * M) {
+            const int line = w / M, n1 = w - line * M;
+            const int y = y0 + line;
+            const size_t pi = (size_t)y * N + n1;
+            const size_t oi = (size_t)(p.x + y) * a.Wo + p.y + n1;
+            float2 v[R];
+#pragma unroll
+            for (int n2 = 0; n2 < R; ++n2) {
+                const size_t pk = pi + M * n2, ok = oi + M * n2;
+                float2 x;
+                if (wave == 0) {
+                    x = cmul(__ldg(a.probe + pk), __ldg(a.obj + ok));
+                } else if (wave == 1) {
+                    x = make_float2(0.f, 0.f);
+                    if (a.dir_obj) x = cmul(__ldg(a.probe + pk), __ldg(a.dir_obj + ok));
+                    if (a.dir_probe) x = cadd(x, cmul(__ldg(a.dir_probe + pk), __ldg(a.obj + ok)));
+                } else {
+                    x = cmul(__ldg(a.dir_probe + pk), __ldg(a.dir_obj + ok));
+                }
+                v[n2] = x;
+            }
+            Dft<R, -1>::run(v);
+            float2* o = buf + line * P + n1;
+            o[0] = v[0];
+#pragma unroll
+            for (int k2 = 1; k2 < R; ++k2) o[k2 * (M + 1)] = cmul(v[k2], tw_get<N, -1>(tw, k2, n1));
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < S::I2; ++i) {
+        const int w = threadIdx.x + i * kThreads;
+        if (w < L * R) {
+            const int line = w / R, k2 = w - line * R;
+            float2 u[M];
+            const float2* src = buf + line * P + k2 * (M + 1);
+#pragma unroll
+            for (int n1 = 0; n1 < M; ++n1) u[n1] = src[n1];
+            Dft<M, -1>::run(u);
+            float2* dst = a.spec + (((size_t)b * 3 + wave) * N + y0 + line) * N + k2;
+            const uint64_t el = policy_evict_last();
+#pragma unroll
+            for (int k1 = 0; k1 < M; ++k1) st_hint(dst + R * k1, u[k1], el);
+        }
+    }
+}
+
+// Blocks per SM of the line-search column pass: it holds A, the d2I partial
+// and one more wave per pixel in registers.
+template <int N>
+__host__ __device__ constexpr int ls_min_blocks() {
+    return Plan<N>::M >= 20 ? 1 : 2;
+}
+
+// Column pass: column transforms of the waves (A first, then C, then B, so
+// that the reduction runs on B while it is in registers) and the FP64 sums
+//   L'(0)  = sum (1 - I_o/I_c) dI,  L''(0) = sum [(1 - I_o/I_c) d2I + (I_o/I_c^2) dI^2]
+// with dI = 2 Re(conj(A) B), d2I = 2 |B|^2 + 4 Re(conj(A) C), over unmasked
+// pixels; one (L', L'') pair per block into ls_part[j][blockIdx.x].  The
+// per-pixel terms are single precision (I_o dI^2 / I_c^2 as I_o (dI / I_c)^2,
+// which stays finite at the I_c floor), summed with compensation per thread and
+// in FP64 across the block.  grid (N / C, frames in batch).
+template <int N>
+__global__ void __launch_bounds__(kThreads, ls_min_blocks<N>()) k_col_ls_r(ProbArgs a, int j0, int nwaves) {
+    using S = RegShape<N>;
+    constexpr int R = S::R, M = S::M, C = S::L, P = S::P;
+    extern __shared__ __align__(16) float2 sm[];
+    __shared__ double red_s[kThreads / 32];
+    float2* tw = sm;
+    float2* buf = sm + N;
+    load_twiddles<N>(tw);
+    const int x0 = blockIdx.x * C;
+    const int b = blockIdx.y;
+    const int j = j0 + b;
+    constexpr float invN2 = 1.0f / float(N * N);
+    float2 A[S::I2][M];
+    float d2[S::I2][M];
+    KahanF l1, l2;  // per-pixel terms in single precision (FP64 throughput is low), compensated sums
+    __syncthreads();
+    for (int s = 0; s < nwaves; ++s) {
+        const int wave = s == 0 ? 0 : (s == nwaves - 1 ? 1 : 2);
+        const float2* spec = a.spec + ((size_t)b * 3 + wave) * N * N + x0;
+#pragma unroll
+        for (int i = 0; i < S::I1; ++i) {
+            const int w = threadIdx.x + i * kThreads;
+            if (w < C * M) {
+                const int n1 = w / C, c = w - n1 * C;
+                float2 v[R];
+#pragma unroll
+                for (int n2 = 0; n2 < R; ++n2) v[n2] = __ldcs(spec + (size_t)(n1 + M * n2) * N + c);
+                Dft<R, -1>::run(v);
+                float2* o = buf + c * P + n1;
+                o[0] = v[0];
+#pragma unroll
+                for (int k2 = 1; k2 < R; ++k2) o[k2 * (M + 1)] = cmul(v[k2], tw_get<N, -1>(tw, k2, n1));
+            }
+        }
+        __syncthreads();
+        float2 u[S::I2][M];
+#pragma unroll
+        for (int i = 0; i < S::I2; ++i) {
+            const int w = threadIdx.x + i * kThreads;
+            if (w < C * R) {
+                const int k2 = w / C, c = w - k2 * C;
+                const float2* src = buf + c * P + k2 * (M + 1);
+#pragma unroll
+                for (int n1 = 0; n1 < M; ++n1) u[i][n1] = src[n1];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < S::I2; ++i) {
+            const int w = threadIdx.x + i * kThreads;
+            if (w < C * R) {
+                const int k2 = w / C, c = w - k2 * C;
+                Dft<M, -1>::run(u[i]);
+                if (s == 0) {
+#pragma unroll
+                    for (int k1 = 0; k1 < M; ++k1) {
+                        A[i][k1] = u[i][k1];
+                        d2[i][k1] = 0.f;
+                    }
+                } else if (wave == 2) {
+#pragma unroll
+                    for (int k1 = 0; k1 < M; ++k1)
+                        d2[i][k1] = 4.f * (A[i][k1].x * u[i][k1].x + A[i][k1].y * u[i][k1].y) * invN2;
+                } else {
+                    uint32_t mbits = 0u;
+                    if (a.mbits) mbits = a.mbits[blockIdx.x * kThreads + threadIdx.x] >> (i * M);
+                    const float* io_p = a.iobs + (size_t)j * N * N + (size_t)k2 * N + x0 + c;
+#pragma unroll
+                    for (int k1 = 0; k1 < M; ++k1) {
+                        const int pix = (k2 + R * k1) * N + x0 + c;
+                        const bool masked = a.mbits ? ((mbits >> k1) & 1u) : (a.mask[pix] != 0);
+                        if (masked) continue;
+                        const float2 av = A[i][k1], bv = u[i][k1];
+                        const float ic = cnorm(av) * invN2 + (a.bg ? __ldg(a.bg + pix) : 0.f);
+                        const float di = 2.f * (av.x * bv.x + av.y * bv.y) * invN2;
+                        const float dd = d2[i][k1] + 2.f * cnorm(bv) * invN2;
+                        const float io = fmaxf(__ldcs(io_p + (size_t)R * k1 * N), 0.f);
+                        const float icf = fmaxf(ic, 1e-30f);
+                        const float w1 = 1.f - io / icf;
+                        const float q = di / icf;  // I_o dI^2 / I_c^2 = I_o q^2
+                        l1.add(w1 * di);
+                        l2.add(fmaf(w1, dd, io * q * q));
+                    }
+                }
+            }
+        }
+    }
+    const double t1 = block_sum_double<kThreads>(l1.value(), red_s);
+    __syncthreads();
+    const double t2 = block_sum_double<kThreads>(l2.value(), red_s);
+    if (threadIdx.x == 0) {
+        double* out = a.ls_part + 2 * ((size_t)j * gridDim.x + blockIdx.x);
+        out[0] = t1;
+        out[1] = t2;
+    }
+}
+
 template <int N>
 size_t smem_row_fwd_r() { return sizeof(float2) * (N + (size_t)RegShape<N>::L * RegShape<N>::P); }
 template <int N>
@@ -483,6 +669,8 @@ cudaError_t set_attrs_r() {
     if ((e = cudaFuncSetAttribute(k_col_r<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_row_bwd_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_fwd_ls_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_ls_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_row_fwd_r<N>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
