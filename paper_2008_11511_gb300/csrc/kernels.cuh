@@ -663,7 +663,10 @@ void launch_row_fwd(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s)
     if constexpr (has_reg<N>()) {
         if (a.K == 1) {
             dim3 grid(N / RegShape<N>::L, nb);
-            k_row_fwd_r<N><<<grid, kThreads, smem_row_fwd_r<N>(), s>>>(a, j0, mode);
+            if (mode == X_DM)
+                k_row_fwd_r<N, true><<<grid, kThreads, smem_row_fwd_r<N>(), s>>>(a, j0);
+            else
+                k_row_fwd_r<N, false><<<grid, kThreads, smem_row_fwd_r<N>(), s>>>(a, j0);
             return;
         }
     }

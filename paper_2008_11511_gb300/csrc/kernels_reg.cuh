@@ -53,11 +53,13 @@ __device__ __forceinline__ float2 tw_get(const float2* tw, int a, int b) {
 }
 
 // ---------------------------------------------------------------------------
-// Row forward: Phi = P O[r_j], X = Phi or 2 Phi - Psi, row FFT -> spec.
+// Row forward: Phi = P O[r_j], X = Phi or 2 Phi - Psi (kDM), row FFT -> spec.
+// The DM form issues its exit-wave loads (HBM) ahead of the probe and object
+// loads (L1 / L2).
 // grid (N / L, frames in batch)
 // ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_r(ProbArgs a, int j0, int mode) {
+template <int N, bool kDM>
+__global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_r(ProbArgs a, int j0) {
     using S = RegShape<N>;
     constexpr int R = S::R, M = S::M, L = S::L, P = S::P;
     extern __shared__ __align__(16) float2 sm[];
@@ -77,17 +79,19 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_r(
             const int y = y0 + line;
             const float2* pr = a.probe + (size_t)y * N + n1;
             const float2* ob = a.obj + (size_t)(p.x + y) * a.Wo + p.y + n1;
-            float2 v[R];
-#pragma unroll
-            for (int n2 = 0; n2 < R; ++n2) v[n2] = cmul(__ldg(pr + M * n2), ob[M * n2]);
-            if (mode == X_DM) {
+            float2 q[kDM ? R : 1];
+            if constexpr (kDM) {
                 const float2* ps = a.psi + ((size_t)j * N + y) * N + n1;
                 const uint64_t ef = policy_evict_first();
 #pragma unroll
-                for (int n2 = 0; n2 < R; ++n2) {
-                    const float2 q = ld_hint(ps + M * n2, ef);
-                    v[n2] = make_float2(2.f * v[n2].x - q.x, 2.f * v[n2].y - q.y);
-                }
+                for (int n2 = 0; n2 < R; ++n2) q[n2] = ld_hint(ps + M * n2, ef);
+            }
+            float2 v[R];
+#pragma unroll
+            for (int n2 = 0; n2 < R; ++n2) v[n2] = cmul(__ldg(pr + M * n2), ob[M * n2]);
+            if constexpr (kDM) {
+#pragma unroll
+                for (int n2 = 0; n2 < R; ++n2) v[n2] = make_float2(2.f * v[n2].x - q[n2].x, 2.f * v[n2].y - q[n2].y);
             }
             Dft<R, -1>::run(v);
             float2* o = buf + line * P + n1;
@@ -665,13 +669,15 @@ cudaError_t set_attrs_r() {
     cudaError_t e;
     const int mx = 200 * 1024;
     const int carve = cudaSharedmemCarveoutMaxShared;  // room for 5-6 blocks of ~37 KB per SM
-    if ((e = cudaFuncSetAttribute(k_row_fwd_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_fwd_r<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_fwd_r<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_row_bwd_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_row_fwd_ls_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_ls_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-    if ((e = cudaFuncSetAttribute(k_row_fwd_r<N>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_fwd_r<N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_fwd_r<N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_row_bwd_r<N>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
