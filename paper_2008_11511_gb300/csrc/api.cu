@@ -251,8 +251,13 @@ void set_batch(ProbHost& h, size_t spec_bytes, int lanes, int cap = 0) {
     if (B > (size_t)p.J) B = p.J;
     if (B > 32768) B = 32768;  // grid.y limit of the batch kernels
     h.B = (int)B;
-    const int rowblk = p.N / h.L3;
-    int G = (2 * 152 + rowblk - 1) / rowblk;
+    // frame slots G of the row-backward pass: (N / L3) row blocks x K modes x G
+    // blocks, 2 resident per SM.  Each block flushes its probe sums once, so
+    // the slots fill the GPU about once (one mode: rounded up; several modes,
+    // where the blocks are K times as many: rounded down).
+    const int resident = 2 * 152;
+    const int rowblk = p.N / h.L3 * p.K;
+    int G = p.K == 1 ? (resident + rowblk - 1) / rowblk : resident / rowblk;
     if (G > h.B) G = h.B;
     if (G < 1) G = 1;
     h.G3 = G;
@@ -263,7 +268,10 @@ void plan_problem(ProbHost& h) {
     h.ks = kernel_set(p.N);
     const int maxl = h.ks->max_lines;
     if (use_reg_kernels(h.ks, p.K)) {
-        h.L1 = h.C2 = h.L3 = h.ks->reg_lines;
+        h.L1 = h.L3 = h.ks->reg_lines;
+        // LLK partials per frame: one per column block (near field: per row
+        // block of its projection pass)
+        h.C2 = p.nearfield > 0.0 ? h.ks->reg_lines : h.ks->reg_cols;
     } else {
         h.L1 = choose_lines(p.N, p.K, maxl);
         h.C2 = choose_lines(p.N, p.K, maxl);
@@ -306,11 +314,11 @@ size_t layout_problem(ProbHost& h) {
     h.lay.cg_probe = o;
     o = align_up(o + 3 * sizeof(float2) * (size_t)p.K * p.N * p.N);
     h.lay.ls_part = o;
-    o = align_up(o + 2 * sizeof(double) * (size_t)p.J * (p.N / std::min(h.ks->ls_lines, h.ks->reg_lines > 0 ? h.ks->reg_lines : h.ks->ls_lines)));
+    o = align_up(o + 2 * sizeof(double) * (size_t)p.J * (p.N / ls_cols(h.ks, p.K)));
     h.lay.cg = o;
     o = align_up(o + 8 * sizeof(double));
     h.lay.mbits = o;
-    if (use_reg_kernels(h.ks, p.K)) o = align_up(o + sizeof(uint32_t) * (size_t)(p.N / h.ks->reg_lines) * kThreads);
+    if (use_reg_kernels(h.ks, p.K)) o = align_up(o + sizeof(uint32_t) * (size_t)(p.N / h.ks->reg_cols) * kThreads);
     h.lay.nf_t = o;
     if (p.nearfield > 0.0) o = align_up(o + sizeof(float2) * (size_t)p.N);
     h.lay.bg_acc = o;
@@ -417,9 +425,9 @@ namespace {
 
 // Mask bits of the register column pass: entry [xb][t] holds, for thread t of
 // column block xb, bit (i M + k1) = mask at row k2 + R k1, column xb C + c of its
-// pass-2 item i (w = t + 256 i, k2 = w / C, c = w % C), C = lines per block.
+// pass-2 item i (w = t + 256 i, k2 = w / C, c = w % C), C = columns per block.
 std::vector<uint32_t> mask_bits(const KernelSet* ks, int N, const uint8_t* mask) {
-    const int C = ks->reg_lines, R = ks->R, M = ks->M, XB = N / C;
+    const int C = ks->reg_cols, R = ks->R, M = ks->M, XB = N / C;
     const int I2 = (C * R + kThreads - 1) / kThreads;
     std::vector<uint32_t> t((size_t)XB * kThreads, 0u);
     for (int xb = 0; xb < XB; ++xb)
@@ -1017,8 +1025,7 @@ ptx_status enqueue_line_coeffs(ptx_handle* h, ProbHost& ph, const float2* d_obj,
         ph.ks->col_ls(a, j0, nb, 0, s);
     }
     // partial pairs per frame: one per column block of the line-search column pass
-    const int ls_cols = use_reg_kernels(ph.ks, ph.p.K) ? ph.ks->reg_lines : ph.ks->ls_lines;
-    k_ls_reduce<<<1, 1024, 0, s>>>(a.ls_part, (size_t)ph.p.J * (ph.p.N / ls_cols), out);
+    k_ls_reduce<<<1, 1024, 0, s>>>(a.ls_part, (size_t)ph.p.J * (ph.p.N / ls_cols(ph.ks, ph.p.K)), out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "line-search launch");
     return PTX_OK;

@@ -625,6 +625,7 @@ struct KernelSet {
     int max_lines;  // lines per block of the shared-memory kernels
     int ls_lines;   // rows / columns per block of the line-search kernels
     int reg_lines;  // lines per block of the register kernels (0: none for this N)
+    int reg_cols;   // columns per block of the register column passes
     int R, M;
     // column pass fed by tensor copies (K = 1; null where N has none) and its persistent grid
     void (*col_tma)(const void* tm_spec, const void* tm_io, const void* tm_mask, const ProbArgs&, int j0, int nb,
@@ -636,8 +637,11 @@ struct KernelSet {
 };
 
 const KernelSet* kernel_set(int N);
-// Whether the register-resident kernels serve a problem with K modes.
-inline bool use_reg_kernels(const KernelSet* ks, int K) { return K == 1 && ks->reg_lines > 0; }
+// Whether the register-resident kernels serve a problem with K modes (they
+// exist for every two-pass size N, any K).
+inline bool use_reg_kernels(const KernelSet* ks, int K) { return K >= 1 && ks->reg_lines > 0; }
+// Columns per block of the line-search column pass (register form for one mode).
+inline int ls_cols(const KernelSet* ks, int K) { return (K == 1 && ks->reg_lines > 0) ? ks->reg_cols : ks->ls_lines; }
 
 template <int N>
 size_t smem_row_fwd_t(int K, int L) { return sizeof(float2) * (N + (size_t)K * L * line_pitch<N>()); }
@@ -661,14 +665,12 @@ constexpr bool has_reg() { return Plan<N>::M > 1; }
 template <int N>
 void launch_row_fwd(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s) {
     if constexpr (has_reg<N>()) {
-        if (a.K == 1) {
-            dim3 grid(N / RegShape<N>::L, nb);
-            if (mode == X_DM)
-                k_row_fwd_r<N, true><<<grid, kThreads, smem_row_fwd_r<N>(), s>>>(a, j0);
-            else
-                k_row_fwd_r<N, false><<<grid, kThreads, smem_row_fwd_r<N>(), s>>>(a, j0);
-            return;
-        }
+        dim3 grid(N / RegShape<N>::L, nb * a.K);
+        if (mode == X_DM)
+            k_row_fwd_r<N, true><<<grid, kThreads, smem_row_fwd_r<N>(), s>>>(a, j0);
+        else
+            k_row_fwd_r<N, false><<<grid, kThreads, smem_row_fwd_r<N>(), s>>>(a, j0);
+        return;
     }
     dim3 grid(N / a.L1, nb);
     k_row_fwd<N><<<grid, kThreads, smem_row_fwd_t<N>(a.K, a.L1), s>>>(a, j0, mode);
@@ -676,14 +678,14 @@ void launch_row_fwd(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s)
 template <int N>
 void launch_col(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s) {
     if constexpr (has_reg<N>()) {
-        if (a.K == 1) {
-            dim3 grid(N / RegShape<N>::L, nb);
-            if (a.bg)
-                k_col_r<N, true><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, mode);
-            else
-                k_col_r<N, false><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, mode);
-            return;
-        }
+        dim3 grid(N / RegShape<N>::C, nb);
+        if (a.K > 1)
+            k_col_modes_r<N><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, mode);
+        else if (a.bg)
+            k_col_r<N, true><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, mode);
+        else
+            k_col_r<N, false><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, mode);
+        return;
     }
     dim3 grid(N / a.C2, nb);
     k_col<N><<<grid, kThreads, smem_col_t<N>(a.K, a.C2), s>>>(a, j0, mode);
@@ -691,11 +693,9 @@ void launch_col(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s) {
 template <int N>
 void launch_row_bwd(const ProbArgs& a, int j0, int nb, int G, int mode, int upd_obj, int upd_probe, cudaStream_t s) {
     if constexpr (has_reg<N>()) {
-        if (a.K == 1) {
-            dim3 grid(N / RegShape<N>::L, G);
-            k_row_bwd_r<N><<<grid, kThreads, smem_row_bwd_r<N>(), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
-            return;
-        }
+        dim3 grid(N / RegShape<N>::L, G * a.K);  // G frame slots per probe mode
+        k_row_bwd_r<N><<<grid, kThreads, smem_row_bwd_r<N>(), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
+        return;
     }
     dim3 grid(N / a.L3, G);
     k_row_bwd<N><<<grid, kThreads, smem_row_bwd_t<N>(a.K, a.L3), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
@@ -724,7 +724,7 @@ template <int N>
 void launch_col_ls(const ProbArgs& a, int j0, int nb, int, cudaStream_t s) {
     if constexpr (has_reg<N>()) {
         if (a.K == 1) {
-            dim3 grid(N / RegShape<N>::L, nb);
+            dim3 grid(N / RegShape<N>::C, nb);
             k_col_ls_r<N><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, (a.dir_obj && a.dir_probe) ? 3 : 2);
             return;
         }
@@ -773,6 +773,7 @@ cudaError_t set_attrs_t() {
 template <int N>
 const KernelSet* make_kernel_set() {
     constexpr int rl = has_reg<N>() ? reg_lines<N>() : 0;
+    constexpr int rc = has_reg<N>() ? reg_cols<N>() : 0;
     static const KernelSet ks = {N,
                                  &launch_row_fwd<N>,
                                  &launch_col<N>,
@@ -783,6 +784,7 @@ const KernelSet* make_kernel_set() {
                                  max_lines<N>(),
                                  ls_lines<N>(),
                                  rl,
+                                 rc,
                                  Plan<N>::R,
                                  Plan<N>::M,
                                  ColTma<N>::kOk ? &launch_col_tma<N> : nullptr,

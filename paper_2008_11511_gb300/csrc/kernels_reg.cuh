@@ -1,4 +1,5 @@
-// Register-resident passes of the cycle for one probe mode (K = 1).
+// Register-resident passes of the cycle (any number of probe modes K; the
+// column pass has a one-mode and a K-mode form).
 //
 // Each line transform N = R * M keeps its data in registers from the global
 // load to the global store with a single padded shared-memory transpose:
@@ -23,6 +24,12 @@ template <int N>
 __host__ __device__ constexpr int reg_lines() {
     return N >= 384 ? 8 : ((N == 192 || N == 80 || N == 160 || N == 224) ? 16 : (4096 / N > N ? N : 4096 / N));
 }
+// Columns per block of the register column passes: 16 for the large sizes,
+// whose radix-16 first stage then gives every thread one pass-2 item.
+template <int N>
+__host__ __device__ constexpr int reg_cols() {
+    return (N == 384 || N == 448 || N == 512) ? 16 : reg_lines<N>();
+}
 // Shared-memory pitch of a line: room for both padded intermediate layouts
 // (R (M+1) and M (R+1) elements), odd.
 template <int N>
@@ -35,6 +42,11 @@ struct RegShape {
     static constexpr int R = Plan<N>::R, M = Plan<N>::M, L = reg_lines<N>(), P = reg_pitch<N>();
     static constexpr int I1 = (L * M + kThreads - 1) / kThreads;  // pass-1 items per thread
     static constexpr int I2 = (L * R + kThreads - 1) / kThreads;  // pass-2 items per thread
+    // the column passes: C columns per block, their items per thread
+    static constexpr int C = reg_cols<N>();
+    static constexpr int CI1 = (C * M + kThreads - 1) / kThreads;
+    static constexpr int CI2 = (C * R + kThreads - 1) / kThreads;
+    static_assert(N % C == 0 && CI2 * M <= 32, "columns divide N; a thread's pixels fit the 32 mask bits");
     // blocks per SM the register budget is sized for: large codelets (24, 32
     // points) need more registers per thread
     static constexpr int MinBlocks = (R > M ? R : M) >= 20 ? 2 : 5;
@@ -53,10 +65,10 @@ __device__ __forceinline__ float2 tw_get(const float2* tw, int a, int b) {
 }
 
 // ---------------------------------------------------------------------------
-// Row forward: Phi = P O[r_j], X = Phi or 2 Phi - Psi (kDM), row FFT -> spec.
-// The DM form issues its exit-wave loads (HBM) ahead of the probe and object
-// loads (L1 / L2).
-// grid (N / L, frames in batch)
+// Row forward: Phi_k = P_k O[r_j], X = Phi_k or 2 Phi_k - Psi_k (kDM), row FFT
+// -> spec.  The DM form issues its exit-wave loads (HBM) ahead of the probe
+// and object loads (L1 / L2).
+// grid (N / L, frames in batch x K); blockIdx.y = frame * K + mode
 // ---------------------------------------------------------------------------
 template <int N, bool kDM>
 __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_r(ProbArgs a, int j0) {
@@ -66,10 +78,12 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_r(
     float2* tw = sm;
     float2* buf = sm + N;
     load_twiddles<N>(tw);
+    const int K = a.K;
     const int y0 = blockIdx.x * L;
-    const int b = blockIdx.y;
+    const int b = blockIdx.y / K, k = blockIdx.y - b * K;
     const int j = j0 + b;
     const int2 p = a.pos[j];
+    const float2* probe = a.probe + (size_t)k * N * N;
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < S::I1; ++i) {
@@ -77,11 +91,11 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_r(
         if (w < L * M) {
             const int line = w / M, n1 = w - line * M;
             const int y = y0 + line;
-            const float2* pr = a.probe + (size_t)y * N + n1;
+            const float2* pr = probe + (size_t)y * N + n1;
             const float2* ob = a.obj + (size_t)(p.x + y) * a.Wo + p.y + n1;
             float2 q[kDM ? R : 1];
             if constexpr (kDM) {
-                const float2* ps = a.psi + ((size_t)j * N + y) * N + n1;
+                const float2* ps = a.psi + (((size_t)j * K + k) * N + y) * N + n1;
                 const uint64_t ef = policy_evict_first();
 #pragma unroll
                 for (int n2 = 0; n2 < R; ++n2) q[n2] = ld_hint(ps + M * n2, ef);
@@ -111,7 +125,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_r(
 #pragma unroll
             for (int n1 = 0; n1 < M; ++n1) u[n1] = src[n1];
             Dft<M, -1>::run(u);
-            float2* dst = a.spec + ((size_t)b * N + y0 + line) * N + k2;
+            float2* dst = a.spec + (((size_t)b * K + k) * N + y0 + line) * N + k2;
             const uint64_t el = policy_evict_last();
 #pragma unroll
             for (int k1 = 0; k1 < M; ++k1) st_hint(dst + R * k1, u[k1], el);
@@ -128,7 +142,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_r(
 template <int N, bool kBg>
 __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(ProbArgs a, int j0, int mode) {
     using S = RegShape<N>;
-    constexpr int R = S::R, M = S::M, C = S::L, P = S::P;
+    constexpr int R = S::R, M = S::M, C = S::C, P = S::P;
     constexpr int I1b = (C * M + kThreads - 1) / kThreads;  // inverse pass-2 items (M per column)
     static_assert(C % 8 == 0 && (C * P) % 2 == 0, "8- / 16-byte chunks and a 16-byte aligned stage");
     extern __shared__ __align__(16) float2 sm[];
@@ -142,9 +156,9 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(P
     float2* spec = a.spec + (size_t)b * N * N + x0;
     // intensities of this thread's pass-2 pixels (rows k2 + R k1 of column c),
     // loaded into registers while the forward transform runs, and their mask bits
-    float io_r[S::I2][M];
+    float io_r[S::CI2][M];
 #pragma unroll
-    for (int i = 0; i < S::I2; ++i) {
+    for (int i = 0; i < S::CI2; ++i) {
         const int w = threadIdx.x + i * kThreads;
         if (w < C * R) {
             const int k2 = w / C, c = w - k2 * C;
@@ -158,7 +172,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(P
         mbits = a.mbits[blockIdx.x * kThreads + threadIdx.x];
     } else {  // callers without the table (the allocation-free entry point) read the mask bytes
 #pragma unroll
-        for (int i = 0; i < S::I2; ++i) {
+        for (int i = 0; i < S::CI2; ++i) {
             const int w = threadIdx.x + i * kThreads;
             if (w < C * R) {
                 const int k2 = w / C, c = w - k2 * C;
@@ -171,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(P
     __syncthreads();
     // forward pass 1: thread (c, n1) holds rows n1 + M n2 of column c
 #pragma unroll
-    for (int i = 0; i < S::I1; ++i) {
+    for (int i = 0; i < S::CI1; ++i) {
         const int w = threadIdx.x + i * kThreads;
         if (w < C * M) {
             const int n1 = w / C, c = w - n1 * C;
@@ -188,9 +202,9 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(P
     }
     __syncthreads();
     // forward pass 2 into registers: thread (c, k2) holds X^[k2 + R k1]
-    float2 u[S::I2][M];
+    float2 u[S::CI2][M];
 #pragma unroll
-    for (int i = 0; i < S::I2; ++i) {
+    for (int i = 0; i < S::CI2; ++i) {
         const int w = threadIdx.x + i * kThreads;
         if (w < C * R) {
             const int k2 = w / C, c = w - k2 * C;
@@ -203,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(P
     constexpr float invN2 = 1.0f / float(N * N);
     KahanF llk;
 #pragma unroll
-    for (int i = 0; i < S::I2; ++i) {
+    for (int i = 0; i < S::CI2; ++i) {
         const int w = threadIdx.x + i * kThreads;
         if (w < C * R) {
             const int k2 = w / C, c = w - k2 * C;
@@ -264,11 +278,168 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(P
 }
 
 // ---------------------------------------------------------------------------
+// Column pass for K > 1 probe modes.  The projection factor of a pixel is
+// common to its modes (sqrt(I_o) / sqrt(sum_k |X^_k|^2)), so the pass runs in
+// two sweeps over the modes:
+//   1. forward column transform of each mode; the thread sums |X^_k|^2 over
+//      the modes for its pixels in registers and writes X^_k back into the
+//      stack at those same pixels (L2);
+//   2. the factor (and the LLK) per pixel, then for each mode: the thread
+//      reloads its own X^_k, scales it, and the inverse column transform
+//      writes the mode back.
+// The thread-to-pixel mapping is that of k_col_r (so the mask-bit table is
+// shared).  grid (N / C, frames in batch).
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_modes_r(ProbArgs a, int j0, int mode) {
+    using S = RegShape<N>;
+    constexpr int R = S::R, M = S::M, C = S::C, P = S::P;
+    constexpr int I1b = (C * M + kThreads - 1) / kThreads;  // inverse pass-2 items (M per column)
+    extern __shared__ __align__(16) float2 sm[];
+    __shared__ double red_s[kThreads / 32];
+    float2* tw = sm;
+    float2* buf = sm + N;
+    load_twiddles<N>(tw);
+    const int K = a.K;
+    const int x0 = blockIdx.x * C;
+    const int b = blockIdx.y;
+    const int j = j0 + b;
+    float2* spec_b = a.spec + (size_t)b * K * N * N + x0;
+    float ic_r[S::CI2][M];  // sum over modes of |X^_k|^2, then the factor
+#pragma unroll
+    for (int i = 0; i < S::CI2; ++i)
+#pragma unroll
+        for (int k1 = 0; k1 < M; ++k1) ic_r[i][k1] = 0.f;
+    __syncthreads();
+    // sweep 1: forward transforms
+    for (int k = 0; k < K; ++k) {
+        float2* spec = spec_b + (size_t)k * N * N;
+#pragma unroll
+        for (int i = 0; i < S::CI1; ++i) {
+            const int w = threadIdx.x + i * kThreads;
+            if (w < C * M) {
+                const int n1 = w / C, c = w - n1 * C;
+                float2 v[R];
+                const uint64_t el = policy_evict_last();
+#pragma unroll
+                for (int n2 = 0; n2 < R; ++n2) v[n2] = ld_hint(spec + (size_t)(n1 + M * n2) * N + c, el);
+                Dft<R, -1>::run(v);
+                float2* o = buf + c * P + n1;
+                o[0] = v[0];
+#pragma unroll
+                for (int k2 = 1; k2 < R; ++k2) o[k2 * (M + 1)] = cmul(v[k2], tw_get<N, -1>(tw, k2, n1));
+            }
+        }
+        __syncthreads();
+        float2 u[S::CI2][M];
+#pragma unroll
+        for (int i = 0; i < S::CI2; ++i) {
+            const int w = threadIdx.x + i * kThreads;
+            if (w < C * R) {
+                const int k2 = w / C, c = w - k2 * C;
+                const float2* src = buf + c * P + k2 * (M + 1);
+#pragma unroll
+                for (int n1 = 0; n1 < M; ++n1) u[i][n1] = src[n1];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < S::CI2; ++i) {
+            const int w = threadIdx.x + i * kThreads;
+            if (w < C * R) {
+                const int k2 = w / C, c = w - k2 * C;
+                Dft<M, -1>::run(u[i]);
+                const uint64_t el = policy_evict_last();
+#pragma unroll
+                for (int k1 = 0; k1 < M; ++k1) {
+                    ic_r[i][k1] += cnorm(u[i][k1]);
+                    st_hint(spec + (size_t)(k2 + R * k1) * N + c, u[i][k1], el);
+                }
+            }
+        }
+    }
+    // the factor per pixel and the LLK
+    constexpr float invN2 = 1.0f / float(N * N);
+    KahanF llk;
+#pragma unroll
+    for (int i = 0; i < S::CI2; ++i) {
+        const int w = threadIdx.x + i * kThreads;
+        if (w < C * R) {
+            const int k2 = w / C, c = w - k2 * C;
+            uint32_t mbits = 0u;
+            if (a.mbits) mbits = a.mbits[blockIdx.x * kThreads + threadIdx.x] >> (i * M);
+            const float* ib = a.iobs + (size_t)j * N * N + (size_t)k2 * N + x0 + c;
+#pragma unroll
+            for (int k1 = 0; k1 < M; ++k1) {
+                const int pix = (k2 + R * k1) * N + x0 + c;
+                const bool masked = a.mbits ? ((mbits >> k1) & 1u) != 0u : a.mask[pix] != 0;
+                float ic = ic_r[i][k1] * invN2;
+                const float io = __ldcs(ib + (size_t)R * k1 * N);
+                if (a.bg) {
+                    ic += __ldg(a.bg + pix);
+                    if (a.bg_acc && !masked) atomicAdd(a.bg_acc + pix, fmaxf(io, 0.f) / fmaxf(ic, 1e-30f));
+                }
+                if (!masked) llk.add(llk_term_fast(ic, io));
+                float f;
+                if (masked)
+                    f = 0.f;
+                else if (mode == COL_PROJECT)
+                    f = (amp_ratio(io, ic) - 1.0f) * invN2;
+                else
+                    f = 2.0f * (1.0f - __fdividef(fmaxf(io, 0.f), fmaxf(ic, 1e-30f))) * invN2;
+                ic_r[i][k1] = f;
+            }
+        }
+    }
+    const double tot = block_sum_double<kThreads>(llk.value(), red_s);
+    if (threadIdx.x == 0) a.llk_part[(size_t)j * gridDim.x + blockIdx.x] = tot;
+    if (mode == COL_LLK) return;
+    // sweep 2: scale and inverse transforms
+    for (int k = 0; k < K; ++k) {
+        float2* spec = spec_b + (size_t)k * N * N;
+#pragma unroll
+        for (int i = 0; i < S::CI2; ++i) {
+            const int w = threadIdx.x + i * kThreads;
+            if (w < C * R) {
+                const int k2 = w / C, c = w - k2 * C;
+                float2 u[M];
+#pragma unroll
+                for (int k1 = 0; k1 < M; ++k1) u[k1] = cscale(spec[(size_t)(k2 + R * k1) * N + c], ic_r[i][k1]);
+                // inverse pass 1: M-point codelet over k1, twiddle w_N^(+k2 k2'), y'[k2' (R+1) + k2]
+                Dft<M, +1>::run(u);
+                float2* o = buf + c * P + k2;
+                o[0] = u[0];
+#pragma unroll
+                for (int kk = 1; kk < M; ++kk) o[kk * (R + 1)] = cmul(u[kk], tw_get<N, +1>(tw, k2, kk));
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < I1b; ++i) {
+            const int w = threadIdx.x + i * kThreads;
+            if (w < C * M) {
+                const int kk = w / C, c = w - kk * C;
+                float2 v[R];
+                const float2* src = buf + c * P + kk * (R + 1);
+#pragma unroll
+                for (int n = 0; n < R; ++n) v[n] = src[n];
+                Dft<R, +1>::run(v);
+                const uint64_t el = policy_evict_last();
+#pragma unroll
+                for (int k1 = 0; k1 < R; ++k1) st_hint(spec + (size_t)(kk + M * k1) * N + c, v[k1], el);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Row backward: inverse row FFT -> D; Psi' = Phi + D stored to the exit-wave
 // stack (AP and DM), probe numerator/denominator in registers across the
 // block's frames, flushed once.  In gradient mode D is the back-propagated
 // weighted wave: G_O is scattered with red.v2, G_P reduced like N_P.
-// grid (N / L, G); block handles rows [y0, y0 + L) of frames blockIdx.y + G t.
+// grid (N / L, G K); blockIdx.y = slot * K + mode: the block handles rows
+// [y0, y0 + L) of one probe mode in frames slot + G t.
 // ---------------------------------------------------------------------------
 template <int N>
 __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, int nb, int mode, int upd_obj,
@@ -288,13 +459,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
     float2* np_s = buf + L * P;                 // [L][N] when !kRegAcc
     float* dp_s = (float*)(np_s + L * N);       // [L][N]
     load_twiddles<N>(tw);
+    const int K = a.K;
     const int y0 = blockIdx.x * L;
+    const int slot = blockIdx.y / K, k = blockIdx.y - slot * K;
+    const int G = gridDim.y / K;
+    const size_t mode_off = (size_t)k * N * N;  // probe mode k
     const bool acc_p = upd_probe != 0;
     // the rows [y0, y0 + L) of frame b are contiguous: copy them in 16-byte chunks
     // The work-stack stage is free once pass 1 has read it; the object stage only
     // after the update that reads it, so the two are refilled at different points.
     auto prefetch_spec = [&](int b) {
-        const float2* src = a.spec + ((size_t)b * N + y0) * N;
+        const float2* src = a.spec + (((size_t)b * K + k) * N + y0) * N;
         const uint64_t ef = policy_evict_first();  // the stack's last read
         for (int e = threadIdx.x; e < L * N / 2; e += kThreads) cp_async16_hint(stage + 2 * e, src + 2 * e, ef);
         cp_async_commit();
@@ -310,9 +485,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
         }
         cp_async_commit();
     };
-    if (blockIdx.y < nb) {
-        prefetch_spec(blockIdx.y);
-        prefetch_obj(blockIdx.y);
+    if (slot < nb) {
+        prefetch_spec(slot);
+        prefetch_obj(slot);
     }
     const bool acc_o = upd_obj != 0;
     float2 np_r[IA][MA];
@@ -340,14 +515,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
             const int w = threadIdx.x + i * kThreads;
             if (w < L * R) {
                 const int line = w / R, k2 = w - line * R;
-                const float2* pr = a.probe + (size_t)(y0 + line) * N + k2;
+                const float2* pr = a.probe + mode_off + (size_t)(y0 + line) * N + k2;
 #pragma unroll
                 for (int k1 = 0; k1 < M; ++k1) pr_r[i][k1] = __ldg(pr + R * k1);
             }
         }
     }
     __syncthreads();
-    for (int b = blockIdx.y; b < nb; b += gridDim.y) {
+    for (int b = slot; b < nb; b += G) {
         const int j = j0 + b;
         const int2 p = a.pos[j];
         cp_async_wait_all();
@@ -369,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
             }
         }
         __syncthreads();
-        if (b + (int)gridDim.y < nb) prefetch_spec(b + gridDim.y);  // the work-stack stage is free again
+        if (b + G < nb) prefetch_spec(b + G);  // the work-stack stage is free again
 #pragma unroll
         for (int i = 0; i < S::I2; ++i) {
             const int w = threadIdx.x + i * kThreads;
@@ -381,10 +556,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
 #pragma unroll
                 for (int n1 = 0; n1 < M; ++n1) u[n1] = src[n1];
                 Dft<M, +1>::run(u);
-                const float2* pr = a.probe + (size_t)y * N + k2;
+                const float2* pr = a.probe + mode_off + (size_t)y * N + k2;
                 const size_t orow = (size_t)(p.x + y) * a.Wo + p.y + k2;
                 const float2* ob = (kStageObj && (mode != BWD_GRAD || acc_p)) ? ostage + line * N + k2 : a.obj + orow;
-                float2* ps = (mode != BWD_GRAD) ? a.psi + ((size_t)j * N + y) * N + k2 : nullptr;
+                float2* ps = (mode != BWD_GRAD) ? a.psi + (((size_t)j * K + k) * N + y) * N + k2 : nullptr;
 #pragma unroll
                 for (int k1 = 0; k1 < M; ++k1) {
                     float2 prv;
@@ -421,7 +596,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
             }
         }
         __syncthreads();
-        if (b + (int)gridDim.y < nb) prefetch_obj(b + gridDim.y);  // the object stage is free again
+        if (b + G < nb) prefetch_obj(b + G);  // the object stage is free again
     }
     if (acc_p) {
         if constexpr (kRegAcc) {
@@ -430,7 +605,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
                 const int w = threadIdx.x + i * kThreads;
                 if (w < L * R) {
                     const int line = w / R, k2 = w - line * R;
-                    const size_t pidx = (size_t)(y0 + line) * N + k2;
+                    const size_t pidx = mode_off + (size_t)(y0 + line) * N + k2;
 #pragma unroll
                     for (int k1 = 0; k1 < M; ++k1) {
                         if (mode == BWD_GRAD)
@@ -448,7 +623,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
                 const int w = threadIdx.x + i * kThreads;
                 if (w < L * R) {
                     const int line = w / R, k2 = w - line * R;
-                    const size_t pidx = (size_t)(y0 + line) * N + k2;
+                    const size_t pidx = mode_off + (size_t)(y0 + line) * N + k2;
 #pragma unroll 4
                     for (int k1 = 0; k1 < M; ++k1) {
                         const int e = line * N + k2 + R * k1;
@@ -554,7 +729,7 @@ __host__ __device__ constexpr int ls_min_blocks() {
 template <int N>
 __global__ void __launch_bounds__(kThreads, ls_min_blocks<N>()) k_col_ls_r(ProbArgs a, int j0, int nwaves) {
     using S = RegShape<N>;
-    constexpr int R = S::R, M = S::M, C = S::L, P = S::P;
+    constexpr int R = S::R, M = S::M, C = S::C, P = S::P;
     extern __shared__ __align__(16) float2 sm[];
     __shared__ double red_s[kThreads / 32];
     float2* tw = sm;
@@ -564,15 +739,15 @@ __global__ void __launch_bounds__(kThreads, ls_min_blocks<N>()) k_col_ls_r(ProbA
     const int b = blockIdx.y;
     const int j = j0 + b;
     constexpr float invN2 = 1.0f / float(N * N);
-    float2 A[S::I2][M];
-    float d2[S::I2][M];
+    float2 A[S::CI2][M];
+    float d2[S::CI2][M];
     KahanF l1, l2;  // per-pixel terms in single precision (FP64 throughput is low), compensated sums
     __syncthreads();
     for (int s = 0; s < nwaves; ++s) {
         const int wave = s == 0 ? 0 : (s == nwaves - 1 ? 1 : 2);
         const float2* spec = a.spec + ((size_t)b * 3 + wave) * N * N + x0;
 #pragma unroll
-        for (int i = 0; i < S::I1; ++i) {
+        for (int i = 0; i < S::CI1; ++i) {
             const int w = threadIdx.x + i * kThreads;
             if (w < C * M) {
                 const int n1 = w / C, c = w - n1 * C;
@@ -587,9 +762,9 @@ __global__ void __launch_bounds__(kThreads, ls_min_blocks<N>()) k_col_ls_r(ProbA
             }
         }
         __syncthreads();
-        float2 u[S::I2][M];
+        float2 u[S::CI2][M];
 #pragma unroll
-        for (int i = 0; i < S::I2; ++i) {
+        for (int i = 0; i < S::CI2; ++i) {
             const int w = threadIdx.x + i * kThreads;
             if (w < C * R) {
                 const int k2 = w / C, c = w - k2 * C;
@@ -600,7 +775,7 @@ __global__ void __launch_bounds__(kThreads, ls_min_blocks<N>()) k_col_ls_r(ProbA
         }
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i < S::I2; ++i) {
+        for (int i = 0; i < S::CI2; ++i) {
             const int w = threadIdx.x + i * kThreads;
             if (w < C * R) {
                 const int k2 = w / C, c = w - k2 * C;
@@ -654,7 +829,7 @@ size_t smem_row_fwd_r() { return sizeof(float2) * (N + (size_t)RegShape<N>::L * 
 template <int N>
 size_t smem_col_r() {
     using S = RegShape<N>;
-    return sizeof(float2) * (N + (size_t)S::L * S::P);
+    return sizeof(float2) * (N + (size_t)S::C * S::P);
 }
 template <int N>
 size_t smem_row_bwd_r() {
@@ -674,6 +849,8 @@ cudaError_t set_attrs_r() {
     if ((e = cudaFuncSetAttribute(k_col_r<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_row_bwd_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_modes_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_modes_r<N>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_row_fwd_ls_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_ls_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_row_fwd_r<N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;

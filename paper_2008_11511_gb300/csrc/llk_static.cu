@@ -104,8 +104,9 @@ ptx_status setup_device(int dev, unsigned char** out) {
     return PTX_OK;
 }
 
+// columns per block of the column pass (= LLK partial sums per frame)
 int lines_for(const ptx::KernelSet* ks, int N, int K) {
-    if (ptx::use_reg_kernels(ks, K)) return ks->reg_lines;
+    if (ptx::use_reg_kernels(ks, K)) return ks->reg_cols;
     int L = 1;
     while (K * L * 2 <= ks->max_lines && N % (L * 2) == 0) L *= 2;
     return L;
