@@ -242,6 +242,20 @@ ptx_status check_problem(const ptx_problem& p, int idx) {
 
 // Batches of frames: `lanes` batches are in flight at once (one per stream),
 // each with its own slice of the work-stack region of `spec_bytes`.
+// SMs of the current device (152 on GB300 when it cannot be asked)
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            cudaGetLastError();
+    }
+    return n > 0 ? n : 152;
+}
+
 void set_batch(ProbHost& h, size_t spec_bytes, int lanes, int cap = 0) {
     const ptx_problem& p = h.p;
     const size_t frame_bytes = (size_t)p.K * p.N * p.N * sizeof(float2);
@@ -252,12 +266,13 @@ void set_batch(ProbHost& h, size_t spec_bytes, int lanes, int cap = 0) {
     if (B > 32768) B = 32768;  // grid.y limit of the batch kernels
     h.B = (int)B;
     // frame slots G of the row-backward pass: (N / L3) row blocks x K modes x G
-    // blocks, 2 resident per SM.  Each block flushes its probe sums once, so
-    // the slots fill the GPU about once (one mode: rounded up; several modes,
-    // where the blocks are K times as many: rounded down).
-    const int resident = 2 * 152;
+    // blocks, as many as are resident at once (each block loops over its
+    // frames and flushes its probe sums once)
+    int per_sm = h.ks->row_bwd_per_sm();
+    if (per_sm <= 0) per_sm = 2;
+    const int resident = per_sm * sm_count();
     const int rowblk = p.N / h.L3 * p.K;
-    int G = p.K == 1 ? (resident + rowblk - 1) / rowblk : resident / rowblk;
+    int G = resident / rowblk;
     if (G > h.B) G = h.B;
     if (G < 1) G = 1;
     h.G3 = G;

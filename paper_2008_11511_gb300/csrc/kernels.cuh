@@ -626,6 +626,7 @@ struct KernelSet {
     int ls_lines;   // rows / columns per block of the line-search kernels
     int reg_lines;  // lines per block of the register kernels (0: none for this N)
     int reg_cols;   // columns per block of the register column passes
+    int (*row_bwd_per_sm)();  // resident row-backward blocks per SM (0: not known yet)
     int R, M;
     // column pass fed by tensor copies (K = 1; null where N has none) and its persistent grid
     void (*col_tma)(const void* tm_spec, const void* tm_io, const void* tm_mask, const ProbArgs&, int j0, int nb,
@@ -770,6 +771,29 @@ cudaError_t set_attrs_t() {
     return cudaSuccess;
 }
 
+// Resident row-backward blocks per SM from the occupancy calculator (cached
+// once known; 0 while it cannot be asked, e.g. before the kernel attributes
+// are set).
+template <int N>
+int row_bwd_per_sm() {
+    static int v = 0;
+    if (v == 0) {
+        int n = 0;
+        cudaError_t e;
+        if constexpr (has_reg<N>())
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_row_bwd_r<N>, kThreads, smem_row_bwd_r<N>());
+        else
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_row_bwd<N>, kThreads,
+                                                              smem_row_bwd_t<N>(1, max_lines<N>()));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        v = n;
+    }
+    return v;
+}
+
 template <int N>
 const KernelSet* make_kernel_set() {
     constexpr int rl = has_reg<N>() ? reg_lines<N>() : 0;
@@ -785,6 +809,7 @@ const KernelSet* make_kernel_set() {
                                  ls_lines<N>(),
                                  rl,
                                  rc,
+                                 &row_bwd_per_sm<N>,
                                  Plan<N>::R,
                                  Plan<N>::M,
                                  ColTma<N>::kOk ? &launch_col_tma<N> : nullptr,

@@ -433,6 +433,28 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_mod
     }
 }
 
+// Factor order of the row-backward transform.  For the large sizes the
+// 16-point factor goes second (N = R' M' with M' = 16), so that a thread's
+// pass-2 pixels (M' of them) keep the probe, its sums and the object rows in
+// registers and shared memory as for the smaller sizes.
+template <int N>
+struct BwdShape {
+    static constexpr bool kSwap = (N == 384 || N == 448 || N == 512);
+    static constexpr int R = kSwap ? Plan<N>::M : Plan<N>::R, M = kSwap ? Plan<N>::R : Plan<N>::M;
+    static constexpr int L = reg_lines<N>();
+    static constexpr int I1 = (L * M + kThreads - 1) / kThreads;
+    static constexpr int I2 = (L * R + kThreads - 1) / kThreads;
+    static constexpr bool kRegAcc = I2 * M <= 16;  // probe accumulators in registers, else shared memory
+    static_assert(R * (M + 1) <= reg_pitch<N>() && M * (R + 1) <= reg_pitch<N>(), "both layouts fit a line");
+};
+// w_N^(+a b) for a < BwdShape::R, b < BwdShape::M from the table tw[a * M + b] = w_N^(-a b) of Plan<N>
+template <int N>
+__device__ __forceinline__ float2 tw_bwd(const float2* tw, int a, int b) {
+    float2 t = BwdShape<N>::kSwap ? tw[b * Plan<N>::M + a] : tw[a * Plan<N>::M + b];
+    t.y = -t.y;
+    return t;
+}
+
 // ---------------------------------------------------------------------------
 // Row backward: inverse row FFT -> D; Psi' = Phi + D stored to the exit-wave
 // stack (AP and DM), probe numerator/denominator in registers across the
@@ -444,9 +466,9 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_mod
 template <int N>
 __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, int nb, int mode, int upd_obj,
                                                            int upd_probe) {
-    using S = RegShape<N>;
-    constexpr int R = S::R, M = S::M, L = S::L, P = S::P;
-    constexpr bool kRegAcc = S::I2 * M <= 16;  // probe accumulators in registers, else shared memory
+    using S = BwdShape<N>;
+    constexpr int R = S::R, M = S::M, L = S::L, P = reg_pitch<N>();
+    constexpr bool kRegAcc = S::kRegAcc;
     constexpr int IA = kRegAcc ? S::I2 : 1, MA = kRegAcc ? M : 1;
     extern __shared__ __align__(16) float2 sm[];
     float2* tw = sm;
@@ -540,7 +562,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
                 float2* o = buf + line * P + n1;
                 o[0] = v[0];
 #pragma unroll
-                for (int k2 = 1; k2 < R; ++k2) o[k2 * (M + 1)] = cmul(v[k2], tw_get<N, +1>(tw, k2, n1));
+                for (int k2 = 1; k2 < R; ++k2) o[k2 * (M + 1)] = cmul(v[k2], tw_bwd<N>(tw, k2, n1));
             }
         }
         __syncthreads();
@@ -833,9 +855,9 @@ size_t smem_col_r() {
 }
 template <int N>
 size_t smem_row_bwd_r() {
-    using S = RegShape<N>;
-    const bool reg_acc = S::I2 * S::M <= 16;
-    return sizeof(float2) * (N + (reg_acc ? 2 : 1) * (size_t)S::L * N + (size_t)S::L * S::P) +
+    using S = BwdShape<N>;
+    const bool reg_acc = S::kRegAcc;
+    return sizeof(float2) * (N + (reg_acc ? 2 : 1) * (size_t)S::L * N + (size_t)S::L * reg_pitch<N>()) +
            (reg_acc ? 0 : (size_t)S::L * N * (sizeof(float2) + sizeof(float)));
 }
 
