@@ -301,7 +301,7 @@ def run_ours(args):
 
     # end to end through the public API with host buffers: every step copies its
     # intensity stack in from pinned host memory and reads the cycle's LLK back.
-    # The copies run on a second stream one step ahead, into the other of two
+    # The copies run on their own streams one step ahead, into the other of two
     # device buffers; each buffer has its own handle, and both handles share the
     # object, the probe and the exit-wave stack.
     host_iobs = torch.from_numpy(s.iobs).pin_memory()
@@ -313,31 +313,39 @@ def run_ours(args):
     iobs2.copy_(iobs)
     pb2.dm(1, llk=llk_buf)  # graph capture outside the timed region
     handles, bufs = (pb, pb2), (iobs, iobs2)
-    copy_stream = torch.cuda.Stream(dev)
-    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    # the upload is split over several copy streams (contiguous frame ranges),
+    # so that more than one copy engine can serve it
+    n_copy = max(1, args.copy_streams)
+    bounds = [s.J * c // n_copy for c in range(n_copy + 1)]
+    copy_streams = [torch.cuda.Stream(dev) for _ in range(n_copy)]
+    copied = [[torch.cuda.Event() for _ in range(n_copy)] for _ in range(2)]
     used = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def upload(nb, wait_used):
+        for c, cs in enumerate(copy_streams):
+            with torch.cuda.stream(cs):
+                if wait_used:
+                    cs.wait_event(used[nb])
+                bufs[nb][bounds[c]:bounds[c + 1]].copy_(host_iobs[bounds[c]:bounds[c + 1]], non_blocking=True)
+                copied[nb][c].record(cs)
+
     e_steps = max(1, min(args.steps, 10))
     barrier(ws)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    with torch.cuda.stream(copy_stream):
-        bufs[0].copy_(host_iobs, non_blocking=True)
-        copied[0].record(copy_stream)
+    upload(0, False)
     for k in range(e_steps):
         b = k % 2
         if k + 1 < e_steps:
-            nb = 1 - b
-            with torch.cuda.stream(copy_stream):
-                if k >= 1:
-                    copy_stream.wait_event(used[nb])
-                bufs[nb].copy_(host_iobs, non_blocking=True)
-                copied[nb].record(copy_stream)
-        stream.wait_event(copied[b])
+            upload(1 - b, k >= 1)
+        for ev in copied[b]:
+            stream.wait_event(ev)
         l = handles[b].dm(1, llk=llk_buf)
         used[b].record(stream)
         host_llk.copy_(l[:1], non_blocking=True)
     stream.synchronize()
-    copy_stream.synchronize()
+    for cs in copy_streams:
+        cs.synchronize()
     el = time.perf_counter() - t0
     barrier(ws)
     el = max_over_ranks(el, ws)
@@ -395,7 +403,7 @@ def run_ours(args):
                 "clocks": clk, "gpu_launches": gpu_launches,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(s.iobs.nbytes),
                         "d2h_bytes_per_step": 8, "steps": e_steps,
-                        "copies": "pinned host -> device on a second stream, one step ahead, two buffers"},
+                        "copies": f"pinned host -> device on {n_copy} copy streams, one step ahead, two buffers"},
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     pb.close()
@@ -414,6 +422,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=0,
                     help="use only the first FRAMES frames of the workload (small cases for profiling)")
+    ap.add_argument("--copy-streams", type=int, default=1,
+                    help="streams the end-to-end leg splits each step's intensity upload over")
     ap.add_argument("--lanes", type=int, default=0,
                     help="batches in flight per cycle (library default when 0)")
     ap.add_argument("--tma", type=int, choices=(0, 1), default=None,

@@ -301,6 +301,55 @@ def test_multimode_dm_parity():
     pb.close()
 
 
+@pytest.mark.parametrize("N,K,J,algo", [
+    (256, 2, 150, "DM"),   # several batches of (frame, mode) blocks, ragged last batch
+    (384, 2, 10, "AP"),    # 16-column blocks, row backward with the 16-point factor second
+    (448, 3, 8, "DM"),
+    (160, 2, 20, "AP"),    # radix-5 factors
+    (64, 3, 40, "DM"),     # several lines per thread
+])
+def test_multimode_register_passes(N, K, J, algo):
+    """K Hermite-Gauss modes through the register-resident passes: one cycle
+    (DM from Psi = Phi) from the oracle's warm state, object, probe, exit waves
+    and LLK against the oracle."""
+    s = make_scan(f"mm{N}", N=N, J=J, Ho=N + 6 * int(N / 8) + 8, Wo=N + 6 * int(N / 8) + 2, K=K, seed=N + K,
+                  photons=1e6, step=N / 8, probe="hg", probe_radius=N / 10, mode_powers=[0.7, 0.2, 0.1][:K],
+                  mask_fraction=0.02)
+    data = data_of(s)
+    o0, p0, _ = oracle.ap_cycle(s.obj0, s.probe0, data)
+    o0, p0 = o0.astype(np.complex64), p0.astype(np.complex64)
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    if algo == "DM":
+        llk = pb.dm(1, init_psi=True).cpu().numpy()
+        o, p, psi, l = oracle.cycles("DM", o0, p0, data, 1)
+    else:
+        llk = pb.ap(1).cpu().numpy()
+        o, p, l = oracle.ap_cycle(o0, p0, data)
+        psi = None
+    _compare_cycle_state(s, pb, o, p, TOL1 * 2, psi_ref=psi)
+    np.testing.assert_allclose(llk, np.atleast_1d(l), rtol=TOL1 * 2)
+    pb.close()
+
+
+@pytest.mark.parametrize("N,K,J", [(64, 2, 24), (256, 2, 12)])
+def test_multimode_ml_grad_parity(N, K, J):
+    s = make_scan(f"mg{N}", N=N, J=J, Ho=N + 5 * int(N / 8) + 4, Wo=N + 5 * int(N / 8) + 4, K=K, seed=3 * N + K,
+                  photons=1e5, step=N / 8, probe="hg", probe_radius=N / 10, mode_powers=[0.8, 0.2],
+                  mask_fraction=0.02)
+    data = data_of(s)
+    o, p = s.obj0, s.probe0
+    for _ in range(3):
+        o, p, _ = oracle.ap_cycle(o, p, data)
+    o, p = o.astype(np.complex64), p.astype(np.complex64)
+    pb = gpu_problem(s, with_psi=False, obj=o, probe=p)
+    L, go, gp = pb.ml_grad()
+    ref_L, ref_go, ref_gp = oracle.ml_grad(o, p, data)
+    assert abs(float(L) - ref_L) / abs(ref_L) < TOL1
+    check_close("G_O", go.cpu().numpy(), ref_go, 1e-4)
+    check_close("G_P", gp.cpu().numpy(), ref_gp, 1e-4)
+    pb.close()
+
+
 def test_zero_extra_mode_equals_single_mode():
     s, o0, p0 = warm("ap64", J=30)
     p2 = np.concatenate([p0, np.zeros_like(p0)])
