@@ -243,6 +243,7 @@ template <int DIR> struct Dft<10, DIR> : DftComposite<5, 2, DIR> {};
 template <int DIR> struct Dft<14, DIR> : DftComposite<7, 2, DIR> {};
 template <int DIR> struct Dft<20, DIR> : DftComposite<5, 4, DIR> {};
 template <int DIR> struct Dft<28, DIR> : DftComposite<7, 4, DIR> {};
+template <int DIR> struct Dft<25, DIR> : DftComposite<5, 5, DIR> {};
 template <int DIR> struct Dft<8, DIR> : DftComposite<4, 2, DIR> {};
 template <int DIR> struct Dft<12, DIR> : DftComposite<4, 3, DIR> {};
 template <int DIR> struct Dft<16, DIR> : DftComposite<4, 4, DIR> {};
@@ -269,7 +270,7 @@ template <> struct Plan<512> { static constexpr int R = 16, M = 32; };
 template <> struct Plan<80>  { static constexpr int R = 10, M = 8;  };
 template <> struct Plan<160> { static constexpr int R = 16, M = 10; };
 template <> struct Plan<224> { static constexpr int R = 16, M = 14; };
-template <> struct Plan<400> { static constexpr int R = 20, M = 20; };
+template <> struct Plan<400> { static constexpr int R = 16, M = 25; };
 template <> struct Plan<448> { static constexpr int R = 16, M = 28; };
 
 // Line pitch (in complex elements) in shared memory: room for the padded

@@ -25,10 +25,10 @@ __host__ __device__ constexpr int reg_lines() {
     return N >= 384 ? 8 : ((N == 192 || N == 80 || N == 160 || N == 224) ? 16 : (4096 / N > N ? N : 4096 / N));
 }
 // Columns per block of the register column passes: 16 for the large sizes,
-// whose radix-16 first stage then gives every thread one pass-2 item.
+// whose 16-point first factor then gives every thread one pass-2 item.
 template <int N>
 __host__ __device__ constexpr int reg_cols() {
-    return (N == 384 || N == 448 || N == 512) ? 16 : reg_lines<N>();
+    return (N == 384 || N == 400 || N == 448 || N == 512) ? 16 : reg_lines<N>();
 }
 // Shared-memory pitch of a line: room for both padded intermediate layouts
 // (R (M+1) and M (R+1) elements), odd.
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_mod
 // registers and shared memory as for the smaller sizes.
 template <int N>
 struct BwdShape {
-    static constexpr bool kSwap = (N == 384 || N == 448 || N == 512);
+    static constexpr bool kSwap = (N == 384 || N == 400 || N == 448 || N == 512);
     static constexpr int R = kSwap ? Plan<N>::M : Plan<N>::R, M = kSwap ? Plan<N>::R : Plan<N>::M;
     static constexpr int L = reg_lines<N>();
     static constexpr int I1 = (L * M + kThreads - 1) / kThreads;
