@@ -331,7 +331,7 @@ size_t layout_problem(ProbHost& h) {
     h.lay.ls_part = o;
     o = align_up(o + 2 * sizeof(double) * (size_t)p.J * (p.N / ls_cols(h.ks, p.K)));
     h.lay.cg = o;
-    o = align_up(o + 8 * sizeof(double));
+    o = align_up(o + (8 + 3 * (size_t)kCgBlocks) * sizeof(double));  // scalars, then the dot-product partials
     h.lay.mbits = o;
     if (use_reg_kernels(h.ks, p.K)) o = align_up(o + sizeof(uint32_t) * (size_t)(p.N / h.ks->reg_cols) * kThreads);
     h.lay.nf_t = o;
@@ -1020,6 +1020,7 @@ CgArgs cg_args(ptx_handle* h, ProbHost& ph) {
     c.n_obj = no;
     c.n_probe = npr;
     c.cg = (double*)(h->scratch + ph.lay.cg);
+    c.cg_part = c.cg + 8;
     return c;
 }
 
@@ -1103,7 +1104,7 @@ ptx_status ptx_ml_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, double*
         if (e == cudaSuccess) e = cudaMemsetAsync(c.gp_probe, 0, 2 * sizeof(float2) * c.n_probe, s);
         if (e != cudaSuccess) return cuda_fail(e, "ML restart memset");
     }
-    const int nblk = 4 * 152;
+    const int nblk = kCgBlocks;
     for (int cyc = 0; cyc < ncycles; ++cyc) {
         // gradient (zero where a part is not updated) and the LLK before the step
         if (!uo && (e = cudaMemsetAsync(c.g_obj, 0, sizeof(float2) * c.n_obj, s)) != cudaSuccess)
@@ -1115,6 +1116,7 @@ ptx_status ptx_ml_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, double*
             return st;
         if ((e = cudaMemsetAsync(c.cg, 0, 8 * sizeof(double), s)) != cudaSuccess) return cuda_fail(e, "memset");
         k_cg_dots<<<nblk, 256, 0, s>>>(c);
+        k_cg_reduce<<<1, 256, 0, s>>>(c);
         k_cg_direction<<<nblk, 256, 0, s>>>(c);
         if ((st = enqueue_line_coeffs(h, ph, uo ? c.d_obj : nullptr, up ? c.d_probe : nullptr, c.cg + 3, s)) != PTX_OK)
             return st;

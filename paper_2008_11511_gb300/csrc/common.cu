@@ -219,8 +219,9 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-// <G,G>, <G,Gp>, <Gp,Gp> over the object and probe parts (FP64 partials, one
-// atomic per warp; cg[0..2] must be zero on entry).
+// <G,G>, <G,Gp>, <Gp,Gp> over the object and probe parts: FP64 sums per block
+// into cg_part[block][0..2] (k_cg_reduce adds the blocks in index order, so the
+// result does not depend on scheduling).  kCgBlocks blocks of 256 threads.
 __global__ void k_cg_dots(CgArgs c) {
     double gg = 0.0, ggp = 0.0, gpgp = 0.0;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -234,13 +235,29 @@ __global__ void k_cg_dots(CgArgs c) {
         ggp += (double)g.x * q.x + (double)g.y * q.y;
         gpgp += (double)q.x * q.x + (double)q.y * q.y;
     }
-    gg = warp_sum_d(gg);
-    ggp = warp_sum_d(ggp);
-    gpgp = warp_sum_d(gpgp);
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(c.cg + 0, gg);
-        atomicAdd(c.cg + 1, ggp);
-        atomicAdd(c.cg + 2, gpgp);
+    __shared__ double red_s[256 / 32];
+    const double t0 = block_sum_double<256>(gg, red_s);
+    __syncthreads();
+    const double t1 = block_sum_double<256>(ggp, red_s);
+    __syncthreads();
+    const double t2 = block_sum_double<256>(gpgp, red_s);
+    if (threadIdx.x == 0) {
+        c.cg_part[3 * blockIdx.x + 0] = t0;
+        c.cg_part[3 * blockIdx.x + 1] = t1;
+        c.cg_part[3 * blockIdx.x + 2] = t2;
+    }
+}
+
+// cg[0..2] = sums of the kCgBlocks partials of k_cg_dots, in a fixed order.
+// One block of 256 threads.
+__global__ void k_cg_reduce(CgArgs c) {
+    __shared__ double red_s[256 / 32];
+    for (int q = 0; q < 3; ++q) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < kCgBlocks; b += 256) v += c.cg_part[3 * b + q];
+        const double t = block_sum_double<256>(v, red_s);
+        if (threadIdx.x == 0) c.cg[q] = t;
+        __syncthreads();
     }
 }
 

@@ -558,6 +558,8 @@ __global__ void k_set_ctl(Ctl* ctl, double* llk_out, int nprob);
 
 // ML conjugate-gradient vector steps.  cg[0..2] receive <G,G>, <G,Gp>, <Gp,Gp>
 // (Re sum conj(a) b over object and probe), cg[3..4] the line-search L'(0), L''(0).
+constexpr int kCgBlocks = 4 * 152;  // blocks of the CG vector kernels
+
 struct CgArgs {
     float2* g_obj;
     float2* g_probe;
@@ -567,8 +569,10 @@ struct CgArgs {
     float2* d_probe;
     size_t n_obj, n_probe;
     double* cg;       // [8] device scalars
+    double* cg_part;  // [kCgBlocks][3] per-block partial dot products
 };
 __global__ void k_cg_dots(CgArgs c);
+__global__ void k_cg_reduce(CgArgs c);
 __global__ void k_cg_direction(CgArgs c);
 __global__ void k_cg_step(CgArgs c, float2* obj, float2* probe);
 __global__ void k_ls_reduce(const double* part, size_t nparts, double* out);
