@@ -301,6 +301,19 @@ def test_multimode_dm_parity():
     pb.close()
 
 
+def test_multimode_dm_trajectory():
+    """Six DM cycles of three modes at 512^2 from the oracle's warm state: the
+    per-cycle LLK (of the reflected wave, which grows under DM here as it does
+    in the oracle) and the final object and probe against the oracle."""
+    s, o0, p0 = warm("modes512", J=40, Ho=1100, Wo=1100)
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    llk = pb.dm(6, init_psi=True).cpu().numpy()
+    o, p, psi, llk_ref = oracle.cycles("DM", o0, p0, data_of(s), 6)
+    np.testing.assert_allclose(llk, llk_ref, rtol=1e-5)
+    _compare_cycle_state(s, pb, o, p, 1e-5, psi_ref=psi)
+    pb.close()
+
+
 @pytest.mark.parametrize("N,K,J,algo", [
     (256, 2, 150, "DM"),   # several batches of (frame, mode) blocks, ragged last batch
     (384, 2, 10, "AP"),    # 16-column blocks, row backward with the 16-point factor second
