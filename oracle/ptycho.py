@@ -19,7 +19,7 @@ exit waves Psi_jk.  ``FT`` is the orthonormal 2D DFT over the last two axes,
 arrays in FFT order (zero frequency at [0, 0]).  A position (row, col) is the
 top-left corner of the frame's object patch.
 
-Readings of points the paper leaves open (each is listed in the design doc):
+Readings of points the paper leaves open:
 * FT normalisation: orthonormal, so IFT = FT^H and Parseval holds exactly.
 * ObjProbe2Psi: Phi_jk(x) = P_k(x) O(r_j + x) (the paper writes
   Psi_j(r) = O(r) P(r - r_j); with integer top-left positions this is the same
