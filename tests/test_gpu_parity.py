@@ -674,6 +674,36 @@ def test_full_size_dm256_cycle_in_bench_configuration():
 
 
 
+def test_full_size_modes512_cycle_sampled_frames():
+    """The three-mode workload at full size — 10000 frames of 512x512, three
+    modes, 6000x6000 object (Psi 62.9 GB on the device) — one DM cycle from
+    Psi = Phi at the true object and probe (well conditioned: the model's far
+    field carries the data's spectrum).  Every frame's new exit waves depend
+    only on that frame, so the oracle computes a sample of 12 frames one by one."""
+    s = make_config("modes512")
+    o_t, p_t = s.obj_true.astype(np.complex64), s.probe_true.astype(np.complex64)
+    pb = gpu_problem(s, with_psi=True, obj=o_t, probe=p_t)
+    pb.dm(1, init_psi=True)
+    for j in np.linspace(0, s.J - 1, 12).astype(int):
+        ref, _ = oracle.dm_frame_update(o_t, p_t, None, s.iobs[j], s.positions[j], s.mask, init_psi=True)
+        check_close(f"Psi' of frame {j}", pb.psi[j].cpu().numpy(), ref, TOL1)
+    pb.close()
+
+
+def test_full_size_ml256_gradient():
+    """The ML workload at full size — 1000 frames of 256x256, 1536x1536 object —
+    the LLK and its gradient at the true object and probe against the oracle."""
+    s = make_config("ml256")
+    o_t, p_t = s.obj_true.astype(np.complex64), s.probe_true.astype(np.complex64)
+    pb = gpu_problem(s, with_psi=False, obj=o_t, probe=p_t)
+    L, go, gp = pb.ml_grad()
+    ref_L, ref_go, ref_gp = oracle.ml_grad(o_t, p_t, data_of(s))
+    assert abs(float(L) - ref_L) / abs(ref_L) < TOL1
+    check_close("G_O", go.cpu().numpy(), ref_go, 1e-4)
+    check_close("G_P", gp.cpu().numpy(), ref_gp, 1e-4)
+    pb.close()
+
+
 # ------------------------------------------------------------------ ML conjugate gradient
 
 def _oracle_direction(s, obj, probe, which):
