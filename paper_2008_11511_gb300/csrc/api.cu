@@ -146,6 +146,7 @@ struct ProbHost {
     // object tiles met by at least one frame, with their frames (CSR, ascending j)
     std::vector<int> tile_ids, tile_ptr, tile_frames;
     int ntx = 0;
+    int tile_h = 0;  // object tile height of the gather (0: not chosen yet)
     Layout lay{};
     ProbArgs args{};
     TileLists tiles{};
@@ -159,10 +160,31 @@ struct ProbHost {
     bool tma_gather = false;
 };
 
-// Per-tile frame lists of the object gather (host, from the positions).
+// Tiles of TW x TH object pixels met by at least one frame.
+size_t active_tiles(const ptx_problem& p, const int32_t* positions, int TW, int TH) {
+    const int ntx = (p.Wo + TW - 1) / TW, nty = (p.Ho + TH - 1) / TH;
+    std::vector<char> hit((size_t)ntx * nty, 0);
+    for (int j = 0; j < p.J; ++j) {
+        const int r = positions[2 * j], c = positions[2 * j + 1];
+        for (int ty = r / TH; ty <= (r + p.N - 1) / TH; ++ty)
+            for (int tx = c / TW; tx <= (c + p.N - 1) / TW; ++tx) hit[(size_t)ty * ntx + tx] = 1;
+    }
+    size_t n = 0;
+    for (char v : hit) n += v;
+    return n;
+}
+
+// Per-tile frame lists of the object gather (host, from the positions).  The
+// tile height is chosen once, at the first build: the full kObjTileH, or half
+// or a quarter of it while the object has fewer tiles than two blocks per SM
+// (a small object would otherwise leave most SMs idle).
 void build_tiles(ProbHost& h, const int32_t* positions) {
     const ptx_problem& p = h.p;
-    const int TW = kObjTileW, TH = kObjTileH;
+    if (h.tile_h == 0) {
+        h.tile_h = kObjTileH;
+        while (h.tile_h > kObjTileH / 4 && active_tiles(p, positions, kObjTileW, h.tile_h) < 2 * 152) h.tile_h /= 2;
+    }
+    const int TW = kObjTileW, TH = h.tile_h;
     const int ntx = (p.Wo + TW - 1) / TW, nty = (p.Ho + TH - 1) / TH;
     std::vector<int> count((size_t)ntx * nty, 0);
     auto span = [&](int j, int& ty0, int& ty1, int& tx0, int& tx1) {
@@ -313,8 +335,9 @@ size_t layout_problem(ProbHost& h) {
     o = align_up(o + 2 * sizeof(unsigned));
     // tile lists sized for any positions (ptx_set_positions rewrites them in place):
     // every object tile, and per frame the tiles an N x N patch can meet
-    const size_t ntiles_max = (size_t)((p.Wo + kObjTileW - 1) / kObjTileW) * ((p.Ho + kObjTileH - 1) / kObjTileH);
-    const size_t per_frame = (size_t)((p.N + kObjTileH - 1) / kObjTileH + 1) * ((p.N + kObjTileW - 1) / kObjTileW + 1);
+    const int th = h.tile_h > 0 ? h.tile_h : kObjTileH / 4;
+    const size_t ntiles_max = (size_t)((p.Wo + kObjTileW - 1) / kObjTileW) * ((p.Ho + th - 1) / th);
+    const size_t per_frame = (size_t)((p.N + th - 1) / th + 1) * ((p.N + kObjTileW - 1) / kObjTileW + 1);
     h.lay.tile_ids = o;
     o = align_up(o + sizeof(int) * std::max(h.tile_ids.size(), ntiles_max));
     h.lay.tile_ptr = o;
@@ -533,6 +556,7 @@ void fill_args(ptx_handle* h, ProbHost& ph) {
     ph.tiles.tile_ptr = (const int*)(h->scratch + ph.lay.tile_ptr);
     ph.tiles.tile_frames = (const int*)(h->scratch + ph.lay.tile_frames);
     ph.tiles.ntx = ph.ntx;
+    ph.tiles.th = ph.tile_h;
 }
 
 // Second half of Psi2ObjProbe, in stages: probe normalisation from its
@@ -872,9 +896,10 @@ ptx_status ptx_create(ptx_handle** out, const ptx_problem* probs, int32_t nprob,
     for (ProbHost& ph : h->probs) {
         const KernelSet* ks = kernel_set(ph.p.N);
         const uint32_t C = (uint32_t)ks->reg_lines, N = (uint32_t)ph.p.N;
+        const uint32_t th = (uint32_t)ph.tile_h;
         ph.tma_gather = ph.p.psi && N >= 64 && kObjTileW == 32 &&
-                        encode_3d(&ph.tm_psi3, ph.p.psi, N, N, (uint64_t)ph.p.J * ph.p.K, 34, 32) &&
-                        encode_3d(&ph.tm_probe3, ph.p.probe, N, N, (uint64_t)ph.p.K, 34, 32);
+                        encode_3d(&ph.tm_psi3, ph.p.psi, N, N, (uint64_t)ph.p.J * ph.p.K, 34, th) &&
+                        encode_3d(&ph.tm_probe3, ph.p.probe, N, N, (uint64_t)ph.p.K, 34, th);
         ph.tma_io = ph.p.K == 1 && ks->col_tma && ks->col_tma_grid() > 0 &&
                     encode_2d(&ph.tm_io, 4, ph.p.iobs, N, (uint64_t)ph.p.J * N, C, N) &&
                     encode_2d(&ph.tm_mask, 1, h->scratch + ph.lay.mask, N, N, C, N);

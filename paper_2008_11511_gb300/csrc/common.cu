@@ -20,7 +20,8 @@ __device__ __forceinline__ float warp_max(float v) {
 __global__ void __launch_bounds__(256) k_obj_gather(ProbArgs a, TileLists tl, int fuse_max) {
     constexpr int TW = kObjTileW, TH = kObjTileH;
     constexpr int RS = 256 / TW;          // rows covered by the block's threads at once
-    constexpr int Q = TW * TH / 256;      // pixels per thread: rows wy + RS q of column x
+    constexpr int Q = TW * TH / 256;      // pixels per thread (at most): rows wy + RS q of column x
+    const int Qr = TW * tl.th / 256;      // this tile height's
     const int t = blockIdx.x;
     const int tid = tl.tile_ids[t];
     const int ty = tid / tl.ntx, tx = tid - ty * tl.ntx;
@@ -35,7 +36,7 @@ __global__ void __launch_bounds__(256) k_obj_gather(ProbArgs a, TileLists tl, in
         d[q] = 0.f;
     }
     const int f0 = tl.tile_ptr[t], f1 = tl.tile_ptr[t + 1];
-    const int y0 = ty * TH + wy;
+    const int y0 = ty * tl.th + wy;
     // F frames per step: all their loads are issued before any is used, so each
     // thread keeps up to 2 F Q loads in flight (the loop is latency-bound otherwise)
     constexpr int F = 4;
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(256) k_obj_gather(ProbArgs a, TileLists tl, in
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
                     const int py = y0 + RS * q - p.x;
-                    ok[u][q] = fi < f1 && px >= 0 && px < N && py >= 0 && py < N;
+                    ok[u][q] = q < Qr && fi < f1 && px >= 0 && px < N && py >= 0 && py < N;
                     const size_t off = ok[u][q] ? ((size_t)k * N + py) * N + px : 0;
                     pr[u][q] = ok[u][q] ? __ldg(a.probe + off) : make_float2(0.f, 0.f);
                     ps[u][q] = ok[u][q] ? __ldcs(a.psi + (size_t)j * K * N * N + off) : make_float2(0.f, 0.f);
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(256) k_obj_gather(ProbArgs a, TileLists tl, in
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int y = y0 + RS * q;
-            if (y < a.Ho) {
+            if (q < Qr && y < a.Ho) {
                 a.acc_obj[(size_t)y * a.Wo + x] = make_float4(n[q].x, n[q].y, d[q], 0.f);
                 dmax = fmaxf(dmax, d[q]);
             }

@@ -1,6 +1,7 @@
-// Object numerator and denominator gathered per 32 x 32 object tile, fed by
-// 3D tensor copies.  For each (frame j, mode k) meeting the tile, the window
-// of Psi'_jk and of P_k under the tile is one box of 32 rows x 34 columns
+// Object numerator and denominator gathered per 32-column object tile (32, 16
+// or 8 rows), fed by 3D tensor copies.  For each (frame j, mode k) meeting the
+// tile, the window of Psi'_jk and of P_k under the tile is one box of the
+// tile's rows x 34 columns
 // (two extra columns so that the box starts on a 16-byte boundary) copied by
 // the tensor memory accelerator into a ring of shared-memory stages; the parts
 // of the window outside the frame arrive as zeros and add nothing.  One
@@ -16,12 +17,13 @@ namespace ptx {
 
 namespace {
 
-constexpr int kT = 32;             // tile side (kObjTileW == kObjTileH == 32)
+constexpr int kT = 32;             // tile width (kObjTileW == 32)
 constexpr int kBoxW = kT + 2;      // 34 columns: 272 bytes per box row
 constexpr int kStages = 4;
 constexpr int kConsumers = 8;      // warps
-constexpr size_t kBox = sizeof(float2) * kBoxW * kT;  // 8704 bytes
-constexpr uint32_t kTx = 2 * (uint32_t)kBox;
+// one box: kRows rows of the tile (32, 16 or 8)
+template <int kRows>
+__host__ __device__ constexpr size_t box_bytes() { return sizeof(float2) * kBoxW * kRows; }
 
 __device__ __forceinline__ uint32_t s_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -65,21 +67,26 @@ __device__ __forceinline__ void flag_error(int* flag) {
     }
 }
 
-// Box origin of frame position p for tile (ty, tx): column rounded down to even.
-__device__ __forceinline__ void box_origin(int2 p, int ty, int tx, int& xs, int& ys, int& off) {
+// Box origin of frame position p for the tile whose first row is y0 and whose
+// column index is tx: column rounded down to even.
+__device__ __forceinline__ void box_origin(int2 p, int y0, int tx, int& xs, int& ys, int& off) {
     const int xr = tx * kT - p.y;
     off = xr & 1;
     xs = xr - off;
-    ys = ty * kT - p.x;
+    ys = y0 - p.x;
 }
 
 }  // namespace
 
+template <int kRows>
 __global__ void __launch_bounds__(32 * (kConsumers + 1), 2)
     k_obj_gather_t(const __grid_constant__ CUtensorMap tm_psi, const __grid_constant__ CUtensorMap tm_probe, ProbArgs a,
                    TileLists tl, int fuse_max) {
+    constexpr size_t kBox = box_bytes<kRows>();
+    constexpr uint32_t kTx = 2 * (uint32_t)kBox;
+    constexpr int kQ = kRows / kConsumers;  // rows per consumer warp
     extern __shared__ __align__(128) unsigned char gsm[];
-    float2(*st)[2][kT * kBoxW] = reinterpret_cast<float2(*)[2][kT * kBoxW]>(gsm);
+    float2(*st)[2][kRows * kBoxW] = reinterpret_cast<float2(*)[2][kRows * kBoxW]>(gsm);
     uint64_t* full = reinterpret_cast<uint64_t*>(gsm + kStages * 2 * kBox);
     uint64_t* empty = full + kStages;
     const int t = blockIdx.x;
@@ -109,7 +116,7 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 2)
                 const int f = f0 + it / K, k = it - (it / K) * K;
                 const int j = tl.tile_frames[f];
                 int xs, ys, off;
-                box_origin(a.pos[j], ty, tx, xs, ys, off);
+                box_origin(a.pos[j], ty * kRows, tx, xs, ys, off);
                 const uint32_t bar = s_u32(&full[s]);
                 bar_expect_tx(bar, kTx);
                 load_3d(s_u32(st[s][0]), &tm_psi, xs, ys, j * K + k, bar);
@@ -126,10 +133,10 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 2)
     }
 
     // consumers: lane = tile column, rows warp + 8 q
-    float2 n[4];
-    float d[4];
+    float2 n[kQ];
+    float d[kQ];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kQ; ++q) {
         n[q] = make_float2(0.f, 0.f);
         d[q] = 0.f;
     }
@@ -138,7 +145,7 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 2)
         const int s = it % kStages;
         const int f = f0 + it / K;
         int xs, ys, off;
-        box_origin(a.pos[tl.tile_frames[f]], ty, tx, xs, ys, off);
+        box_origin(a.pos[tl.tile_frames[f]], ty * kRows, tx, xs, ys, off);
         if (!bar_wait(s_u32(&full[s]), (it / kStages) & 1)) {
             ok = false;
             break;
@@ -146,7 +153,7 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 2)
         const float2* ps = st[s][0] + off + lane;
         const float2* pr = st[s][1] + off + lane;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < kQ; ++q) {
             const int r = (warp + 8 * q) * kBoxW;
             const float2 pv = pr[r], sv = ps[r];
             const float2 c = cconjmul(pv, sv);
@@ -162,8 +169,8 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 2)
     float dmax = 0.f;
     if (x < a.Wo) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int y = ty * kT + warp + 8 * q;
+        for (int q = 0; q < kQ; ++q) {
+            const int y = ty * kRows + warp + 8 * q;
             if (y < a.Ho) {
                 a.acc_obj[(size_t)y * a.Wo + x] = make_float4(n[q].x, n[q].y, d[q], 0.f);
                 dmax = fmaxf(dmax, d[q]);
@@ -177,16 +184,31 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 2)
     }
 }
 
-constexpr size_t kGatherSmem = kStages * 2 * kBox + 2 * kStages * sizeof(uint64_t);
+template <int kRows>
+constexpr size_t gather_smem() { return kStages * 2 * box_bytes<kRows>() + 2 * kStages * sizeof(uint64_t); }
 
 cudaError_t set_attrs_gather_tma() {
-    return cudaFuncSetAttribute(k_obj_gather_t, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGatherSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_obj_gather_t<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gather_smem<32>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_obj_gather_t<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gather_smem<16>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_obj_gather_t<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gather_smem<8>());
+    return e;
 }
 
+// tl.th selects the instantiation; the tensor maps' boxes are 34 x tl.th
 void launch_obj_gather_tma(const void* tm_psi, const void* tm_probe, const ProbArgs& a, const TileLists& tl,
                            int ntiles, int fuse_max, cudaStream_t s) {
-    k_obj_gather_t<<<ntiles, 32 * (kConsumers + 1), kGatherSmem, s>>>(
-        *(const CUtensorMap*)tm_psi, *(const CUtensorMap*)tm_probe, a, tl, fuse_max);
+    const CUtensorMap& mp = *(const CUtensorMap*)tm_psi;
+    const CUtensorMap& mq = *(const CUtensorMap*)tm_probe;
+    constexpr int kTh = 32 * (kConsumers + 1);
+    if (tl.th == 8)
+        k_obj_gather_t<8><<<ntiles, kTh, gather_smem<8>(), s>>>(mp, mq, a, tl, fuse_max);
+    else if (tl.th == 16)
+        k_obj_gather_t<16><<<ntiles, kTh, gather_smem<16>(), s>>>(mp, mq, a, tl, fuse_max);
+    else
+        k_obj_gather_t<32><<<ntiles, kTh, gather_smem<32>(), s>>>(mp, mq, a, tl, fuse_max);
 }
 
 }  // namespace ptx

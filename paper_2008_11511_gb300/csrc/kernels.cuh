@@ -522,9 +522,11 @@ __global__ void __launch_bounds__(kThreads) k_col_ls(ProbArgs a, int j0, int C) 
 // ---------------------------------------------------------------------------
 // Normalisation (Psi2ObjProbe second half) and reductions.
 // ---------------------------------------------------------------------------
-// Object tiles of the gather: kObjTileW x kObjTileH pixels, one block each.
-// Wide tiles make every frame's share of a tile a few long row segments
-// (kObjTileW * 8 bytes each), which HBM serves more efficiently than short ones.
+// Object tiles of the gather: kObjTileW x th pixels, one block each, th =
+// kObjTileH, or a half or a quarter of it for objects with few tiles (more
+// blocks).  Wide tiles make every frame's share of a tile a few long row
+// segments (kObjTileW * 8 bytes each), which HBM serves more efficiently than
+// short ones.
 #ifndef PTX_OBJ_TILE_W
 #define PTX_OBJ_TILE_W 32
 #endif
@@ -536,6 +538,7 @@ struct TileLists {
     const int* tile_ptr;     // [ntiles + 1] CSR offsets into tile_frames
     const int* tile_frames;  // frames j whose patch meets the tile, ascending
     int ntx;                 // tiles per object row
+    int th;                  // tile height (kObjTileH, kObjTileH / 2 or kObjTileH / 4)
 };
 __global__ void k_obj_gather(ProbArgs a, TileLists tl, int fuse_max);
 // Column pass with the 16-point DFT stages on the tensor cores (tcgen05, TF32
