@@ -299,6 +299,19 @@ ptx_status ptx_llk_static(int32_t N, int32_t K, int32_t J, int32_t Ho, int32_t W
                           const void* probe, const int32_t* positions, const float* iobs, const uint8_t* mask,
                           double* llk_dev, void* stream);
 
+/* Self-test of the failure path of the bounded device waits (no GPU fault is
+ * involved): enqueues one kernel whose single waiting thread waits for a flag
+ * that nothing sets, for at most limit_us microseconds of the GPU's global
+ * timer (1..1000000), and then records the give-up in the handle's device
+ * error flag exactly as a cycle's tensor-copy wait that gives up does.  The
+ * next ptx_ap_cycles / ptx_dm_cycles / ptx_cycles call on the handle, made
+ * after the stream has passed the kernel, returns PTX_ERR_TIMEOUT once and
+ * enqueues nothing; later calls work as before.  Returns PTX_OK when the
+ * kernel is enqueued; PTX_ERR_INVALID_ARG for a null handle or a limit out of
+ * range, PTX_ERR_NOT_READY when the handle has no error flag (mapped host
+ * memory was unavailable at create). */
+ptx_status ptx_wait_selftest(ptx_handle* h, int32_t limit_us, void* stream);
+
 /* Text of the last failure on the calling thread ("" if none). */
 const char* ptx_last_error(void);
 

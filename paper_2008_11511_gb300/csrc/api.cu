@@ -1306,6 +1306,18 @@ ptx_status ptx_set_positions(ptx_handle* h, int32_t p, const int32_t* positions,
 
 const char* ptx_last_error(void) { return g_last_error.c_str(); }
 
+ptx_status ptx_wait_selftest(ptx_handle* h, int32_t limit_us, void* stream) {
+    if (!h) return fail(PTX_ERR_INVALID_ARG, "null handle");
+    if (limit_us < 1 || limit_us > 1000000) return fail(PTX_ERR_INVALID_ARG, "limit_us=%d must be in 1..1000000", limit_us);
+    ptx_status st = check_device(h);
+    if (st != PTX_OK) return st;
+    if (!h->err_dev) return fail(PTX_ERR_NOT_READY, "the handle has no device error flag");
+    k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>(h->err_dev, 1000ull * (unsigned long long)limit_us);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "self-test launch");
+    return PTX_OK;
+}
+
 void ptx_destroy(ptx_handle* h) {
     if (!h) return;
     drop_graphs(h);

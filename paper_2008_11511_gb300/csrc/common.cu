@@ -202,6 +202,29 @@ __global__ void k_bg_update(float* bg, float* acc, const uint8_t* mask, int n, f
     }
 }
 
+// Self-test of the bounded-wait failure path: one thread waits for a
+// shared-memory flag that nothing sets, at most limit_ns of the global timer
+// (and at most 2^31 SM clocks), then records the give-up in err_flag as the
+// tensor-copy waits do.  The wait always ends.
+__global__ void k_wait_selftest(int* err_flag, unsigned long long limit_ns) {
+    __shared__ volatile int never;
+    never = 0;
+    __syncthreads();
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    const long long c0 = clock64();
+    while (!never) {
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > limit_ns || clock64() - c0 > (1ll << 31)) {
+            if (err_flag) {
+                *(volatile int*)err_flag = 1;
+                __threadfence_system();
+            }
+            return;
+        }
+    }
+}
+
 __global__ void k_set_ctl(Ctl* ctl, double* llk_out, int nprob) {
     ctl->llk_out = llk_out;
     ctl->cycle = 0;

@@ -574,6 +574,7 @@ struct CgArgs {
     double* cg;       // [8] device scalars
     double* cg_part;  // [kCgBlocks][3] per-block partial dot products
 };
+__global__ void k_wait_selftest(int* err_flag, unsigned long long limit_ns);
 __global__ void k_cg_dots(CgArgs c);
 __global__ void k_cg_reduce(CgArgs c);
 __global__ void k_cg_direction(CgArgs c);

@@ -1,0 +1,74 @@
+"""Failure detection without a GPU fault.
+
+The library's device-side waits (tensor-copy arrivals in the object gather and
+the column pass) are bounded: a wait that runs out records the fact in the
+handle's error flag (mapped host memory) and the kernel returns, so the
+context stays usable, and the next cycle call reports PTX_ERR_TIMEOUT once.
+Here the wait that runs out is ptx_wait_selftest's, on a flag that nothing
+sets; no GPU fault, trap or hang is involved.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from synthetic import make_config
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2008_11511_gb300 import build as b
+    b.build()
+
+
+def _dev(x):
+    return torch.tensor(np.ascontiguousarray(x), device="cuda")
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((np.asarray(a) - b).ravel()) / np.linalg.norm(np.asarray(b).ravel()))
+
+
+def test_wait_timeout_is_reported_once_and_the_handle_stays_usable():
+    from paper_2008_11511_gb300 import Ptycho, _lib
+    from paper_2008_11511_gb300._lib import PtychoError
+    s = make_config("ap64", J=30)
+    data = oracle.Data.make(s.iobs, s.positions, s.mask)
+    o0, p0, _ = oracle.ap_cycle(s.obj0, s.probe0, data)
+    o0, p0 = o0.astype(np.complex64), p0.astype(np.complex64)
+    pb = Ptycho(_dev(o0), _dev(p0), _dev(s.iobs), s.positions, s.mask)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _lib.call("ptx_wait_selftest", pb._handle(), 2000, stream)  # gives up after 2 ms
+    torch.cuda.synchronize()
+    with pytest.raises(PtychoError) as ei:
+        pb.ap(1)
+    assert ei.value.status_name == "PTX_ERR_TIMEOUT"
+    assert "bounded device wait" in str(ei.value)
+    # reported once; the refused call enqueued nothing, so the next cycle starts from (o0, p0)
+    llk = pb.ap(1).cpu().numpy()
+    o, p, l = oracle.ap_cycle(o0, p0, data)
+    assert _rel(pb.probe.cpu().numpy(), p) < 1e-5
+    d = oracle.object_denominator(p, s.positions, o.shape)
+    ill = d > 1e-3 * d.max()
+    assert _rel(pb.obj.cpu().numpy()[ill], o[ill]) < 1e-5
+    assert abs(llk[0] - l) < 1e-5 * abs(l)
+    pb.close()
+
+
+def test_wait_selftest_rejects_limits_out_of_range():
+    from paper_2008_11511_gb300 import Ptycho, _lib
+    from paper_2008_11511_gb300._lib import PtychoError
+    s = make_config("ap64", J=10)
+    pb = Ptycho(_dev(s.obj0), _dev(s.probe0), _dev(s.iobs), s.positions, s.mask)
+    for bad in (0, -5, 1000001):
+        with pytest.raises(PtychoError) as ei:
+            _lib.call("ptx_wait_selftest", pb._handle(), bad, None)
+        assert ei.value.status_name == "PTX_ERR_INVALID_ARG"
+    pb.ap(1)  # nothing was enqueued; the handle works
+    pb.close()
