@@ -63,6 +63,40 @@ def test_batched_cycles_match_oracle_per_problem():
     pb.close()
 
 
+def test_full_size_batched_workload_sampled():
+    """The 16-scan batched workload at full size (22 245 frames, N from 128 to
+    512, AP and DM alternately) through one handle, one cycle from the true
+    objects and probes (DM from Psi = Phi): for each DM scan the new exit waves
+    of four frames spread over the scan, for each AP scan of up to 1000 frames
+    the cycle's LLK (the exact LLK at the truth), against the oracle."""
+    from paper_2008_11511_gb300 import PtychoBatch
+    from synthetic import batched_problem_specs
+    specs = batched_problem_specs()
+    scans = [make_scan(sp["name"], N=sp["N"], J=sp["J"], Ho=sp["Ho"], Wo=sp["Wo"], K=1, seed=sp["seed"],
+                       photons=sp["photons"], step=sp["step"], probe_radius=sp["probe_radius"], mask_fraction=0.0)
+             for sp in specs]
+    algos = [sp["algorithm"] for sp in specs]
+    truth = [(s.obj_true.astype(np.complex64), s.probe_true.astype(np.complex64)) for s in scans]
+    items = [dict(obj=dev(o), probe=dev(p), iobs=dev(s.iobs), positions=s.positions, mask=s.mask)
+             for s, (o, p) in zip(scans, truth)]
+    pb = PtychoBatch(items)
+    llk = pb.cycles(1, algos, init_psi=True).cpu().numpy()
+    checked = 0
+    for i, (s, (o, p), a) in enumerate(zip(scans, truth, algos)):
+        if a == "DM":
+            for j in np.linspace(0, s.J - 1, 4).astype(int):
+                ref, _ = oracle.dm_frame_update(o, p, None, s.iobs[j], s.positions[j], s.mask, init_psi=True)
+                assert rel(pb.items[i]["psi"][j].cpu().numpy(), ref) < TOL1, (i, j)
+                checked += 1
+        elif s.J <= 1000:
+            data = oracle.Data.make(s.iobs, s.positions, s.mask)
+            ref = oracle.frames_llk(o, p, data, np.arange(s.J))
+            assert abs(llk[0, i] - ref) < TOL1 * abs(ref), (i, llk[0, i], ref)
+            checked += 1
+    assert checked >= 20
+    pb.close()
+
+
 def test_batched_equals_separate_handles_over_cycles():
     from paper_2008_11511_gb300 import Ptycho, PtychoBatch
     probs = _problems()[:3]
