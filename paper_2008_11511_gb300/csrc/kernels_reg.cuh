@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(P
     }
     __syncthreads();
     constexpr float invN2 = 1.0f / float(N * N);
-    KahanF llk;
+    float llk = 0.f;  // the terms are >= 0: a plain float sum of a thread's pixels
 #pragma unroll
     for (int i = 0; i < S::CI2; ++i) {
         const int w = threadIdx.x + i * kThreads;
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(P
                     ic += __ldg(a.bg + pix);
                     if (a.bg_acc && !masked) atomicAdd(a.bg_acc + pix, fmaxf(io, 0.f) / fmaxf(ic, 1e-30f));
                 }
-                if (!masked) llk.add(llk_term_fast(ic, io));
+                if (!masked) llk += llk_term_fast(ic, io);
                 float f;
                 if (masked) {
                     f = 0.f;
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(P
             }
         }
     }
-    double tot = block_sum_double<kThreads>(llk.value(), red_s);
+    double tot = block_sum_double<kThreads>((double)llk, red_s);
     if (threadIdx.x == 0) a.llk_part[(size_t)j * gridDim.x + blockIdx.x] = tot;
     if (mode == COL_LLK) return;
     __syncthreads();
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_mod
     }
     // the factor per pixel and the LLK
     constexpr float invN2 = 1.0f / float(N * N);
-    KahanF llk;
+    float llk = 0.f;  // the terms are >= 0: a plain float sum of a thread's pixels
 #pragma unroll
     for (int i = 0; i < S::CI2; ++i) {
         const int w = threadIdx.x + i * kThreads;
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_mod
                     ic += __ldg(a.bg + pix);
                     if (a.bg_acc && !masked) atomicAdd(a.bg_acc + pix, fmaxf(io, 0.f) / fmaxf(ic, 1e-30f));
                 }
-                if (!masked) llk.add(llk_term_fast(ic, io));
+                if (!masked) llk += llk_term_fast(ic, io);
                 float f;
                 if (masked)
                     f = 0.f;
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_mod
             }
         }
     }
-    const double tot = block_sum_double<kThreads>(llk.value(), red_s);
+    const double tot = block_sum_double<kThreads>((double)llk, red_s);
     if (threadIdx.x == 0) a.llk_part[(size_t)j * gridDim.x + blockIdx.x] = tot;
     if (mode == COL_LLK) return;
     // sweep 2: scale and inverse transforms
