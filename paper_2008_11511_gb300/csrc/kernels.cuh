@@ -143,20 +143,20 @@ __device__ __forceinline__ float llk_term(float ic, float io) {
 // ulp): u, t by __fdividef, ln by __logf in the branch where |u - ln(1+u)| is
 // at least 0.19 |u|, so the term keeps a relative error of a few 1e-7.
 __device__ __forceinline__ float llk_term_fast(float ic, float io) {
-    if (!(io > 0.f)) return ic;
+    // both forms are evaluated and the right one selected: no branches (a warp
+    // usually holds pixels of both kinds); for io <= 0 the selects discard the
+    // non-finite intermediates
     const float icf = fmaxf(ic, 1e-30f);
-    const float u = __fdividef(icf - io, io);
-    float f;
-    if (u > -0.5f && u < 1.0f) {
-        const float t = __fdividef(u, 2.0f + u);
-        const float t2 = t * t;
-        const float poly = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, 1.f / 15.f, 1.f / 13.f), 1.f / 11.f),
-                                                           1.f / 9.f), 1.f / 7.f), 1.f / 5.f), 1.f / 3.f);
-        f = fmaf(u, t, -2.0f * t * t2 * poly);
-    } else {
-        f = u - __logf(__fdividef(icf, io));
-    }
-    return io * f;
+    const float rio = __fdividef(1.0f, io);
+    const float u = (icf - io) * rio;
+    const float t = __fdividef(u, 2.0f + u);
+    const float t2 = t * t;
+    const float poly = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, 1.f / 15.f, 1.f / 13.f), 1.f / 11.f),
+                                                       1.f / 9.f), 1.f / 7.f), 1.f / 5.f), 1.f / 3.f);
+    const float fs = fmaf(u, t, -2.0f * t * t2 * poly);
+    const float fl = u - __logf(icf * rio);
+    const float f = (u > -0.5f && u < 1.0f) ? fs : fl;
+    return io > 0.f ? io * f : ic;
 }
 
 // sqrt(max(io, 0)) / max(sqrt(ic), 1e-20): the amplitude-projection factor, with
