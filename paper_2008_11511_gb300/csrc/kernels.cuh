@@ -703,7 +703,10 @@ template <int N>
 void launch_row_bwd(const ProbArgs& a, int j0, int nb, int G, int mode, int upd_obj, int upd_probe, cudaStream_t s) {
     if constexpr (has_reg<N>()) {
         dim3 grid(N / RegShape<N>::L, G * a.K);  // G frame slots per probe mode
-        k_row_bwd_r<N><<<grid, kThreads, smem_row_bwd_r<N>(), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
+        if (mode != BWD_GRAD && upd_probe)  // AP and DM store Psi' alike
+            k_row_bwd_r<N, true><<<grid, kThreads, smem_row_bwd_r<N>(), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
+        else
+            k_row_bwd_r<N, false><<<grid, kThreads, smem_row_bwd_r<N>(), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
         return;
     }
     dim3 grid(N / a.L3, G);
@@ -789,7 +792,7 @@ int row_bwd_per_sm() {
         int n = 0;
         cudaError_t e;
         if constexpr (has_reg<N>())
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_row_bwd_r<N>, kThreads, smem_row_bwd_r<N>());
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_row_bwd_r<N, true>, kThreads, smem_row_bwd_r<N>());
         else
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_row_bwd<N>, kThreads,
                                                               smem_row_bwd_t<N>(1, max_lines<N>()));

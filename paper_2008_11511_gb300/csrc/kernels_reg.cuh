@@ -463,9 +463,13 @@ __device__ __forceinline__ float2 tw_bwd(const float2* tw, int a, int b) {
 // grid (N / L, G K); blockIdx.y = slot * K + mode: the block handles rows
 // [y0, y0 + L) of one probe mode in frames slot + G t.
 // ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, int nb, int mode, int upd_obj,
-                                                           int upd_probe) {
+// kCycle: the cycle's form (AP / DM, probe sums accumulated), with the mode and
+// the probe flag fixed at compile time; otherwise both come from the arguments.
+template <int N, bool kCycle>
+__global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, int nb, int mode_arg, int upd_obj,
+                                                           int upd_probe_arg) {
+    const int mode = kCycle ? (int)BWD_DM : mode_arg;
+    const int upd_probe = kCycle ? 1 : upd_probe_arg;
     using S = BwdShape<N>;
     constexpr int R = S::R, M = S::M, L = S::L, P = reg_pitch<N>();
     constexpr bool kRegAcc = S::kRegAcc;
@@ -870,7 +874,8 @@ cudaError_t set_attrs_r() {
     if ((e = cudaFuncSetAttribute(k_row_fwd_r<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_modes_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_modes_r<N>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_row_fwd_ls_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
@@ -879,7 +884,8 @@ cudaError_t set_attrs_r() {
     if ((e = cudaFuncSetAttribute(k_row_fwd_r<N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
-    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     return cudaSuccess;
 }
 
