@@ -138,9 +138,12 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_r(
 // grid (N / L, frames in batch); block handles columns [x0, x0 + L).
 // ---------------------------------------------------------------------------
 // kBg: the problem has an incoherent background (separate instantiation, so
-// that the common path carries none of its loads and sums).
-template <int N, bool kBg>
-__global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(ProbArgs a, int j0, int mode) {
+// that the common path carries none of its loads and sums).  kCycle: the
+// cycle's projection (COL_PROJECT) fixed at compile time; otherwise the mode
+// comes from the argument.
+template <int N, bool kBg, bool kCycle>
+__global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(ProbArgs a, int j0, int mode_arg) {
+    const int mode = kCycle ? (int)COL_PROJECT : mode_arg;
     using S = RegShape<N>;
     constexpr int R = S::R, M = S::M, C = S::C, P = S::P;
     constexpr int I1b = (C * M + kThreads - 1) / kThreads;  // inverse pass-2 items (M per column)
@@ -872,8 +875,10 @@ cudaError_t set_attrs_r() {
     const int carve = cudaSharedmemCarveoutMaxShared;  // room for 5-6 blocks of ~37 KB per SM
     if ((e = cudaFuncSetAttribute(k_row_fwd_r<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_row_fwd_r<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-    if ((e = cudaFuncSetAttribute(k_col_r<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-    if ((e = cudaFuncSetAttribute(k_col_r<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_r<N, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_r<N, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_r<N, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_r<N, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_modes_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
@@ -882,8 +887,10 @@ cudaError_t set_attrs_r() {
     if ((e = cudaFuncSetAttribute(k_col_ls_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_row_fwd_r<N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_row_fwd_r<N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
-    if ((e = cudaFuncSetAttribute(k_col_r<N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
-    if ((e = cudaFuncSetAttribute(k_col_r<N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_r<N, false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_r<N, false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_r<N, true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_r<N, true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     return cudaSuccess;
