@@ -536,7 +536,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
     }
     // the block's probe rows are the same for all its frames: this thread's
     // pass-2 pixels stay in registers (one-mode sizes with register sums)
-    constexpr bool kRegProbe = kRegAcc;
+    // (the sizes with a 28- or 32-point first factor read it from L1 instead:
+    // their pass-1 values would push it out of the registers)
+    constexpr bool kRegProbe = kRegAcc && R < 28;
     float2 pr_r[kRegProbe ? S::I2 : 1][kRegProbe ? M : 1];
     if constexpr (kRegProbe) {
 #pragma unroll
