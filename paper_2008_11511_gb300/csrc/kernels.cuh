@@ -708,9 +708,11 @@ void launch_row_bwd(const ProbArgs& a, int j0, int nb, int G, int mode, int upd_
     if constexpr (has_reg<N>()) {
         dim3 grid(N / RegShape<N>::L, G * a.K);  // G frame slots per probe mode
         if (mode != BWD_GRAD && upd_probe)  // AP and DM store Psi' alike
-            k_row_bwd_r<N, true><<<grid, kThreads, smem_row_bwd_r<N>(), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
+            k_row_bwd_r<N, 1><<<grid, kThreads, smem_row_bwd_r<N>(), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
+        else if (mode == BWD_GRAD && upd_obj && !upd_probe)
+            k_row_bwd_r<N, 2><<<grid, kThreads, smem_row_bwd_r<N>(), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
         else
-            k_row_bwd_r<N, false><<<grid, kThreads, smem_row_bwd_r<N>(), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
+            k_row_bwd_r<N, 0><<<grid, kThreads, smem_row_bwd_r<N>(), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
         return;
     }
     dim3 grid(N / a.L3, G);
@@ -796,7 +798,7 @@ int row_bwd_per_sm() {
         int n = 0;
         cudaError_t e;
         if constexpr (has_reg<N>())
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_row_bwd_r<N, true>, kThreads, smem_row_bwd_r<N>());
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_row_bwd_r<N, 1>, kThreads, smem_row_bwd_r<N>());
         else
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_row_bwd<N>, kThreads,
                                                               smem_row_bwd_t<N>(1, max_lines<N>()));

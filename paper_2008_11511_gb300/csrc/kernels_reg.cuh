@@ -466,13 +466,15 @@ __device__ __forceinline__ float2 tw_bwd(const float2* tw, int a, int b) {
 // grid (N / L, G K); blockIdx.y = slot * K + mode: the block handles rows
 // [y0, y0 + L) of one probe mode in frames slot + G t.
 // ---------------------------------------------------------------------------
-// kCycle: the cycle's form (AP / DM, probe sums accumulated), with the mode and
-// the probe flag fixed at compile time; otherwise both come from the arguments.
-template <int N, bool kCycle>
-__global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, int nb, int mode_arg, int upd_obj,
+// kForm fixes the mode and the flags at compile time: 1 = the cycle's form
+// (AP / DM: Psi' stored, probe sums accumulated), 2 = the object gradient
+// alone (BWD_GRAD, no probe gradient); 0 = all from the arguments.
+template <int N, int kForm>
+__global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, int nb, int mode_arg, int upd_obj_arg,
                                                            int upd_probe_arg) {
-    const int mode = kCycle ? (int)BWD_DM : mode_arg;
-    const int upd_probe = kCycle ? 1 : upd_probe_arg;
+    const int mode = kForm == 1 ? (int)BWD_DM : kForm == 2 ? (int)BWD_GRAD : mode_arg;
+    const int upd_probe = kForm == 1 ? 1 : kForm == 2 ? 0 : upd_probe_arg;
+    const int upd_obj = kForm == 2 ? 1 : upd_obj_arg;
     using S = BwdShape<N>;
     constexpr int R = S::R, M = S::M, L = S::L, P = reg_pitch<N>();
     constexpr bool kRegAcc = S::kRegAcc;
@@ -881,8 +883,9 @@ cudaError_t set_attrs_r() {
     if ((e = cudaFuncSetAttribute(k_col_r<N, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_modes_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_modes_r<N>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_row_fwd_ls_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
@@ -893,8 +896,9 @@ cudaError_t set_attrs_r() {
     if ((e = cudaFuncSetAttribute(k_col_r<N, false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N, true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_col_r<N, true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
-    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
-    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     return cudaSuccess;
 }
 
