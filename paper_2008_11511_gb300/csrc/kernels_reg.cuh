@@ -293,8 +293,11 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(P
 // The thread-to-pixel mapping is that of k_col_r (so the mask-bit table is
 // shared).  grid (N / C, frames in batch).
 // ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_modes_r(ProbArgs a, int j0, int mode) {
+// kCycle: the cycle's projection without a background, fixed at compile time.
+template <int N, bool kCycle>
+__global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_modes_r(ProbArgs a, int j0, int mode_arg) {
+    const int mode = kCycle ? (int)COL_PROJECT : mode_arg;
+    const float* bgp = kCycle ? nullptr : a.bg;
     using S = RegShape<N>;
     constexpr int R = S::R, M = S::M, C = S::C, P = S::P;
     constexpr int I1b = (C * M + kThreads - 1) / kThreads;  // inverse pass-2 items (M per column)
@@ -378,8 +381,8 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_mod
                 const bool masked = a.mbits ? ((mbits >> k1) & 1u) != 0u : a.mask[pix] != 0;
                 float ic = ic_r[i][k1] * invN2;
                 const float io = __ldcs(ib + (size_t)R * k1 * N);
-                if (a.bg) {
-                    ic += __ldg(a.bg + pix);
+                if (bgp) {
+                    ic += __ldg(bgp + pix);
                     if (a.bg_acc && !masked) atomicAdd(a.bg_acc + pix, fmaxf(io, 0.f) / fmaxf(ic, 1e-30f));
                 }
                 if (!masked) llk += llk_term_fast(ic, io);
@@ -886,8 +889,10 @@ cudaError_t set_attrs_r() {
     if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_row_bwd_r<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-    if ((e = cudaFuncSetAttribute(k_col_modes_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
-    if ((e = cudaFuncSetAttribute(k_col_modes_r<N>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_modes_r<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_modes_r<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_modes_r<N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
+    if ((e = cudaFuncSetAttribute(k_col_modes_r<N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
     if ((e = cudaFuncSetAttribute(k_row_fwd_ls_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_col_ls_r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_row_fwd_r<N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, carve))) return e;
