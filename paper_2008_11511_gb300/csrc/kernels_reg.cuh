@@ -840,9 +840,9 @@ __global__ void __launch_bounds__(kThreads, ls_min_blocks<N>()) k_col_ls_r(ProbA
                         const float di = 2.f * (av.x * bv.x + av.y * bv.y) * invN2;
                         const float dd = d2[i][k1] + 2.f * cnorm(bv) * invN2;
                         const float io = fmaxf(__ldcs(io_p + (size_t)R * k1 * N), 0.f);
-                        const float icf = fmaxf(ic, 1e-30f);
-                        const float w1 = 1.f - io / icf;
-                        const float q = di / icf;  // I_o dI^2 / I_c^2 = I_o q^2
+                        const float ric = __fdividef(1.0f, fmaxf(ic, 1e-30f));  // 1 / I_c (a few ulp)
+                        const float w1 = fmaf(-io, ric, 1.f);
+                        const float q = di * ric;  // I_o dI^2 / I_c^2 = I_o q^2
                         l1.add(w1 * di);
                         l2.add(fmaf(w1, dd, io * q * q));
                     }
