@@ -1055,8 +1055,11 @@ ptx_status enqueue_line_coeffs(ptx_handle* h, ProbHost& ph, const float2* d_obj,
     ProbArgs a = ph.args;
     a.dir_obj = d_obj;
     a.dir_probe = d_probe;
-    const size_t frame3 = 3 * (size_t)ph.p.K * ph.p.N * ph.p.N * sizeof(float2);
-    size_t B = h->spec_bytes / frame3;
+    // work stack per frame: the waves A, B (and C with both parts of the
+    // direction) of one mode for the register kernels, 3 K waves otherwise
+    const int waves = (ph.p.K == 1 && ph.ks->reg_lines > 0) ? ((d_obj && d_probe) ? 3 : 2) : 3 * ph.p.K;
+    const size_t frame_w = (size_t)waves * ph.p.N * ph.p.N * sizeof(float2);
+    size_t B = h->spec_bytes / frame_w;
     if (B < 1) B = 1;
     if (B > (size_t)ph.p.J) B = ph.p.J;
     if (B > 32768) B = 32768;

@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, i
 // direction are given.
 //
 // Row pass: grid (N / L, frames in batch, waves), blockIdx.z = wave (0: A,
-// 1: B, 2: C); row transforms into spec[b][wave].
+// 1: B, 2: C); row transforms into spec[b][wave] (gridDim.z waves per frame).
 // ---------------------------------------------------------------------------
 template <int N>
 __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_ls_r(ProbArgs a, int j0) {
@@ -739,7 +739,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_ls
 #pragma unroll
             for (int n1 = 0; n1 < M; ++n1) u[n1] = src[n1];
             Dft<M, -1>::run(u);
-            float2* dst = a.spec + (((size_t)b * 3 + wave) * N + y0 + line) * N + k2;
+            float2* dst = a.spec + (((size_t)b * gridDim.z + wave) * N + y0 + line) * N + k2;
             const uint64_t el = policy_evict_last();
 #pragma unroll
             for (int k1 = 0; k1 < M; ++k1) st_hint(dst + R * k1, u[k1], el);
@@ -781,7 +781,7 @@ __global__ void __launch_bounds__(kThreads, ls_min_blocks<N>()) k_col_ls_r(ProbA
     __syncthreads();
     for (int s = 0; s < nwaves; ++s) {
         const int wave = s == 0 ? 0 : (s == nwaves - 1 ? 1 : 2);
-        const float2* spec = a.spec + ((size_t)b * 3 + wave) * N * N + x0;
+        const float2* spec = a.spec + ((size_t)b * nwaves + wave) * N * N + x0;
 #pragma unroll
         for (int i = 0; i < S::CI1; ++i) {
             const int w = threadIdx.x + i * kThreads;
