@@ -223,6 +223,93 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def exact_counts(x):
+    """The intensities as uint16 photon counts when that is exact, else None."""
+    if x.min() < 0 or x.max() > 65535 or not np.array_equal(x, np.rint(x)):
+        return None
+    return x.astype(np.uint16)
+
+
+def run_e2e(args, s, pb, obj, probe, iobs, params, llk_buf, stream, dev, ws):
+    """The end-to-end leg: per step the host -> device upload of the intensity
+    stack from pinned memory, the DM cycle, the LLK read back; the upload of
+    step k + 1 runs on copy streams while step k computes.
+
+    Photon counts (the synthetic intensities are Poisson counts) go up as
+    uint16 and are widened into the problem's float32 array on the device by
+    ``counts_to_float`` before the cycle (half the bytes of a float32 upload);
+    otherwise float32 frames go up into the other of two device buffers, each
+    with its own handle sharing the object, the probe and the exit waves.
+    Returns (frames/s, bytes uploaded per step, description)."""
+    import torch
+    from paper_2008_11511_gb300 import Ptycho, counts_to_float
+    counts = exact_counts(s.iobs) if args.e2e_dtype in ("auto", "u16") else None
+    if args.e2e_dtype == "u16" and counts is None:
+        raise SystemExit("--e2e-dtype u16: the intensities are not exact uint16 counts")
+    host_llk = torch.empty(1, dtype=torch.float64).pin_memory()
+    n_copy = max(1, args.copy_streams)
+    bounds = [s.J * c // n_copy for c in range(n_copy + 1)]
+    copy_streams = [torch.cuda.Stream(dev) for _ in range(n_copy)]
+    copied = [[torch.cuda.Event() for _ in range(n_copy)] for _ in range(2)]
+    used = [torch.cuda.Event(), torch.cuda.Event()]
+    extra = None
+    if counts is not None:
+        host = torch.from_numpy(counts).pin_memory()
+        stage = [torch.empty(counts.shape, dtype=torch.uint16, device=dev) for _ in range(2)]
+        handles, desc = (pb, pb), "uint16 photon counts (exact) from pinned host memory, widened to float32 on the device"
+    else:
+        host = torch.from_numpy(s.iobs).pin_memory()
+        iobs2 = torch.empty_like(iobs)
+        extra = Ptycho(obj, probe, iobs2, s.positions, s.mask, psi=pb.psi)
+        for name, val in params:
+            extra.set_param(name, val)
+        iobs2.copy_(iobs)
+        extra.dm(1, llk=llk_buf)  # graph capture outside the timed region
+        stage = [iobs, iobs2]
+        handles, desc = (pb, extra), "float32 frames from pinned host memory into two device buffers"
+    desc += f", on {n_copy} copy stream(s) one step ahead"
+
+    def upload(nb, wait_used):
+        for c, cs in enumerate(copy_streams):
+            with torch.cuda.stream(cs):
+                if wait_used:
+                    cs.wait_event(used[nb])
+                stage[nb][bounds[c]:bounds[c + 1]].copy_(host[bounds[c]:bounds[c + 1]], non_blocking=True)
+                copied[nb][c].record(cs)
+
+    e_steps = max(1, min(args.steps, 10))
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    upload(0, False)
+    for k in range(e_steps):
+        b = k % 2
+        if k + 1 < e_steps:
+            upload(1 - b, k >= 1)
+        for ev in copied[b]:
+            stream.wait_event(ev)
+        if counts is not None:
+            counts_to_float(iobs, stage[b])
+            used[b].record(stream)
+            l = pb.dm(1, llk=llk_buf)
+        else:
+            l = handles[b].dm(1, llk=llk_buf)
+            used[b].record(stream)
+        host_llk.copy_(l[:1], non_blocking=True)
+    stream.synchronize()
+    for cs in copy_streams:
+        cs.synchronize()
+    el = time.perf_counter() - t0
+    barrier(ws)
+    el = max_over_ranks(el, ws)
+    if extra is not None:
+        extra.close()
+    if counts is not None:  # the device array holds the same values again
+        counts_to_float(iobs, stage[0])
+        torch.cuda.synchronize(dev)
+    return s.J * e_steps * ws / el, host.numel() * host.element_size(), desc
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_init()
@@ -301,57 +388,7 @@ def run_ours(args):
 
     # end to end through the public API with host buffers: every step copies its
     # intensity stack in from pinned host memory and reads the cycle's LLK back.
-    # The copies run on their own streams one step ahead, into the other of two
-    # device buffers; each buffer has its own handle, and both handles share the
-    # object, the probe and the exit-wave stack.
-    host_iobs = torch.from_numpy(s.iobs).pin_memory()
-    host_llk = torch.empty(1, dtype=torch.float64).pin_memory()
-    iobs2 = torch.empty_like(iobs)
-    pb2 = Ptycho(obj, probe, iobs2, s.positions, s.mask, psi=pb.psi)
-    for name, val in params:
-        pb2.set_param(name, val)
-    iobs2.copy_(iobs)
-    pb2.dm(1, llk=llk_buf)  # graph capture outside the timed region
-    handles, bufs = (pb, pb2), (iobs, iobs2)
-    # the upload is split over several copy streams (contiguous frame ranges),
-    # so that more than one copy engine can serve it
-    n_copy = max(1, args.copy_streams)
-    bounds = [s.J * c // n_copy for c in range(n_copy + 1)]
-    copy_streams = [torch.cuda.Stream(dev) for _ in range(n_copy)]
-    copied = [[torch.cuda.Event() for _ in range(n_copy)] for _ in range(2)]
-    used = [torch.cuda.Event(), torch.cuda.Event()]
-
-    def upload(nb, wait_used):
-        for c, cs in enumerate(copy_streams):
-            with torch.cuda.stream(cs):
-                if wait_used:
-                    cs.wait_event(used[nb])
-                bufs[nb][bounds[c]:bounds[c + 1]].copy_(host_iobs[bounds[c]:bounds[c + 1]], non_blocking=True)
-                copied[nb][c].record(cs)
-
-    e_steps = max(1, min(args.steps, 10))
-    barrier(ws)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    upload(0, False)
-    for k in range(e_steps):
-        b = k % 2
-        if k + 1 < e_steps:
-            upload(1 - b, k >= 1)
-        for ev in copied[b]:
-            stream.wait_event(ev)
-        l = handles[b].dm(1, llk=llk_buf)
-        used[b].record(stream)
-        host_llk.copy_(l[:1], non_blocking=True)
-    stream.synchronize()
-    for cs in copy_streams:
-        cs.synchronize()
-    el = time.perf_counter() - t0
-    barrier(ws)
-    el = max_over_ranks(el, ws)
-    e2e_value = s.J * e_steps * ws / el
-    pb2.close()
-    del iobs2
+    e2e_value, e2e_bytes, e2e_copies = run_e2e(args, s, pb, obj, probe, iobs, params, llk_buf, stream, dev, ws)
 
     # roofline: the dominant kernel by time share
     pk = peaks()
@@ -401,9 +438,8 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (Psi 2.1 GB + I 1.05 GB per replica); no flush"},
                 "roofline": roof, "roofline_cycle": roof_cycle, "kernels": kstats,
                 "clocks": clk, "gpu_launches": gpu_launches,
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(s.iobs.nbytes),
-                        "d2h_bytes_per_step": 8, "steps": e_steps,
-                        "copies": f"pinned host -> device on {n_copy} copy streams, one step ahead, two buffers"},
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(e2e_bytes),
+                        "d2h_bytes_per_step": 8, "steps": max(1, min(args.steps, 10)), "copies": e2e_copies},
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     pb.close()
@@ -422,6 +458,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=0,
                     help="use only the first FRAMES frames of the workload (small cases for profiling)")
+    ap.add_argument("--e2e-dtype", choices=("auto", "u16", "f32"), default="auto",
+                    help="intensity upload of the end-to-end leg: uint16 counts when exact (auto), or float32")
     ap.add_argument("--copy-streams", type=int, default=1,
                     help="streams the end-to-end leg splits each step's intensity upload over")
     ap.add_argument("--lanes", type=int, default=0,

@@ -299,6 +299,15 @@ ptx_status ptx_llk_static(int32_t N, int32_t K, int32_t J, int32_t Ho, int32_t W
                           const void* probe, const int32_t* positions, const float* iobs, const uint8_t* mask,
                           double* llk_dev, void* stream);
 
+/* Photon counts to intensities: dst[i] = (float)src[i] for i < n, on the
+ * device, asynchronous on the stream.  Detectors count photons as 16-bit
+ * integers; uploading the counts and widening them on the device moves half
+ * the bytes of a float32 upload (every uint16 value is exact in float32).
+ * dst: device float32 [n] (e.g. a problem's iobs array, written in place),
+ * src: device uint16 [n]; both 16-byte aligned.  n = 0 does nothing.
+ * PTX_ERR_INVALID_ARG for a null or misaligned pointer. */
+ptx_status ptx_counts_to_float(float* dst, const uint16_t* src, size_t n, void* stream);
+
 /* Self-test of the failure path of the bounded device waits (no GPU fault is
  * involved): enqueues one kernel whose single waiting thread waits for a flag
  * that nothing sets, for at most limit_us microseconds of the GPU's global

@@ -1232,6 +1232,16 @@ ptx_status ptx_fft2(void* data, int32_t nframes, int32_t N, int32_t direction, v
     return PTX_OK;
 }
 
+ptx_status ptx_counts_to_float(float* dst, const uint16_t* src, size_t n, void* stream) {
+    if (n == 0) return PTX_OK;
+    if (!dst || !src) return fail(PTX_ERR_INVALID_ARG, "null dst or src");
+    if ((uintptr_t)dst % 16 || (uintptr_t)src % 16) return fail(PTX_ERR_INVALID_ARG, "dst and src must be 16-byte aligned");
+    k_counts_to_float<<<4 * 152, 256, 0, (cudaStream_t)stream>>>(src, dst, n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ptx_counts_to_float launch");
+    return PTX_OK;
+}
+
 ptx_status ptx_profile_enable(ptx_handle* h, int32_t enable) {
     if (!h) return fail(PTX_ERR_INVALID_ARG, "null handle");
     h->profiling = enable != 0;

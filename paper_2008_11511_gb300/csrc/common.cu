@@ -225,6 +225,27 @@ __global__ void k_wait_selftest(int* err_flag, unsigned long long limit_ns) {
     }
 }
 
+// Photon counts (uint16) to the float32 intensities the passes read: 8 counts
+// (16 bytes) per thread and step, exact (every uint16 is a float32 integer).
+__global__ void k_counts_to_float(const uint16_t* __restrict__ src, float* __restrict__ dst, size_t n) {
+    const size_t n8 = n / 8;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n8; i += stride) {
+        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(src) + i);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        float4 lo, hi;
+        lo.x = (float)(w[0] & 0xffffu); lo.y = (float)(w[0] >> 16);
+        lo.z = (float)(w[1] & 0xffffu); lo.w = (float)(w[1] >> 16);
+        hi.x = (float)(w[2] & 0xffffu); hi.y = (float)(w[2] >> 16);
+        hi.z = (float)(w[3] & 0xffffu); hi.w = (float)(w[3] >> 16);
+        float4* d = reinterpret_cast<float4*>(dst) + 2 * i;
+        d[0] = lo;
+        d[1] = hi;
+    }
+    // the tail (n not a multiple of 8)
+    for (size_t i = 8 * n8 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = (float)src[i];
+}
+
 __global__ void k_set_ctl(Ctl* ctl, double* llk_out, int nprob) {
     ctl->llk_out = llk_out;
     ctl->cycle = 0;

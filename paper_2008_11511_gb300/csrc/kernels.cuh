@@ -575,6 +575,7 @@ struct CgArgs {
     double* cg_part;  // [kCgBlocks][3] per-block partial dot products
 };
 __global__ void k_wait_selftest(int* err_flag, unsigned long long limit_ns);
+__global__ void k_counts_to_float(const uint16_t* __restrict__ src, float* __restrict__ dst, size_t n);
 __global__ void k_cg_dots(CgArgs c);
 __global__ void k_cg_reduce(CgArgs c);
 __global__ void k_cg_direction(CgArgs c);

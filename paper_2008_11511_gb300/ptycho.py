@@ -367,6 +367,21 @@ def fft2(x: torch.Tensor, direction: int = -1) -> torch.Tensor:
     return x
 
 
+def counts_to_float(dst: torch.Tensor, counts: torch.Tensor) -> torch.Tensor:
+    """dst[...] = counts as float32, on the GPU (photon counts uploaded as
+    16-bit integers and widened on the device, e.g. into a problem's ``iobs``).
+    ``counts`` is a uint16 CUDA tensor with as many elements as ``dst``.
+    Returns ``dst``."""
+    _require_cuda(dst, "dst", torch.float32)
+    _require_cuda(counts, "counts", torch.uint16)
+    if counts.numel() != dst.numel():
+        raise ValueError("counts and dst must have the same number of elements")
+    with torch.cuda.device(dst.device):
+        _lib.call("ptx_counts_to_float", ctypes.c_void_p(dst.data_ptr()), ctypes.c_void_p(counts.data_ptr()),
+                  ctypes.c_size_t(dst.numel()), _stream_ptr(dst.device))
+    return dst
+
+
 class PtychoLLK(torch.autograd.Function):
     """L(O, P) = Poisson LLK as a differentiable function of the object and the
     probe.  ``forward`` copies (obj, probe) into the problem's buffers and calls

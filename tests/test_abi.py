@@ -97,6 +97,8 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert STATUS_NAMES[lib.ptx_fft2(ctypes.c_void_p(0x1000), 1, 100, -1, None)] == "PTX_ERR_UNSUPPORTED"
     assert STATUS_NAMES[lib.ptx_fft2(ctypes.c_void_p(0x1000), 1, 64, 2, None)] == "PTX_ERR_INVALID_ARG"
     assert STATUS_NAMES[lib.ptx_wait_selftest(None, 1000, None)] == "PTX_ERR_INVALID_ARG"
+    assert STATUS_NAMES[lib.ptx_counts_to_float(None, None, 0, None)] == "PTX_OK"
+    assert STATUS_NAMES[lib.ptx_counts_to_float(None, None, 5, None)] == "PTX_ERR_INVALID_ARG"
     lib.ptx_destroy(None)
 
 

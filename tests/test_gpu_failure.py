@@ -72,3 +72,27 @@ def test_wait_selftest_rejects_limits_out_of_range():
         assert ei.value.status_name == "PTX_ERR_INVALID_ARG"
     pb.ap(1)  # nothing was enqueued; the handle works
     pb.close()
+
+
+def test_counts_to_float_is_exact_with_a_ragged_tail():
+    """uint16 photon counts widened on the device: every value exact, n not a
+    multiple of the 8 counts a thread converts at once."""
+    from paper_2008_11511_gb300 import counts_to_float
+    rng = np.random.default_rng(9)
+    n = 1_000_003
+    c = rng.integers(0, 65536, size=n, dtype=np.uint16)
+    c[:3] = (0, 65535, 1)
+    dst = torch.full((n,), -1.0, dtype=torch.float32, device="cuda")
+    counts_to_float(dst, torch.from_numpy(c).cuda())
+    assert np.array_equal(dst.cpu().numpy(), c.astype(np.float32))
+
+
+def test_counts_to_float_rejects_misaligned_pointers():
+    from paper_2008_11511_gb300 import _lib
+    from paper_2008_11511_gb300._lib import PtychoError
+    buf = torch.zeros(64, dtype=torch.float32, device="cuda")
+    src = torch.zeros(64, dtype=torch.uint16, device="cuda")
+    with pytest.raises(PtychoError) as ei:
+        _lib.call("ptx_counts_to_float", ctypes.c_void_p(buf.data_ptr() + 4), ctypes.c_void_p(src.data_ptr()),
+                  ctypes.c_size_t(8), None)
+    assert ei.value.status_name == "PTX_ERR_INVALID_ARG"
