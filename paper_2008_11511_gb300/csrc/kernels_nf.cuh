@@ -23,8 +23,8 @@ namespace ptx {
 // Column pass of the propagator: grid (N / L, frames in batch); block
 // handles columns [x0, x0 + L).  nf_t = t[k] (complex64, k in FFT order).
 // ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_nf(ProbArgs a, int dir) {
+template <int N, int DIR>
+__global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_nf(ProbArgs a) {
     using S = RegShape<N>;
     constexpr int R = S::R, M = S::M, C = S::L, P = S::P;
     constexpr int I1b = (C * M + kThreads - 1) / kThreads;
@@ -74,11 +74,11 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_nf(
             Dft<M, -1>::run(u[i]);
             // X^[ky = k2 + R k1][kx] times h (or conj(h)) / N^2
             float2 tx = a.nf_t[x0 + c];
-            if (dir < 0) tx.y = -tx.y;
+            if constexpr (DIR < 0) tx.y = -tx.y;
 #pragma unroll
             for (int k1 = 0; k1 < M; ++k1) {
                 float2 ty = a.nf_t[k2 + R * k1];
-                if (dir < 0) ty.y = -ty.y;
+                if constexpr (DIR < 0) ty.y = -ty.y;
                 u[i][k1] = cscale(cmul(u[i][k1], cmul(ty, tx)), invN2);
             }
             Dft<M, +1>::run(u[i]);
@@ -112,8 +112,12 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_nf(
 // correction back into the work stack (skipped with llk_only).
 // grid (N / L, frames in batch); block handles rows [y0, y0 + L) of frame j0 + blockIdx.y.
 // ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_row_proj(ProbArgs a, int j0, int llk_only) {
+// kCycle: the cycle's form (the correction written back, no background) fixed
+// at compile time; otherwise llk_only and the background come from the arguments.
+template <int N, bool kCycle>
+__global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_row_proj(ProbArgs a, int j0, int llk_only_arg) {
+    const int llk_only = kCycle ? 0 : llk_only_arg;
+    const float* bgp = kCycle ? nullptr : a.bg;
     using S = RegShape<N>;
     constexpr int R = S::R, M = S::M, L = S::L, P = S::P;
     extern __shared__ __align__(16) float2 sm[];
@@ -156,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_row_pro
         }
     }
     __syncthreads();
-    KahanF llk;
+    float llk = 0.f;  // the terms are >= 0: a plain float sum of a thread's pixels
 #pragma unroll
     for (int i = 0; i < S::I2; ++i) {
         const int w = threadIdx.x + i * kThreads;
@@ -171,12 +175,12 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_row_pro
                 float ic = cnorm(u[i][k1]);
                 const float io = __ldcs(io_row + R * k1);
                 const bool masked = mk_row[R * k1] != 0;
-                if (a.bg) {  // incoherent background in the detector plane
+                if (bgp) {  // incoherent background in the detector plane
                     const int pix = y * N + k2 + R * k1;
-                    ic += __ldg(a.bg + pix);
+                    ic += __ldg(bgp + pix);
                     if (a.bg_acc && !masked) atomicAdd(a.bg_acc + pix, fmaxf(io, 0.f) / fmaxf(ic, 1e-30f));
                 }
-                if (!masked) llk.add(llk_term_fast(ic, io));
+                if (!masked) llk += llk_term_fast(ic, io);
                 const float f = masked ? 0.f : amp_ratio(io, ic) - 1.0f;
                 u[i][k1] = cscale(u[i][k1], f);
             }
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_row_pro
             }
         }
     }
-    const double tot = block_sum_double<kThreads>(llk.value(), red_s);
+    const double tot = block_sum_double<kThreads>((double)llk, red_s);
     if (threadIdx.x == 0) a.llk_part[(size_t)j * gridDim.x + blockIdx.x] = tot;
     if (llk_only) return;
     __syncthreads();
@@ -245,29 +249,37 @@ template <int N>
 void launch_col_nf(const ProbArgs& a, int nb, int dir, cudaStream_t s) {
     if constexpr (Plan<N>::M > 1) {
         dim3 grid(N / RegShape<N>::L, nb);
-        k_col_nf<N><<<grid, kThreads, smem_nf<N>(), s>>>(a, dir);
+        if (dir < 0)
+            k_col_nf<N, -1><<<grid, kThreads, smem_nf<N>(), s>>>(a);
+        else
+            k_col_nf<N, +1><<<grid, kThreads, smem_nf<N>(), s>>>(a);
     }
 }
 template <int N>
 void launch_row_proj(const ProbArgs& a, int j0, int nb, int llk_only, cudaStream_t s) {
     if constexpr (Plan<N>::M > 1) {
         dim3 grid(N / RegShape<N>::L, nb);
-        k_row_proj<N><<<grid, kThreads, smem_nf<N>(), s>>>(a, j0, llk_only);
+        if (!llk_only && !a.bg)
+            k_row_proj<N, true><<<grid, kThreads, smem_nf<N>(), s>>>(a, j0, llk_only);
+        else
+            k_row_proj<N, false><<<grid, kThreads, smem_nf<N>(), s>>>(a, j0, llk_only);
     }
+}
+template <int N, class F>
+cudaError_t nf_attrs(F f) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    return e;
 }
 template <int N>
 cudaError_t set_attrs_nf() {
     if constexpr (Plan<N>::M > 1) {
         cudaError_t e;
-        if ((e = cudaFuncSetAttribute(k_col_nf<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024))) return e;
-        if ((e = cudaFuncSetAttribute(k_row_proj<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024)))
-            return e;
-        if ((e = cudaFuncSetAttribute(k_col_nf<N>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                      cudaSharedmemCarveoutMaxShared)))
-            return e;
-        if ((e = cudaFuncSetAttribute(k_row_proj<N>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                      cudaSharedmemCarveoutMaxShared)))
-            return e;
+        if ((e = nf_attrs<N>(k_col_nf<N, -1>))) return e;
+        if ((e = nf_attrs<N>(k_col_nf<N, +1>))) return e;
+        if ((e = nf_attrs<N>(k_row_proj<N, true>))) return e;
+        if ((e = nf_attrs<N>(k_row_proj<N, false>))) return e;
     }
     return cudaSuccess;
 }
