@@ -89,6 +89,9 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 2)
     float2(*st)[2][kRows * kBoxW] = reinterpret_cast<float2(*)[2][kRows * kBoxW]>(gsm);
     uint64_t* full = reinterpret_cast<uint64_t*>(gsm + kStages * 2 * kBox);
     uint64_t* empty = full + kStages;
+    // column offset (0 or 1) of each stage's window, written by the producer
+    // before its arrival on the stage's full barrier
+    __shared__ int stage_off[kStages];
     const int t = blockIdx.x;
     const int tid = tl.tile_ids[t];
     const int ty = tid / tl.ntx, tx = tid - ty * tl.ntx;
@@ -117,6 +120,7 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 2)
                 const int j = tl.tile_frames[f];
                 int xs, ys, off;
                 box_origin(a.pos[j], ty * kRows, tx, xs, ys, off);
+                stage_off[s] = off;
                 const uint32_t bar = s_u32(&full[s]);
                 bar_expect_tx(bar, kTx);
                 load_3d(s_u32(st[s][0]), &tm_psi, xs, ys, j * K + k, bar);
@@ -143,13 +147,11 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 2)
     bool ok = true;
     for (int it = 0; it < nitems; ++it) {
         const int s = it % kStages;
-        const int f = f0 + it / K;
-        int xs, ys, off;
-        box_origin(a.pos[tl.tile_frames[f]], ty * kRows, tx, xs, ys, off);
         if (!bar_wait(s_u32(&full[s]), (it / kStages) & 1)) {
             ok = false;
             break;
         }
+        const int off = stage_off[s];
         const float2* ps = st[s][0] + off + lane;
         const float2* pr = st[s][1] + off + lane;
 #pragma unroll
