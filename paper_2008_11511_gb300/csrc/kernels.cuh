@@ -621,8 +621,9 @@ __global__ void __launch_bounds__(kThreads) k_fft_cols(float2* data, int C) {
 }
 
 // Launch table for one frame size.  The row_fwd / col / row_bwd entries pick
-// the register-resident kernels (kernels_reg.cuh) for one probe mode and
-// two-pass sizes, and the shared-memory kernels above otherwise.
+// the register-resident kernels (kernels_reg.cuh) for the two-pass sizes (any
+// number of probe modes), and the shared-memory kernels above for the one-pass
+// sizes 8, 12 and 16.
 struct KernelSet {
     int N;
     void (*row_fwd)(const ProbArgs&, int j0, int nb, int mode, cudaStream_t);
