@@ -58,3 +58,12 @@ def test_source_hash_dates_the_traffic_file(bench):
     for k in ("col", "row_fwd", "row_bwd", "obj_gather"):
         assert len(d[k]["source_hash"]) == 16
     assert (bench.ncu_traffic("col") is None) == (d["col"]["source_hash"] != h)
+
+
+def test_code_hash_ignores_comments_only(bench):
+    a = 'int f(int x) {  // twice\n    return 2 * x; /* the double */\n}\nconst char* s = "// kept";\n'
+    b = 'int f(int x) {\n\n    return 2 * x;\n}\nconst char* s = "// kept";\n'
+    c = 'int f(int x) {\n    return 3 * x;\n}\nconst char* s = "// kept";\n'
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(c)
+    assert '"// kept"' in bench._code_only(a)
