@@ -394,6 +394,29 @@ def run_ours(args):
         pb.close()
         return
 
+    # the other form of the metric's comparison on the same box and data: the
+    # split-precision tensor-core column pass (TF32 hi + lo DFT stages) when the
+    # plain form was timed above, and the plain form otherwise
+    other = None
+    if not args.no_form_comparison and s.N == 256 and s.K == 1:
+        tc_other = 0 if args.tc else 1
+        pb.set_param("tc", tc_other)
+        pb.dm(2, llk=llk_buf)  # capture the other form's graph
+        torch.cuda.synchronize(dev)
+        n_other = max(1, min(args.steps, 10))
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        pb.dm(n_other, llk=llk_buf)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_o = max_over_ranks(f0.elapsed_time(f1), ws) / n_other
+        other = {"form": "tf32 hi+lo tensor-core DFT stages in the column pass" if tc_other else "fp32 (plain)",
+                 "value": s.J * ws / (ms_o / 1e3), "ms_per_step": ms_o, "steps": n_other}
+        pb.set_param("tc", 1 if args.tc else 0)
+        pb.dm(1, llk=llk_buf)
+        torch.cuda.synchronize(dev)
+
     # per-kernel durations, live, with events on the launch stream (direct launches)
     _lib.call("ptx_profile_enable", pb._handle(), 1)
     pb.dm(args.steps, llk=llk_buf)
@@ -461,7 +484,7 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "desc": workload_desc(s), "form": ("tf32 hi+lo tensor-core DFT stages in the column pass, fp32 elsewhere" if args.tc else "fp32 (plain)"),
                            "parallelism": f"replicas x{ws}",
                            "l2": "inputs larger than L2 (Psi 2.1 GB + I 1.05 GB per replica); no flush"},
-                "roofline": roof, "roofline_cycle": roof_cycle, "kernels": kstats,
+                "roofline": roof, "roofline_cycle": roof_cycle, "kernels": kstats, "other_form": other,
                 "clocks": clk, "gpu_launches": gpu_launches,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(e2e_bytes),
                         "d2h_bytes_per_step": 8, "steps": max(1, min(args.steps, 10)), "copies": e2e_copies},
@@ -483,6 +506,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=0,
                     help="use only the first FRAMES frames of the workload (small cases for profiling)")
+    ap.add_argument("--no-form-comparison", action="store_true",
+                    help="skip timing the other number format (plain FP32 vs the tensor-core column pass)")
     ap.add_argument("--e2e-dtype", choices=("auto", "u16", "f32"), default="auto",
                     help="intensity upload of the end-to-end leg: uint16 counts when exact (auto), or float32")
     ap.add_argument("--copy-streams", type=int, default=1,
