@@ -108,30 +108,49 @@ __global__ void __launch_bounds__(32 * (kConsumers + 1), 2)
     }
     __syncthreads();
 
-    if (warp == kConsumers) {  // producer
-        if (lane == 0) {
-            bool ok = true;
-            int it = 0;
-            for (; it < nitems && ok; ++it) {
-                const int s = it % kStages;
-                if (it >= kStages) ok = bar_wait(s_u32(&empty[s]), ((it / kStages) - 1) & 1);
-                if (!ok) break;
-                const int f = f0 + it / K, k = it - (it / K) * K;
-                const int j = tl.tile_frames[f];
-                int xs, ys, off;
-                box_origin(a.pos[j], ty * kRows, tx, xs, ys, off);
-                stage_off[s] = off;
-                const uint32_t bar = s_u32(&full[s]);
-                bar_expect_tx(bar, kTx);
-                load_3d(s_u32(st[s][0]), &tm_psi, xs, ys, j * K + k, bar);
-                load_3d(s_u32(st[s][1]), &tm_probe, xs, ys, k, bar);
+    if (warp == kConsumers) {  // producer warp
+        // the tile's frames and their positions are staged in shared memory by
+        // the whole warp, a chunk at a time, so that lane 0 issues the copies
+        // without dependent global loads between them
+        constexpr int kChunk = 128;
+        __shared__ int pf_j[kChunk];
+        __shared__ int2 pf_pos[kChunk];
+        int ok = 1;
+        int it = 0;
+        const int nf = f1 - f0;
+        for (int c0 = 0; c0 < nf && ok; c0 += kChunk) {
+            const int cn = min(kChunk, nf - c0);
+            __syncwarp();  // lane 0 is done with the previous chunk
+            for (int q = lane; q < cn; q += 32) {
+                const int j = tl.tile_frames[f0 + c0 + q];
+                pf_j[q] = j;
+                pf_pos[q] = a.pos[j];
             }
-            if (!ok) {
-                flag_error(a.err_flag);
-                // the copies already issued land before the block may exit
-                for (int q = (it > kStages ? it - kStages : 0); q < it; ++q)
-                    bar_wait(s_u32(&full[q % kStages]), (q / kStages) & 1);
+            __syncwarp();
+            if (lane == 0) {
+                for (int q = 0; q < cn && ok; ++q)
+                    for (int k = 0; k < K; ++k, ++it) {
+                        const int s = it % kStages;
+                        if (it >= kStages) ok = bar_wait(s_u32(&empty[s]), ((it / kStages) - 1) & 1);
+                        if (!ok) break;
+                        const int j = pf_j[q];
+                        int xs, ys, off;
+                        box_origin(pf_pos[q], ty * kRows, tx, xs, ys, off);
+                        stage_off[s] = off;
+                        const uint32_t bar = s_u32(&full[s]);
+                        bar_expect_tx(bar, kTx);
+                        load_3d(s_u32(st[s][0]), &tm_psi, xs, ys, j * K + k, bar);
+                        load_3d(s_u32(st[s][1]), &tm_probe, xs, ys, k, bar);
+                    }
             }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            it = __shfl_sync(0xffffffffu, it, 0);
+        }
+        if (lane == 0 && !ok) {
+            flag_error(a.err_flag);
+            // the copies already issued land before the block may exit
+            for (int q = (it > kStages ? it - kStages : 0); q < it; ++q)
+                bar_wait(s_u32(&full[q % kStages]), (q / kStages) & 1);
         }
         return;
     }
