@@ -289,8 +289,9 @@ ptx_status ptx_profile_read(ptx_handle* h, int32_t nkinds, int64_t* launches, do
  * GPU loading the library holds until the process exits.  The first call on
  * a device looks up that array's address with cudaGetSymbolAddress, clears its mask region
  * and synchronises the device once: make that first call before any stream
- * capture.  Sizes beyond the array (J > 65536, J * N / lines > 65536 partial
- * sums, or one frame's K * N * N * 8-byte work stack larger than the array's
+ * capture.  Sizes beyond the array (J > 65536, J * N / C > 65536 partial
+ * sums with C columns per block of the column pass, or one frame's
+ * K * N * N * 8-byte work stack larger than the array's
  * work region) are rejected with PTX_ERR_UNSUPPORTED and a message; nothing
  * is enqueued then.  All calls share the array and it keeps the last call's
  * contents; every call rewrites what it reads, but calls that overlap on the
