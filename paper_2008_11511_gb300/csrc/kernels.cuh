@@ -98,11 +98,7 @@ __device__ __forceinline__ void cp_async16_hint(void* smem_dst, const void* gmem
                  : "memory");
 }
 
-// Asynchronous 16-byte global -> shared copy (cp.async, bypassing L1).
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
-}
+// Asynchronous 8-byte global -> shared copy (cp.async).
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem_src) : "memory");
