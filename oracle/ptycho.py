@@ -500,12 +500,14 @@ def _dot(a, b):
     return float(np.real(np.vdot(a, b)))
 
 
-def ml_cg(obj, probe, data: Data, n, update_obj=True, update_probe=False):
+def ml_cg(obj, probe, data: Data, n, update_obj=True, update_probe=False, trace=None):
     """n steps of maximum-likelihood conjugate gradient on the Poisson LLK (the ML
     operator; Thibault & Guizar-Sicairos 2012; the paper's ML defaults update the
     object only).  Polak-Ribiere direction with beta = max(0, beta_PR) (0 at the
     first step); step alpha = -L'(0) / L''(0) from ``ml_line_coeffs`` (no step
-    when L''(0) <= 0).  Returns (obj, probe, [LLK before each step])."""
+    when L''(0) <= 0).  If ``trace`` is a list, each step appends a dict with its
+    start point, beta, search direction and alpha (for the tests).
+    Returns (obj, probe, [LLK before each step])."""
     obj = np.asarray(obj, dtype=np.complex128).copy()
     probe = np.asarray(probe, dtype=np.complex128).copy()
     g_prev = d = None
@@ -527,6 +529,9 @@ def ml_cg(obj, probe, data: Data, n, update_obj=True, update_probe=False):
             d = (-go + beta * d[0], -gp + beta * d[1])
         l1, l2 = ml_line_coeffs(obj, probe, d[0], d[1], data)
         alpha = -l1 / l2 if l2 > 0 else 0.0
+        if trace is not None:
+            trace.append({"obj": obj.copy(), "probe": probe.copy(), "beta": beta,
+                          "dir": (d[0].copy(), d[1].copy()), "alpha": alpha})
         obj = obj + alpha * d[0]
         probe = probe + alpha * d[1]
         g_prev = (go, gp)
