@@ -286,10 +286,12 @@ ptx_status ptx_profile_read(ptx_handle* h, int32_t nkinds, int64_t* launches, do
  * double.  No handle, no scratch argument: all working memory (copied
  * positions and mask, the Fourier work stack, the FP64 partial sums) lives in
  * one file-scope device array of PTX_STATIC_SCRATCH_BYTES (16 MiB) that every
- * GPU loading the library holds until the process exits.  The first call on
- * a device looks up that array's address with cudaGetSymbolAddress, clears its mask region
- * and synchronises the device once: make that first call before any stream
- * capture.  Sizes beyond the array (J > 65536, J * N / C > 65536 partial
+ * GPU loading the library holds until the process exits.  Every call looks
+ * up that array's address on the current device with cudaGetSymbolAddress
+ * (no synchronisation).  The first call that sees an address on a device (the
+ * first call there, or the first after a cudaDeviceReset reloaded the module)
+ * also clears the array's mask region and synchronises the device once: make
+ * that first call before any stream capture.  Sizes beyond the array (J > 65536, J * N / C > 65536 partial
  * sums with C columns per block of the column pass, or one frame's
  * K * N * N * 8-byte work stack larger than the array's
  * work region) are rejected with PTX_ERR_UNSUPPORTED and a message; nothing

@@ -151,10 +151,12 @@ __global__ void __launch_bounds__(256, 2) k_col_tc(ProbArgs a, int j0) {
     // this thread's D row: M-tile t / 128 at column 32 (t / 128), lane t % 128
     const uint32_t my_d = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (t >> 7));
     uint32_t parity = 0;
-    bool ok = true;
 
-    // one tensor-core DFT stage over the A tile: D = A B^T, B = matrix `m` (0 fwd, 1 inv)
-    auto stage = [&](int m, float* out) {
+    // one tensor-core DFT stage over the A tile: D = A B^T, B = matrix `m` (0 fwd, 1 inv).
+    // Every thread waits (bounded) for the stage's commit; the outcome is made
+    // block-uniform, so a give-up seen by any thread stops the whole block: no
+    // later stage issues MMAs, and the caller reports it and frees TMEM.
+    auto stage = [&](int m, float* out) -> bool {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
@@ -174,10 +176,12 @@ __global__ void __launch_bounds__(256, 2) k_col_tc(ProbArgs a, int j0) {
             }
             commit(bar);
         }
-        ok &= bar_wait(bar, parity);
+        const bool mine = bar_wait(bar, parity);
+        if (__syncthreads_or(!mine)) return false;  // parity stays at the pending phase
         parity ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         tmem_ld32(my_d, out);
+        return true;
     };
     // write this thread's 16 complex values as its own A row (hi, lo)
     auto put_row = [&](const float2* v) {
@@ -215,42 +219,49 @@ __global__ void __launch_bounds__(256, 2) k_col_tc(ProbArgs a, int j0) {
         for (int k1 = 0; k1 < 16; ++k1) io[k1] = __ldcs(ib + (size_t)16 * k1 * N);
     }
     const uint32_t mbits = a.mbits[blockIdx.x * 256 + t];
-    put_row(v);
-    stage(0, o);
-    // twiddle w^(n1 k2) and the transpose into the vectors (c, k2)
-#pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) {
-        const float2 y = make_float2(o[2 * k2], o[2 * k2 + 1]);
-        v[k2] = k2 == 0 ? y : cmul(y, tw_get<N, -1>(tw, k2, q));
-    }
-    // the A tile may be rewritten at once: the stage's MMAs have completed (mbarrier);
-    // the next stage's barrier orders every thread's D read before its MMAs
-    put_col(v, q);
-    stage(0, o);
-    // projection and LLK on X^[q + 16 k1] (thread = vector (c, k2 = q))
     constexpr float invN2 = 1.0f / float(N * N);
     KahanF llk;
-#pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) {
-        const float2 X = make_float2(o[2 * k1], o[2 * k1 + 1]);
-        const float ic = cnorm(X) * invN2;
-        const bool masked = (mbits >> k1) & 1u;
-        if (!masked) llk.add(llk_term_fast(ic, io[k1]));
-        const float f = masked ? 0.f : (amp_ratio(io[k1], ic) - 1.0f) * invN2;
-        v[k1] = cscale(X, f);
-    }
-    // inverse stage 1 over k1 on the thread's own vector, then twiddle w^(+k2 kk)
     put_row(v);
-    stage(1, o);
+    // `good` is block-uniform (each stage combines the threads' wait outcomes)
+    bool good = stage(0, o);
+    if (good) {
+        // twiddle w^(n1 k2) and the transpose into the vectors (c, k2)
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-        const float2 y = make_float2(o[2 * kk], o[2 * kk + 1]);
-        v[kk] = kk == 0 ? y : cmul(y, tw_get<N, +1>(tw, q, kk));
+        for (int k2 = 0; k2 < 16; ++k2) {
+            const float2 y = make_float2(o[2 * k2], o[2 * k2 + 1]);
+            v[k2] = k2 == 0 ? y : cmul(y, tw_get<N, -1>(tw, k2, q));
+        }
+        // the A tile may be rewritten at once: the stage's MMAs have completed (mbarrier);
+        // the next stage's barrier orders every thread's D read before its MMAs
+        put_col(v, q);
+        good = stage(0, o);
     }
-    put_col(v, q);
-    stage(1, o);
-    // rows kk + 16 k1' of column c (thread = vector (c, kk = q))
-    {
+    if (good) {
+        // projection and LLK on X^[q + 16 k1] (thread = vector (c, k2 = q))
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) {
+            const float2 X = make_float2(o[2 * k1], o[2 * k1 + 1]);
+            const float ic = cnorm(X) * invN2;
+            const bool masked = (mbits >> k1) & 1u;
+            if (!masked) llk.add(llk_term_fast(ic, io[k1]));
+            const float f = masked ? 0.f : (amp_ratio(io[k1], ic) - 1.0f) * invN2;
+            v[k1] = cscale(X, f);
+        }
+        // inverse stage 1 over k1 on the thread's own vector, then twiddle w^(+k2 kk)
+        put_row(v);
+        good = stage(1, o);
+    }
+    if (good) {
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            const float2 y = make_float2(o[2 * kk], o[2 * kk + 1]);
+            v[kk] = kk == 0 ? y : cmul(y, tw_get<N, +1>(tw, q, kk));
+        }
+        put_col(v, q);
+        good = stage(1, o);
+    }
+    if (good) {
+        // rows kk + 16 k1' of column c (thread = vector (c, kk = q))
         const uint64_t el = policy_evict_last();
 #pragma unroll
         for (int k1 = 0; k1 < 16; ++k1)
@@ -259,9 +270,14 @@ __global__ void __launch_bounds__(256, 2) k_col_tc(ProbArgs a, int j0) {
     const double tot = block_sum_double<256>(llk.value(), red_s);
     if (t == 0) {
         a.llk_part[(size_t)j * gridDim.x + blockIdx.x] = tot;
-        if (!ok && a.err_flag) {
-            *(volatile int*)a.err_flag = 1;
-            __threadfence_system();
+        if (!good) {
+            // a stage's commit did not arrive in time: wait once more (bounded) for
+            // the MMAs in flight before TMEM is freed, and report the give-up
+            bar_wait(bar, parity);
+            if (a.err_flag) {
+                *(volatile int*)a.err_flag = 1;
+                __threadfence_system();
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -12,10 +12,13 @@
 // The working memory is the file-scope array g_llk_scratch below
 // (kStaticScratchBytes = 16 MiB); every GPU that loads the library holds it
 // until the process exits.  Host code cannot use the array's name as a device
-// address, so the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current), clears the mask region of
-// the array, and caches the address; that first call synchronises the device
-// once and must therefore come before any stream capture.  All calls share the
+// address, so every call looks the address up with cudaGetSymbolAddress (with
+// the caller's device current; the lookup does not synchronise).  The first
+// call that sees a given address on a device (the first call on the device, or
+// the first after a cudaDeviceReset that reloaded the module) also clears the
+// mask region of the array and sets the kernels' attributes; that call
+// synchronises the device once and must therefore come before any stream
+// capture.  All calls share the
 // array and it keeps the last call's contents: each call rewrites every byte
 // it reads (positions, mask, Fourier work stack, partial sums) before reading
 // it, so calls that run one after the other are independent, but calls that
@@ -68,7 +71,7 @@ static_assert(kSpecOff < kStaticScratchBytes, "work stack region must exist");
 __device__ __align__(256) unsigned char g_llk_scratch[kStaticScratchBytes];
 
 std::mutex g_setup_mutex;
-void* g_addr[64] = {};  // device address of g_llk_scratch per device ordinal
+void* g_ready[64] = {};  // per device ordinal: the address whose one-time set-up is done
 
 ptx_status fail(ptx_status st, const char* fmt, ...) {
     char buf[512];
@@ -80,16 +83,17 @@ ptx_status fail(ptx_status st, const char* fmt, ...) {
     return st;
 }
 
-// First call on a device: address of the array, cleared mask region, kernel attributes.
+// Every call: the array's device address on the current device.  The first
+// call that sees that address: cleared mask region, kernel attributes.
 ptx_status setup_device(int dev, unsigned char** out) {
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (g_addr[dev]) {
-        *out = (unsigned char*)g_addr[dev];
-        return PTX_OK;
-    }
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_llk_scratch);
     if (e != cudaSuccess) return fail(PTX_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (g_ready[dev] == ptr) {
+        *out = (unsigned char*)ptr;
+        return PTX_OK;
+    }
     cudaError_t (*attrs[])() = {ptx::set_attrs_8,   ptx::set_attrs_12,  ptx::set_attrs_16,  ptx::set_attrs_32,
                                 ptx::set_attrs_64,  ptx::set_attrs_128, ptx::set_attrs_192, ptx::set_attrs_256,
                                 ptx::set_attrs_384, ptx::set_attrs_512, ptx::set_attrs_80,  ptx::set_attrs_160,
@@ -99,7 +103,7 @@ ptx_status setup_device(int dev, unsigned char** out) {
     if ((e = cudaMemset((char*)ptr + kMaskOff, 0, kMaskBytes)) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess)
         return fail(PTX_ERR_CUDA, "clearing the static scratch: %s", cudaGetErrorString(e));
-    g_addr[dev] = ptr;
+    g_ready[dev] = ptr;
     *out = (unsigned char*)ptr;
     return PTX_OK;
 }

@@ -5,7 +5,9 @@ that owns all device memory, or a loop that must not enter an allocator) get
 the exact Poisson LLK from ptx_llk_static, whose working memory is a fixed
 file-scope device array.  It must agree with the handle-based ptx_llk (same
 kernels, so to within the 1e-5 relative tolerance of the other GPU tests and in
-practice exactly), including on a second call in a row that reuses the array.
+practice exactly), including on a second call in a row that reuses the array,
+and with the FP64 oracle's LLK.  A masked call followed by an unmasked one must
+not see the first call's mask (the array keeps the last call's contents).
 This file is collected last on purpose.
 """
 import ctypes
@@ -13,6 +15,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from synthetic import make_config
 
 torch = pytest.importorskip("torch")
@@ -81,3 +84,48 @@ def test_static_llk_rejects_sizes_beyond_its_array(lib):
     assert _static_llk(lib, wide, obj, probe, iobs, out) == 2
     assert b"static scratch" in lib.ptx_last_error()
     assert _static_llk(lib, s, obj, probe, iobs, out) == 0
+
+
+def _warm(cfg, J, **over):
+    """The oracle's state after one AP cycle from the configured start (where the
+    single-precision far field resolves the whole detector), as complex64."""
+    s = make_config(cfg, J=J, **over)
+    o, p, _ = oracle.ap_cycle(s.obj0, s.probe0, oracle.Data.make(s.iobs, s.positions, s.mask))
+    return s, o.astype(np.complex64), p.astype(np.complex64)
+
+
+def test_static_llk_matches_the_oracle(lib):
+    s, o, p = _warm("ap64", 100, mask_fraction=0.03)
+    assert s.mask.any()
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    obj, probe, iobs = _dev(o), _dev(p), _dev(s.iobs)
+    for i in range(2):
+        assert _static_llk(lib, s, obj, probe, iobs, out[i:i + 1]) == 0, lib.ptx_last_error()
+    ref = oracle.llk(o, p, oracle.Data.make(s.iobs, s.positions, s.mask))
+    got = out.cpu().numpy()
+    assert abs(got[0] - ref) <= TOL1 * abs(ref) and abs(got[1] - ref) <= TOL1 * abs(ref), (got, ref)
+
+
+def test_static_llk_masked_then_unmasked_call(lib):
+    """The second, unmasked call in the same stream must see no mask: the masked
+    call clears its mask region of the shared array behind it."""
+    from paper_2008_11511_gb300 import Ptycho
+    s, o, p = _warm("ap64", 60, mask_fraction=0.05)
+    assert s.mask.any()
+    obj, probe, iobs = _dev(o), _dev(p), _dev(s.iobs)
+    nomask = make_config("ap64", J=60, mask_fraction=0.05)
+    nomask.mask = np.zeros_like(s.mask)
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    assert _static_llk(lib, s, obj, probe, iobs, out[0:1]) == 0, lib.ptx_last_error()
+    assert _static_llk(lib, nomask, obj, probe, iobs, out[1:2]) == 0, lib.ptx_last_error()
+    got = out.cpu().numpy()
+    pb_m = Ptycho(obj, probe, iobs, s.positions, s.mask, with_psi=False)
+    pb_u = Ptycho(obj, probe, iobs, s.positions, None, with_psi=False)
+    ref_m, ref_u = float(pb_m.llk()), float(pb_u.llk())
+    pb_m.close()
+    pb_u.close()
+    assert abs(ref_u - ref_m) > 1e-3 * abs(ref_u)  # the mask matters on this case
+    assert abs(got[0] - ref_m) <= TOL1 * abs(ref_m), (got, ref_m)
+    assert abs(got[1] - ref_u) <= TOL1 * abs(ref_u), (got, ref_u)
+    ref_o = oracle.llk(o, p, oracle.Data.make(s.iobs, s.positions, None))
+    assert abs(got[1] - ref_o) <= TOL1 * abs(ref_o), (got, ref_o)
