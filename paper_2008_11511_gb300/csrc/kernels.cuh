@@ -155,6 +155,28 @@ __device__ __forceinline__ float llk_term_fast(float ic, float io) {
     return io > 0.f ? io * f : ic;
 }
 
+// The LLK term of llk_term_fast and, from the same quotient, the amplitude
+// factor sqrt(max(io, 0) / max(ic, 1e-30)) of the projection: with
+// q = max(ic, 1e-30) / io (= 1 + u), the factor is rsqrt(q), one reciprocal
+// square root (0 where io <= 0).  Where the oracle's floor differs
+// (ic < 1e-30) the model wave is below 1e-15 in modulus and the projected
+// value rounds to the same result.
+__device__ __forceinline__ float llk_term_ratio(float ic, float io, float& ratio) {
+    const float icf = fmaxf(ic, 1e-30f);
+    const float rio = __fdividef(1.0f, io);
+    const float u = (icf - io) * rio;
+    const float t = __fdividef(u, 2.0f + u);
+    const float t2 = t * t;
+    const float poly = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, 1.f / 15.f, 1.f / 13.f), 1.f / 11.f),
+                                                       1.f / 9.f), 1.f / 7.f), 1.f / 5.f), 1.f / 3.f);
+    const float fs = fmaf(u, t, -2.0f * t * t2 * poly);
+    const float q = icf * rio;
+    const float fl = u - __logf(q);
+    const float f = (u > -0.5f && u < 1.0f) ? fs : fl;
+    ratio = io > 0.f ? rsqrtf(q) : 0.f;
+    return io > 0.f ? io * f : ic;
+}
+
 // sqrt(max(io, 0)) / max(sqrt(ic), 1e-20): the amplitude-projection factor, with
 // reciprocal square roots (<= 2 ulp each); ic below 1e-40 keeps the floor.
 __device__ __forceinline__ float amp_ratio(float io, float ic) {
@@ -187,6 +209,25 @@ __device__ __forceinline__ double block_sum_double(double v, double* red_smem) {
         r = (threadIdx.x < T / 32) ? red_smem[threadIdx.x] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    return r;  // valid in thread 0
+}
+
+// Block sum of per-thread partial sums that are >= 0 (LLK terms): a tree of
+// warp shuffles in FP32 (five levels, relative error <= 5 u on top of the
+// threads' own sums), then the warps' sums in FP64 by thread 0.  Leaves the
+// FP64 pipe almost idle (one conversion per warp, T / 32 additions).
+template <int T>
+__device__ __forceinline__ double block_sum_pos(float v, double* red_smem) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red_smem[warp] = (double)v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int w = 0; w < T / 32; ++w) r += red_smem[w];
     }
     return r;  // valid in thread 0
 }

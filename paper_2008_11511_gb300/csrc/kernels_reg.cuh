@@ -235,14 +235,15 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(P
                     ic += __ldg(a.bg + pix);
                     if (a.bg_acc && !masked) atomicAdd(a.bg_acc + pix, fmaxf(io, 0.f) / fmaxf(ic, 1e-30f));
                 }
-                if (!masked) llk += llk_term_fast(ic, io);
                 float f;
-                if (masked) {
-                    f = 0.f;
-                } else if (mode == COL_PROJECT) {
-                    f = (amp_ratio(io, ic) - 1.0f) * invN2;
+                if (mode == COL_PROJECT) {
+                    float ratio;
+                    const float term = llk_term_ratio(ic, io, ratio);
+                    if (!masked) llk += term;
+                    f = masked ? 0.f : (ratio - 1.0f) * invN2;
                 } else {
-                    f = 2.0f * (1.0f - __fdividef(fmaxf(io, 0.f), fmaxf(ic, 1e-30f))) * invN2;
+                    if (!masked) llk += llk_term_fast(ic, io);
+                    f = masked ? 0.f : 2.0f * (1.0f - __fdividef(fmaxf(io, 0.f), fmaxf(ic, 1e-30f))) * invN2;
                 }
                 u[i][k1] = cscale(u[i][k1], f);
             }
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(P
             }
         }
     }
-    double tot = block_sum_double<kThreads>((double)llk, red_s);
+    double tot = block_sum_pos<kThreads>(llk, red_s);
     if (threadIdx.x == 0) a.llk_part[(size_t)j * gridDim.x + blockIdx.x] = tot;
     if (mode == COL_LLK) return;
     __syncthreads();
@@ -385,19 +386,21 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_mod
                     ic += __ldg(bgp + pix);
                     if (a.bg_acc && !masked) atomicAdd(a.bg_acc + pix, fmaxf(io, 0.f) / fmaxf(ic, 1e-30f));
                 }
-                if (!masked) llk += llk_term_fast(ic, io);
                 float f;
-                if (masked)
-                    f = 0.f;
-                else if (mode == COL_PROJECT)
-                    f = (amp_ratio(io, ic) - 1.0f) * invN2;
-                else
-                    f = 2.0f * (1.0f - __fdividef(fmaxf(io, 0.f), fmaxf(ic, 1e-30f))) * invN2;
+                if (mode == COL_PROJECT) {
+                    float ratio;
+                    const float term = llk_term_ratio(ic, io, ratio);
+                    if (!masked) llk += term;
+                    f = masked ? 0.f : (ratio - 1.0f) * invN2;
+                } else {
+                    if (!masked) llk += llk_term_fast(ic, io);
+                    f = masked ? 0.f : 2.0f * (1.0f - __fdividef(fmaxf(io, 0.f), fmaxf(ic, 1e-30f))) * invN2;
+                }
                 ic_r[i][k1] = f;
             }
         }
     }
-    const double tot = block_sum_double<kThreads>((double)llk, red_s);
+    const double tot = block_sum_pos<kThreads>(llk, red_s);
     if (threadIdx.x == 0) a.llk_part[(size_t)j * gridDim.x + blockIdx.x] = tot;
     if (mode == COL_LLK) return;
     // sweep 2: scale and inverse transforms
