@@ -335,6 +335,84 @@ def run_e2e(args, s, pb, obj, probe, iobs, params, llk_buf, stream, dev, ws):
     return s.J * e_steps * ws / el, host.numel() * host.element_size(), desc
 
 
+def _events_ms(fn, n, stream):
+    """Median over n calls of fn() timed with CUDA events on `stream` (ms per call)."""
+    import torch
+    out = []
+    for _ in range(n):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return statistics.median(out)
+
+
+def run_extra_ml(dev, fma_peak, ws):
+    """The ML workload (1000 frames of 256^2, object 1536^2): the Poisson-LLK
+    gradient and one conjugate-gradient step, against the FP32 ALU roof (the
+    gradient moves 0.3 GB but transforms every frame twice)."""
+    import torch
+    from paper_2008_11511_gb300 import Ptycho
+    from synthetic import make_config
+    s = make_config("ml256")
+    obj = torch.tensor(s.obj0, device=dev)
+    probe = torch.tensor(s.probe0, device=dev)
+    iobs = torch.tensor(s.iobs, device=dev)
+    pb = Ptycho(obj, probe, iobs, s.positions, s.mask, with_psi=False)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        pb.ml_grad()
+        pb.ml(1)
+    torch.cuda.synchronize(dev)
+    ms_g = _events_ms(lambda: pb.ml_grad(), 10, stream)
+    ms_cg = _events_ms(lambda: pb.ml(1), 10, stream)
+    pb.close()
+    m = kernel_models(s)
+    # the gradient: forward transform and back-propagation of every frame
+    flops = s.J * (m["row_fwd"]["flops"] + m["col"]["flops"] + m["row_bwd"]["flops"])
+    tf = flops / (ms_g * 1e-3) / 1e12
+    return {"workload": f"ML gradient and CG step, {s.J} frames {s.N}x{s.N}, object {s.Ho}x{s.Wo}, "
+                        f"{s.photons:.0e} photons/frame",
+            "ms_per_gradient": ms_g, "gradient_frames_per_s": s.J * ws / (ms_g * 1e-3),
+            "ms_per_cg_step": ms_cg, "cg_frames_per_s": s.J * ws / (ms_cg * 1e-3),
+            "roofline": {"kernel": "gradient (three passes)", "bound": "alu", "achieved": tf, "peak": fma_peak,
+                         "unit": "TFLOP/s", "frac": tf / fma_peak, "flops_per_gradient": flops,
+                         "peak_src": "measured FP32 FMA probe"}}
+
+
+def run_extra_modes(dev, pk, ws, J=1500, H=2800):
+    """Three incoherent probe modes of 512^2 (the multi-mode workload, on its
+    first 1500 positions and a 2800^2 object that covers them): DM cycles
+    against the HBM roof on the scope table's bytes."""
+    import torch
+    from paper_2008_11511_gb300 import Ptycho
+    from synthetic import make_config
+    s = make_config("modes512", J=J, Ho=H, Wo=H)
+    obj = torch.tensor(s.obj0, device=dev)
+    probe = torch.tensor(s.probe0, device=dev)
+    iobs = torch.tensor(s.iobs, device=dev)
+    pb = Ptycho(obj, probe, iobs, s.positions, s.mask, with_psi=True)
+    stream = torch.cuda.current_stream(dev)
+    llk = torch.empty(8, dtype=torch.float64, device=dev)
+    pb.dm(2, init_psi=True, llk=llk)
+    pb.dm(2, llk=llk)
+    torch.cuda.synchronize(dev)
+    ms = _events_ms(lambda: pb.dm(3, llk=llk), 3, stream) / 3
+    pb.close()
+    px = s.N * s.N
+    b = s.J * s.K * px * 16 + s.J * px * 4 + s.Ho * s.Wo * 16 + s.K * px * 16
+    gbs = b / (ms * 1e-3) / 1e9
+    return {"workload": f"DM cycle, {s.J} frames {s.N}x{s.N}, K={s.K} modes, object {s.Ho}x{s.Wo}, "
+                        f"{s.photons:.0e} photons/frame (first {J} positions of the 10000-position scan)",
+            "ms_per_cycle": ms, "frames_per_s": s.J * ws / (ms * 1e-3),
+            "frame_modes_per_s": s.J * s.K * ws / (ms * 1e-3),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs / pk["hbm_gbs"], "alg_bytes_per_cycle": b, "peak_src": pk["src"]}}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_init()
@@ -367,30 +445,40 @@ def run_ours(args):
     pb.dm(args.warmup, init_psi=True, llk=llk_buf)
     pb.dm(1, llk=llk_buf)
     torch.cuda.synchronize(dev)
+    import ctypes
+    nk = ctypes.c_int64()
+    _lib.call("ptx_cycle_kernels", pb._handle(), _lib.PTX_ALGO_DM, _lib.PTX_UPDATE_OBJ | _lib.PTX_UPDATE_PROBE,
+              ctypes.byref(nk))
+    cycle_kernels = int(nk.value)
 
-    # timed region: K DM cycles (inputs ~3 GB >> 129 MB L2, so no flush is needed)
+    # timed region: K DM cycles (inputs ~3 GB >> 129 MB L2, so no flush is needed),
+    # repeated; each repeat is bracketed by a barrier and a synchronise, the
+    # max over ranks is taken per repeat and the median of the repeats reported
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    barrier(ws)
-    torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    pb.dm(args.steps, llk=llk_buf)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    barrier(ws)
+    rep_ms = []
+    for _ in range(max(1, args.repeats)):
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pb.dm(args.steps, llk=llk_buf)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(ws)
+        rep_ms.append(max_over_ranks(e0.elapsed_time(e1), ws))
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    ms_max = max_over_ranks(ms, ws)
+    ms_max = statistics.median(rep_ms)
     value = s.J * args.steps * ws / (ms_max / 1e3)
     ms_per_step = ms_max / args.steps
 
     if args.timing_only:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms_per_step,
-                              "frames": s.J, "steps": args.steps, "timing_only": True}), flush=True)
+                              "frames": s.J, "steps": args.steps, "repeats_ms": rep_ms, "timing_only": True}),
+                  flush=True)
         pb.close()
         return
 
@@ -421,7 +509,6 @@ def run_ours(args):
     _lib.call("ptx_profile_enable", pb._handle(), 1)
     pb.dm(args.steps, llk=llk_buf)
     torch.cuda.synchronize(dev)
-    import ctypes
     nk = len(_lib.KERNEL_KINDS)
     launches = (ctypes.c_int64 * nk)()
     tot = (ctypes.c_double * nk)()
@@ -438,7 +525,9 @@ def run_ours(args):
     # intensity stack in from pinned host memory and reads the cycle's LLK back.
     e2e_value, e2e_bytes, e2e_copies = run_e2e(args, s, pb, obj, probe, iobs, params, llk_buf, stream, dev, ws)
 
-    # roofline: the dominant kernel by time share
+    # roofline: the dominant kernel by time share, against the measured FMA peak
+    from paper_2008_11511_gb300 import fma_tflops
+    fma_peak = fma_tflops(dev)
     pk = peaks()
     models = kernel_models(s)
     dom = max(("row_fwd", "col", "row_bwd", "obj_gather"), key=lambda k: kstats[k]["total_ms"])
@@ -452,23 +541,34 @@ def run_ours(args):
                 "alg_bytes_per_launch": models[dom]["bytes"] * nframes_per_launch, "traffic": traffic}
     else:
         flops = models[dom]["flops"] * nframes_per_launch
-        alu_peak_tflops = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+        alu_derived = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
         achieved_tflops = flops / (ks["avg_us"] * 1e-6) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved_tflops, "peak": alu_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved_tflops / alu_peak_tflops,
-                "peak_src": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock (derived)",
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved_tflops, "peak": fma_peak,
+                "unit": "TFLOP/s", "frac": achieved_tflops / fma_peak,
+                "peak_src": "measured: FP32 FMA probe (ptx_fma_peak) on this GPU, best of 3",
+                "peak_derived": alu_derived, "frac_of_derived": achieved_tflops / alu_derived,
                 "flops_per_launch": flops, "alg_bytes_per_launch": models[dom]["bytes"] * nframes_per_launch,
                 "traffic": traffic}
-    cyc_bytes = alg_bytes_per_cycle(s, "DM")
-    cyc_gbs = cyc_bytes / (ms_per_step * 1e-3) / 1e9
-    # the same roof with the bytes of a single-pass (simultaneous) overlap update,
-    # which never re-reads Psi': J K px 16 + J px 4 + Ho Wo 16 + K px 16
+    # the cycle against the HBM roof, on the scope table's algorithmic bytes:
+    # J K px 16 (Psi read + written) + J px 4 (I) + Ho Wo 16 (O) + K px 16 (P);
+    # beside it the bytes of this design, whose object update re-reads Psi'
     px = s.N * s.N
     single = s.J * s.K * px * 16 + s.J * px * 4 + s.Ho * s.Wo * 16 + s.K * px * 16
+    cyc_gbs = single / (ms_per_step * 1e-3) / 1e9
+    cyc_bytes = alg_bytes_per_cycle(s, "DM")
     roof_cycle = {"bound": "hbm", "achieved": cyc_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                  "frac": cyc_gbs / pk["hbm_gbs"], "peak_src": pk["src"], "alg_bytes_per_cycle": cyc_bytes,
-                  "frac_single_pass_bytes": single / (ms_per_step * 1e-3) / 1e9 / pk["hbm_gbs"],
-                  "alg_bytes_single_pass": single}
+                  "frac": cyc_gbs / pk["hbm_gbs"], "peak_src": pk["src"], "alg_bytes_per_cycle": single,
+                  "bytes_src": "J K px 16 + J px 4 + Ho Wo 16 + K px 16 (Psi read and written once)",
+                  "with_psi_reread": {"alg_bytes_per_cycle": cyc_bytes,
+                                      "frac": cyc_bytes / (ms_per_step * 1e-3) / 1e9 / pk["hbm_gbs"]}}
+
+    extras = None
+    if not args.no_extras:
+        pb.close()
+        del pb
+        torch.cuda.synchronize(dev)
+        extras = {"ml256": run_extra_ml(dev, fma_peak, ws), "modes512": run_extra_modes(dev, pk, ws)}
+        pb = None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -476,7 +576,9 @@ def run_ours(args):
         cpu = {"value": rate, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
                "sample": f"one FP64 DM cycle on {J} of {s.J} frames (evenly spaced), full object; {dt:.1f} s"}
 
-    gpu_launches = sum(v["launches"] for v in kstats.values()) + 1  # + the per-call control kernel
+    # kernels in the timed region: per repeat, `steps` replays of the cycle graph
+    # (its kernel nodes, counted by the library) and the per-call control kernel
+    gpu_launches = len(rep_ms) * (args.steps * cycle_kernels + 1)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -485,12 +587,14 @@ def run_ours(args):
                            "parallelism": f"replicas x{ws}",
                            "l2": "inputs larger than L2 (Psi 2.1 GB + I 1.05 GB per replica); no flush"},
                 "roofline": roof, "roofline_cycle": roof_cycle, "kernels": kstats, "other_form": other,
+                "repeats_ms": rep_ms, "fma_peak_tflops": fma_peak, "extra": extras,
                 "clocks": clk, "gpu_launches": gpu_launches,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(e2e_bytes),
                         "d2h_bytes_per_step": 8, "steps": max(1, min(args.steps, 10)), "copies": e2e_copies},
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
-    pb.close()
+    if pb is not None:
+        pb.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -522,6 +626,10 @@ def main():
                     help="the split-precision form: column-pass DFT stages on the tensor cores (TF32 hi + lo)")
     ap.add_argument("--batch-frames", type=int, default=0,
                     help="upper bound on frames per batch (library default when 0)")
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="timed repeats of the K-step region (the median is reported)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the secondary workloads (ML gradient and CG step, three-mode 512^2 DM cycle)")
     ap.add_argument("--timing-only", action="store_true",
                     help="stop after the timed region (no per-kernel pass, e2e or CPU baseline)")
     args = ap.parse_args()

@@ -324,6 +324,41 @@ ptx_status ptx_counts_to_float(float* dst, const uint16_t* src, size_t n, void* 
  * memory was unavailable at create). */
 ptx_status ptx_wait_selftest(ptx_handle* h, int32_t limit_us, void* stream);
 
+/* Number of kernel launches in one cycle of `algorithm` (PTX_ALGO_AP or
+ * PTX_ALGO_DM, for every problem of the handle) with the cycle flags `flags`,
+ * as the cycle's captured CUDA graph holds them (the graph is captured now if
+ * it was not yet; call outside any stream capture).  A ptx_ap_cycles /
+ * ptx_dm_cycles call adds one control kernel per call.  *count receives the
+ * number (host).  PTX_ERR_INVALID_ARG for a null pointer or an unknown
+ * algorithm. */
+ptx_status ptx_cycle_kernels(ptx_handle* h, int32_t algorithm, uint32_t flags, int64_t* count);
+
+/* FP32 fused multiply-add throughput probe (no counterpart in the paper; it
+ * measures the ALU roof the FFT passes are compared against).  Enqueues
+ * `blocks` blocks of 256 threads, each thread running `iters` rounds of 16
+ * independent FMA chains, and writes one float per thread to `sink` (device
+ * float32 [blocks * 256], caller-owned).  *flops (host) receives the floating-
+ * point operations the launch performs (2 per FMA); time the launch with
+ * events on `stream` and divide.  PTX_ERR_INVALID_ARG for blocks or iters < 1
+ * or a null pointer. */
+ptx_status ptx_fma_peak(int32_t blocks, int32_t iters, float* sink, double* flops, void* stream);
+
+/* Position refinement, host step (paper Section 4: position refinement after
+ * Odstrcil et al. 2018): the per-frame shifts of ptx_position_shifts (copied
+ * to the host) accumulate into sub-pixel positions and frames move when their
+ * rounded position changes.  For each frame j and axis a (row, col):
+ *   pos_subpixel[j][a] = clip(pos_subpixel[j][a] + clip(step * shifts[j][a],
+ *                             -max_shift, max_shift), 0, max_a)
+ *   positions[j][a]    = nearest integer to pos_subpixel[j][a] (halves to even)
+ * with max_row = Ho - N, max_col = Wo - N.  shifts: host float32 [J][2];
+ * pos_subpixel: host float64 [J][2], in / out; positions: host int32 [J][2],
+ * in (current) / out (new); *moved receives the number of frames whose integer
+ * position changed (pass `positions` to ptx_set_positions when it is > 0).
+ * Host only: touches no device memory and enqueues nothing.
+ * PTX_ERR_INVALID_ARG for J < 0, a null pointer, or a negative bound. */
+ptx_status ptx_accumulate_shifts(int32_t J, const float* shifts, double step, double max_shift, int32_t max_row,
+                                 int32_t max_col, double* pos_subpixel, int32_t* positions, int32_t* moved);
+
 /* Text of the last failure on the calling thread ("" if none). */
 const char* ptx_last_error(void);
 

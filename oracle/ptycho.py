@@ -387,6 +387,21 @@ def position_shifts(obj, probe, psi, positions, filter_ratio=0.1):
     return out
 
 
+def refine_positions_step(pos_subpixel, shifts, step, max_shift, max_row, max_col):
+    """The host step of position refinement (paper Section 4, after Odstrcil et
+    al. 2018; positions stay integer inside the cycle): each frame's shift,
+    scaled by ``step`` and clipped to [-max_shift, max_shift] pixels per axis,
+    is added to its sub-pixel position, which is kept inside [0, max_row] x
+    [0, max_col] (max_row = Ho - N, max_col = Wo - N); the frame's integer
+    position is the nearest integer, halves to even.
+    Returns (sub-pixel positions float64 (J, 2), integer positions int64 (J, 2))."""
+    pos = np.asarray(pos_subpixel, dtype=np.float64)
+    d = np.clip(step * np.asarray(shifts, dtype=np.float64), -max_shift, max_shift)
+    hi = np.array([max_row, max_col], dtype=np.float64)
+    new = np.clip(pos + d, 0.0, hi)
+    return new, np.rint(new).astype(np.int64)
+
+
 def dm_cycle(obj, probe, psi, data: Data, alpha_obj=1e-2, alpha_probe=1e-2,
              update_obj=True, update_probe=True, init_psi=False):
     """One Difference Map cycle (beta = 1; Elser 2007, Thibault et al. 2008):
@@ -603,7 +618,7 @@ __all__ = [
     "normalise", "overlap_update", "ap_cycle", "dm_cycle", "llk", "ml_grad",
     "cycles", "dm_frame_update", "frames_llk", "object_denominator", "frames_covering", "ml_line_coeffs", "ml_cg",
     "ap_cycle_background", "near_field_transfer", "propagate_near_field", "object_gradient", "position_shifts",
-    "ICALC_FLOOR", "AMP_FLOOR", "STACK",
+    "refine_positions_step", "ICALC_FLOOR", "AMP_FLOOR", "STACK",
 ]
 
 

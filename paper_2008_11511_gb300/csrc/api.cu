@@ -5,6 +5,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -439,6 +440,7 @@ struct ptx_handle {
     int device = 0;
     cudaStream_t cap_stream = nullptr;
     std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::map<GraphKey, int64_t> graph_kernels;  // kernel nodes of each captured cycle
     // batch lanes: extra streams and fork / join events (lane 0 is the call's stream)
     int lanes = kDefaultLanes;
     int batch_cap = 0;  // ptx_set_param "batch_frames"
@@ -770,6 +772,19 @@ ptx_status get_graph(ptx_handle* h, const std::vector<int>& algos, uint32_t flag
         return st;
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    {
+        size_t n = 0;
+        int64_t nk = 0;
+        if (cudaGraphGetNodes(g, nullptr, &n) == cudaSuccess && n > 0) {
+            std::vector<cudaGraphNode_t> nodes(n);
+            if (cudaGraphGetNodes(g, nodes.data(), &n) == cudaSuccess)
+                for (size_t i = 0; i < n; ++i) {
+                    cudaGraphNodeType t;
+                    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+                }
+        }
+        h->graph_kernels[key] = nk;
+    }
     cudaGraphExec_t ex = nullptr;
     e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
@@ -782,6 +797,7 @@ ptx_status get_graph(ptx_handle* h, const std::vector<int>& algos, uint32_t flag
 void drop_graphs(ptx_handle* h) {
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
+    h->graph_kernels.clear();
 }
 
 ptx_status check_device(ptx_handle* h) {
@@ -968,6 +984,22 @@ ptx_status ptx_ap_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, double*
 ptx_status ptx_dm_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, double* llk_dev, void* stream) {
     if (!h) return fail(PTX_ERR_INVALID_ARG, "null handle");
     return run_cycles(h, std::vector<int>(h->probs.size(), ALGO_DM), ncycles, flags, llk_dev, stream);
+}
+
+ptx_status ptx_cycle_kernels(ptx_handle* h, int32_t algorithm, uint32_t flags, int64_t* count) {
+    if (!h || !count) return fail(PTX_ERR_INVALID_ARG, "null handle or count");
+    if (algorithm != ALGO_AP && algorithm != ALGO_DM) return fail(PTX_ERR_INVALID_ARG, "algorithm %d", algorithm);
+    ptx_status st = check_device(h);
+    if (st != PTX_OK) return st;
+    const uint32_t f = flags & (PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_NO_NORMALISE | PTX_UPDATE_BACKGROUND |
+                                PTX_DM_INIT_PSI);
+    const std::vector<int> algos(h->probs.size(), algorithm);
+    cudaGraphExec_t ex;
+    if ((st = get_graph(h, algos, f, &ex)) != PTX_OK) return st;
+    GraphKey key{algos, f, h->lanes, h->tma | (h->tma_gather << 1) | (h->tc << 2)};
+    auto it = h->graph_kernels.find(key);
+    *count = it == h->graph_kernels.end() ? 0 : it->second;
+    return PTX_OK;
 }
 
 ptx_status ptx_cycles(ptx_handle* h, int32_t ncycles, uint32_t flags, const int32_t* algorithms, double* llk_dev,
@@ -1239,6 +1271,40 @@ ptx_status ptx_counts_to_float(float* dst, const uint16_t* src, size_t n, void* 
     k_counts_to_float<<<4 * 152, 256, 0, (cudaStream_t)stream>>>(src, dst, n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "ptx_counts_to_float launch");
+    return PTX_OK;
+}
+
+ptx_status ptx_fma_peak(int32_t blocks, int32_t iters, float* sink, double* flops, void* stream) {
+    if (blocks < 1 || iters < 1 || !sink || !flops)
+        return fail(PTX_ERR_INVALID_ARG, "blocks and iters must be >= 1, sink and flops non-null");
+    *flops = 32.0 * 256.0 * (double)blocks * (double)iters;
+    k_fma_peak<<<blocks, 256, 0, (cudaStream_t)stream>>>(sink, iters, 0.999999f, 1e-6f);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ptx_fma_peak launch");
+    return PTX_OK;
+}
+
+ptx_status ptx_accumulate_shifts(int32_t J, const float* shifts, double step, double max_shift, int32_t max_row,
+                                 int32_t max_col, double* pos_subpixel, int32_t* positions, int32_t* moved) {
+    if (J < 0 || !moved || (J > 0 && (!shifts || !pos_subpixel || !positions)))
+        return fail(PTX_ERR_INVALID_ARG, "J >= 0 and non-null arrays needed");
+    if (!(max_shift >= 0.0) || max_row < 0 || max_col < 0)
+        return fail(PTX_ERR_INVALID_ARG, "max_shift, max_row and max_col must be >= 0");
+    const double hi[2] = {(double)max_row, (double)max_col};
+    int32_t n = 0;
+    for (int32_t j = 0; j < J; ++j) {
+        bool changed = false;
+        for (int a = 0; a < 2; ++a) {
+            const double d = std::min(std::max(step * (double)shifts[2 * j + a], -max_shift), max_shift);
+            const double v = std::min(std::max(pos_subpixel[2 * j + a] + d, 0.0), hi[a]);
+            pos_subpixel[2 * j + a] = v;
+            const int32_t r = (int32_t)std::nearbyint(v);  // round half to even (default rounding mode)
+            changed |= r != positions[2 * j + a];
+            positions[2 * j + a] = r;
+        }
+        n += changed ? 1 : 0;
+    }
+    *moved = n;
     return PTX_OK;
 }
 

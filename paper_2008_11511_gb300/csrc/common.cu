@@ -225,6 +225,24 @@ __global__ void k_wait_selftest(int* err_flag, unsigned long long limit_ns) {
     }
 }
 
+// FP32 FMA throughput probe: every thread runs `iters` rounds of 16 independent
+// FMA chains (32 flop per round), enough independent work per warp to keep the
+// FMA pipes issuing every cycle.  The chains' sum goes to sink[thread] so that
+// nothing is dropped by the compiler; a, b keep the values bounded.
+__global__ void __launch_bounds__(256) k_fma_peak(float* __restrict__ sink, int iters, float a, float b) {
+    float x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = (float)(threadIdx.x + i) * 1e-3f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = fmaf(x[i], a, b);
+    }
+    float t = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) t += x[i];
+    sink[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
 // Photon counts (uint16) to the float32 intensities the passes read: 8 counts
 // (16 bytes) per thread and step, exact (every uint16 is a float32 integer).
 __global__ void k_counts_to_float(const uint16_t* __restrict__ src, float* __restrict__ dst, size_t n) {

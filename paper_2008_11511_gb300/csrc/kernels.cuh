@@ -613,6 +613,7 @@ struct CgArgs {
 };
 __global__ void k_wait_selftest(int* err_flag, unsigned long long limit_ns);
 __global__ void k_counts_to_float(const uint16_t* __restrict__ src, float* __restrict__ dst, size_t n);
+__global__ void k_fma_peak(float* __restrict__ sink, int iters, float a, float b);
 __global__ void k_cg_dots(CgArgs c);
 __global__ void k_cg_reduce(CgArgs c);
 __global__ void k_cg_direction(CgArgs c);

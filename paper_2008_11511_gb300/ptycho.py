@@ -187,13 +187,14 @@ class Ptycho:
         sub-pixel positions, and frames whose rounded position changes move.
         Returns the sub-pixel positions (float64 (J, 2))."""
         if getattr(self, "_pos_f", None) is None:
-            self._pos_f = self.positions.astype(np.float64)
-        d = self.position_shifts(filter_ratio).cpu().numpy().astype(np.float64)
-        self._pos_f += np.clip(step * d, -max_shift, max_shift)
-        hi = np.array([self.Ho - self.N, self.Wo - self.N], dtype=np.float64)
-        self._pos_f = np.clip(self._pos_f, 0.0, hi)
-        new = np.rint(self._pos_f).astype(np.int32)
-        if np.any(new != self.positions):
+            self._pos_f = np.ascontiguousarray(self.positions.astype(np.float64))
+        d = np.ascontiguousarray(self.position_shifts(filter_ratio).cpu().numpy())
+        new = np.ascontiguousarray(self.positions.astype(np.int32))
+        moved = ctypes.c_int32()
+        _lib.call("ptx_accumulate_shifts", int(self.J), ctypes.c_void_p(d.ctypes.data), float(step),
+                  float(max_shift), int(self.Ho - self.N), int(self.Wo - self.N),
+                  ctypes.c_void_p(self._pos_f.ctypes.data), ctypes.c_void_p(new.ctypes.data), ctypes.byref(moved))
+        if moved.value > 0:
             self.set_positions(new)
         return self._pos_f.copy()
 
@@ -365,6 +366,31 @@ def fft2(x: torch.Tensor, direction: int = -1) -> torch.Tensor:
         _lib.call("ptx_fft2", ctypes.c_void_p(x.data_ptr()), int(nframes), int(N), int(direction),
                   _stream_ptr(x.device))
     return x
+
+
+def fma_tflops(device=None, iters: int = 8192, blocks_per_sm: int = 8, repeats: int = 3) -> float:
+    """Measured FP32 FMA throughput of the GPU in TFLOP/s (best of ``repeats``
+    launches of ``ptx_fma_peak``, timed with CUDA events on the current stream):
+    the ALU roof the FFT passes are compared against."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = sms * blocks_per_sm
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
+    flops = ctypes.c_double()
+    best = 0.0
+    with torch.cuda.device(dev):
+        stream = torch.cuda.current_stream(dev)
+        for r in range(repeats + 1):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _lib.call("ptx_fma_peak", int(blocks), int(iters), ctypes.c_void_p(sink.data_ptr()), ctypes.byref(flops),
+                      _stream_ptr(dev))
+            e1.record(stream)
+            e1.synchronize()
+            if r > 0:  # the first launch warms up
+                best = max(best, flops.value / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
 
 
 def counts_to_float(dst: torch.Tensor, counts: torch.Tensor) -> torch.Tensor:

@@ -115,3 +115,53 @@ def test_python_api_imports_without_a_gpu():
     from paper_2008_11511_gb300 import Ptycho, PtychoError, PtychoLLK, fft2  # noqa: F401
     import paper_2008_11511_gb300.ptycho as m
     assert m.Ptycho is Ptycho
+
+
+# ---------------------------------------------------------------- position refinement, host step
+
+def test_oracle_refine_positions_step_pins():
+    """The oracle's host step of position refinement against hand-worked cases:
+    0.3 px per step moves the frame after the second step (10.6 rounds to 11),
+    a 5 px shift is clipped to max_shift, the object edge stops the position,
+    and exact halves round to even."""
+    from oracle import ptycho as orc
+    pos = np.array([[10.0, 10.0]])
+    pos, ip = orc.refine_positions_step(pos, np.array([[0.3, -0.3]]), 1.0, 2.0, 50, 50)
+    assert np.allclose(pos, [[10.3, 9.7]]) and ip.tolist() == [[10, 10]]
+    pos, ip = orc.refine_positions_step(pos, np.array([[0.3, -0.3]]), 1.0, 2.0, 50, 50)
+    assert np.allclose(pos, [[10.6, 9.4]]) and ip.tolist() == [[11, 9]]
+    pos, ip = orc.refine_positions_step(np.array([[20.0, 20.0]]), np.array([[5.0, -5.0]]), 1.0, 2.0, 50, 50)
+    assert ip.tolist() == [[22, 18]]
+    pos, ip = orc.refine_positions_step(np.array([[0.5, 49.5]]), np.array([[-3.0, 3.0]]), 0.5, 2.0, 50, 49)
+    assert pos.tolist() == [[0.0, 49.0]] and ip.tolist() == [[0, 49]]
+    pos, ip = orc.refine_positions_step(np.array([[10.25, 11.25]]), np.array([[0.25, 0.25]]), 1.0, 2.0, 50, 50)
+    assert ip.tolist() == [[10, 12]]  # 10.5 -> 10, 11.5 -> 12
+
+
+def test_accumulate_shifts_matches_the_oracle(lib):
+    """ptx_accumulate_shifts (library host code, no GPU) equals the oracle's step
+    bit for bit over several steps of random shifts, and reports the moves."""
+    from oracle import ptycho as orc
+    rng = np.random.default_rng(5)
+    J, max_row, max_col = 300, 90, 70
+    pos_f = np.ascontiguousarray(np.stack([rng.uniform(0, max_row, J), rng.uniform(0, max_col, J)], 1))
+    pos_f[:5] = [[0, 0], [max_row, max_col], [0.5, 1.5], [2.5, 3.5], [45.0, 35.0]]
+    ref_f = pos_f.copy()
+    ipos = np.ascontiguousarray(np.rint(pos_f).astype(np.int32))
+    for it in range(4):
+        shifts = np.ascontiguousarray((rng.standard_normal((J, 2)) * 1.5).astype(np.float32))
+        shifts[:3] = [[-4, -4], [4, 4], [0, 0]]
+        step, max_shift = 0.7, 2.0
+        before = ipos.copy()
+        moved = ctypes.c_int32()
+        st = lib.ptx_accumulate_shifts(J, ctypes.c_void_p(shifts.ctypes.data), ctypes.c_double(step),
+                                       ctypes.c_double(max_shift), max_row, max_col,
+                                       ctypes.c_void_p(pos_f.ctypes.data), ctypes.c_void_p(ipos.ctypes.data),
+                                       ctypes.byref(moved))
+        assert st == 0
+        ref_f, ref_i = orc.refine_positions_step(ref_f, shifts, step, max_shift, max_row, max_col)
+        assert np.array_equal(pos_f, ref_f)
+        assert np.array_equal(ipos, ref_i)
+        assert moved.value == int(np.any(ipos != before, axis=1).sum())
+    assert lib.ptx_accumulate_shifts(-1, None, ctypes.c_double(1.0), ctypes.c_double(1.0), 1, 1, None, None,
+                                     ctypes.byref(moved)) == 1
