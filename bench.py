@@ -36,6 +36,10 @@ if ROOT not in sys.path:
 METRIC = "DM-cycle frames/s at 256² (plain FP32 vs chosen form, same GB300); % HBM roof"
 UNIT = "frames/s"
 WORKLOAD = "dm256"
+FORMS = {0: "fp32 (plain)",
+         1: "tf32 hi+lo tensor-core DFT stages in the column pass, fp32 elsewhere",
+         2: "bf16 hi+mid+lo tensor-core DFT stages in the column pass, fp32 elsewhere",
+         3: "bf16 hi+lo tensor-core DFT stages in the column pass (below fp32 accuracy), fp32 elsewhere"}
 PROFILES = os.path.join(ROOT, "profiles")
 
 
@@ -435,7 +439,7 @@ def run_ours(args):
     if args.tma_gather is not None:
         params.append(("tma_gather", args.tma_gather))
     if args.tc:
-        params.append(("tc", 1))
+        params.append(("tc", args.tc))
     for name, val in params:
         pb.set_param(name, val)
     stream = torch.cuda.current_stream(dev)
@@ -487,21 +491,24 @@ def run_ours(args):
     # plain form was timed above, and the plain form otherwise
     other = None
     if not args.no_form_comparison and s.N == 256 and s.K == 1:
-        tc_other = 0 if args.tc else 1
-        pb.set_param("tc", tc_other)
-        pb.dm(2, llk=llk_buf)  # capture the other form's graph
-        torch.cuda.synchronize(dev)
-        n_other = max(1, min(args.steps, 10))
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        pb.dm(n_other, llk=llk_buf)
-        f1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms_o = max_over_ranks(f0.elapsed_time(f1), ws) / n_other
-        other = {"form": "tf32 hi+lo tensor-core DFT stages in the column pass" if tc_other else "fp32 (plain)",
-                 "value": s.J * ws / (ms_o / 1e3), "ms_per_step": ms_o, "steps": n_other}
-        pb.set_param("tc", 1 if args.tc else 0)
+        other = []
+        for tc_other in range(4):
+            if tc_other == args.tc:
+                continue
+            pb.set_param("tc", tc_other)
+            pb.dm(2, llk=llk_buf)  # capture the other form's graph
+            torch.cuda.synchronize(dev)
+            n_other = max(1, min(args.steps, 10))
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            pb.dm(n_other, llk=llk_buf)
+            f1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms_o = max_over_ranks(f0.elapsed_time(f1), ws) / n_other
+            other.append({"form": FORMS[tc_other], "value": s.J * ws / (ms_o / 1e3), "ms_per_step": ms_o,
+                          "steps": n_other})
+        pb.set_param("tc", args.tc)
         pb.dm(1, llk=llk_buf)
         torch.cuda.synchronize(dev)
 
@@ -583,7 +590,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "desc": workload_desc(s), "form": ("tf32 hi+lo tensor-core DFT stages in the column pass, fp32 elsewhere" if args.tc else "fp32 (plain)"),
+                "config": {"workload": WORKLOAD, "desc": workload_desc(s), "form": FORMS[args.tc],
                            "parallelism": f"replicas x{ws}",
                            "l2": "inputs larger than L2 (Psi 2.1 GB + I 1.05 GB per replica); no flush"},
                 "roofline": roof, "roofline_cycle": roof_cycle, "kernels": kstats, "other_form": other,
@@ -622,8 +629,9 @@ def main():
                     help="column pass staged by tensor copies (1) or the register column pass (0, the library default)")
     ap.add_argument("--tma-gather", type=int, choices=(0, 1), default=None,
                     help="object gather fed by tensor copies (1, the library default) or the plain gather (0)")
-    ap.add_argument("--tc", action="store_true",
-                    help="the split-precision form: column-pass DFT stages on the tensor cores (TF32 hi + lo)")
+    ap.add_argument("--tc", type=int, choices=(0, 1, 2, 3), default=0,
+                    help="number format of the column pass's DFT stages: 0 FP32 (CUDA cores), or on the tensor "
+                         "cores 1 TF32 hi+lo, 2 BF16 hi+mid+lo, 3 BF16 hi+lo")
     ap.add_argument("--batch-frames", type=int, default=0,
                     help="upper bound on frames per batch (library default when 0)")
     ap.add_argument("--repeats", type=int, default=5,

@@ -55,6 +55,19 @@ typedef enum {
 #define PTX_NO_NORMALISE 0x8u  /* accumulate N_O, D_O, N_P, D_P but do not normalise (data-parallel split) */
 #define PTX_NO_GRAPH     0x10u /* enqueue kernels directly instead of replaying a captured CUDA graph */
 #define PTX_UPDATE_BACKGROUND 0x40u /* AP only: update the incoherent background of the problems that have one */
+/* Number format of the column pass's 16-point DFT stages (one-mode problems
+ * with N = 256; other problems run FP32).  No PTX_FORM_* flag: the handle's
+ * "tc" parameter (default FP32, the CUDA-core codelets).  At most one flag.
+ * The tensor-core forms run each stage as tcgen05.mma GEMMs with the operands
+ * split into terms of the narrow type and FP32 accumulation in TMEM:
+ *   PTX_FORM_TF32X2  TF32 hi + lo, 3 products, about 2^-21 per product;
+ *   PTX_FORM_BF16X3  BF16 hi + mid + lo, 6 products (every product down to
+ *                    2^-16 of the result), the BF16 split that meets FP32 parity;
+ *   PTX_FORM_BF16X2  BF16 hi + lo, 3 products, about 2^-16 per product: the
+ *                    two-term split, below FP32 accuracy. */
+#define PTX_FORM_TF32X2 0x1000u
+#define PTX_FORM_BF16X3 0x2000u
+#define PTX_FORM_BF16X2 0x4000u
 
 #define PTX_MAX_MODES 8
 
@@ -216,11 +229,12 @@ ptx_status ptx_accumulators(ptx_handle* h, int32_t p, void** obj_acc, size_t* ob
  * per SM).  "tma_gather" (1, default: the object numerator / denominator of
  * frames with N >= 64 is gathered from boxes of Psi' and P brought into shared
  * memory by 3D tensor copies through a four-stage mbarrier ring; 0: the plain
- * gather).  "tc" (0, default; 1: the AP / DM column pass of one-mode problems
- * with N = 256 runs its four 16-point DFT stages on the tensor cores:
- * tcgen05.mma kind::tf32 with hi + lo split operands and FP32 accumulation in
- * TMEM, relative error about 2^-21 per product instead of FP32's 2^-24).
- * Each pair of variants gives the same results up to rounding. */
+ * gather).  "tc": the number format of the DFT stages of the AP / DM column
+ * pass of one-mode problems with N = 256 (0, default: FP32 on the CUDA cores;
+ * 1: TF32X2, 2: BF16X3, 3: BF16X2 on the tensor cores, as the PTX_FORM_*
+ * cycle flags describe); a PTX_FORM_* flag of a cycle call overrides it for
+ * that call.  Each pair of variants gives the same results up to rounding
+ * (BF16X2: up to its larger rounding). */
 ptx_status ptx_set_param(ptx_handle* h, const char* name, double value);
 
 /* In-place orthonormal 2D FFT of `nframes` N x N complex64 frames (the FT

@@ -30,6 +30,9 @@ PTX_NO_NORMALISE = 0x8
 PTX_NO_GRAPH = 0x10
 PTX_ML_RESTART = 0x20
 PTX_UPDATE_BACKGROUND = 0x40
+PTX_FORM_TF32X2 = 0x1000
+PTX_FORM_BF16X3 = 0x2000
+PTX_FORM_BF16X2 = 0x4000
 PTX_MAX_MODES = 8
 PTX_ALGO_AP = 0
 PTX_ALGO_DM = 1

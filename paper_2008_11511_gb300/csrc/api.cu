@@ -446,7 +446,7 @@ struct ptx_handle {
     int batch_cap = 0;  // ptx_set_param "batch_frames"
     int tma = 0;        // ptx_set_param "tma": column pass fed by tensor copies where available
     int tma_gather = 1; // ptx_set_param "tma_gather": object gather fed by tensor copies where available
-    int tc = 0;         // ptx_set_param "tc": column pass with the DFT stages on the tensor cores (N = 256, K = 1)
+    int tc = 0;         // ptx_set_param "tc": TcForm of the column pass's DFT stages on the tensor cores (N = 256, K = 1)
     // flag in mapped pinned host memory that a device wait sets when it gives up
     int* err_host = nullptr;
     int* err_dev = nullptr;
@@ -644,6 +644,15 @@ ptx_status ensure_lanes(ptx_handle* h) {
     return PTX_OK;
 }
 
+// Number format of the column pass's DFT stages for a call: a PTX_FORM_* flag,
+// else the handle's "tc" parameter.
+int tc_form(const ptx_handle* h, uint32_t flags) {
+    if (flags & PTX_FORM_TF32X2) return TC_TF32X2;
+    if (flags & PTX_FORM_BF16X3) return TC_BF16X3;
+    if (flags & PTX_FORM_BF16X2) return TC_BF16X2;
+    return h->tc;
+}
+
 // One cycle of every problem, enqueued on `s`.  With one lane everything runs
 // on s.  With several, the batches of all problems go round-robin to the lane
 // streams, each lane with its own slice of the work-stack region; s forks the
@@ -651,6 +660,7 @@ ptx_status ensure_lanes(ptx_handle* h) {
 // update and LLK reduction (while the lanes go on with the next problem), and
 // joins the lanes at the end.
 ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t flags, cudaStream_t s) {
+    const int form = tc_form(h, flags);
     const bool upd_o = flags & PTX_UPDATE_OBJ;
     const bool upd_p = flags & PTX_UPDATE_PROBE;
     const bool init = flags & PTX_DM_INIT_PSI;
@@ -703,9 +713,9 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
                     ProfScope ps(h, PTX_KERNEL_COL, ls);
                     ks->col_nf(al, nb, -1, ls);
                 }
-            } else if (h->tc && ph.p.N == 256 && ph.p.K == 1 && !ph.p.background) {
+            } else if (form != TC_NONE && ph.p.N == 256 && ph.p.K == 1 && !ph.p.background) {
                 ProfScope ps(h, PTX_KERNEL_COL, ls);
-                launch_col_tc(al, j0, nb, ls);
+                launch_col_tc(al, j0, nb, form, ls);
             } else {
                 ProfScope ps(h, PTX_KERNEL_COL, ls);
                 CUtensorMap tm_spec;
@@ -813,9 +823,11 @@ ptx_status run_cycles(ptx_handle* h, const std::vector<int>& algos, int ncycles,
                       void* stream) {
     if (!h) return fail(PTX_ERR_INVALID_ARG, "null handle");
     if (ncycles < 0) return fail(PTX_ERR_INVALID_ARG, "ncycles=%d must be >= 0", ncycles);
-    const uint32_t known =
-        PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_DM_INIT_PSI | PTX_NO_NORMALISE | PTX_NO_GRAPH | PTX_UPDATE_BACKGROUND;
+    const uint32_t forms = PTX_FORM_TF32X2 | PTX_FORM_BF16X3 | PTX_FORM_BF16X2;
+    const uint32_t known = PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_DM_INIT_PSI | PTX_NO_NORMALISE | PTX_NO_GRAPH |
+                           PTX_UPDATE_BACKGROUND | forms;
     if (flags & ~known) return fail(PTX_ERR_INVALID_ARG, "unknown flag bits 0x%x", flags & ~known);
+    if (__builtin_popcount(flags & forms) > 1) return fail(PTX_ERR_INVALID_ARG, "more than one PTX_FORM_* flag");
     if ((int)algos.size() != (int)h->probs.size()) return fail(PTX_ERR_INVALID_ARG, "one algorithm per problem");
     for (int a : algos)
         if (a != ALGO_AP && a != ALGO_DM) return fail(PTX_ERR_INVALID_ARG, "algorithm %d is neither AP nor DM", a);
@@ -836,7 +848,7 @@ ptx_status run_cycles(ptx_handle* h, const std::vector<int>& algos, int ncycles,
     cudaStream_t s = (cudaStream_t)stream;
     k_set_ctl<<<1, 1, 0, s>>>(h->ctl, llk_dev, (int)h->probs.size());
     const bool graph = !(flags & PTX_NO_GRAPH) && !h->profiling;
-    const uint32_t base = flags & (PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_NO_NORMALISE | PTX_UPDATE_BACKGROUND);
+    const uint32_t base = flags & (PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_NO_NORMALISE | PTX_UPDATE_BACKGROUND | forms);
     for (int c = 0; c < ncycles; ++c) {
         uint32_t f = base;
         if (c == 0 && (flags & PTX_DM_INIT_PSI)) f |= PTX_DM_INIT_PSI;
@@ -992,7 +1004,7 @@ ptx_status ptx_cycle_kernels(ptx_handle* h, int32_t algorithm, uint32_t flags, i
     ptx_status st = check_device(h);
     if (st != PTX_OK) return st;
     const uint32_t f = flags & (PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_NO_NORMALISE | PTX_UPDATE_BACKGROUND |
-                                PTX_DM_INIT_PSI);
+                                PTX_DM_INIT_PSI | PTX_FORM_TF32X2 | PTX_FORM_BF16X3 | PTX_FORM_BF16X2);
     const std::vector<int> algos(h->probs.size(), algorithm);
     cudaGraphExec_t ex;
     if ((st = get_graph(h, algos, f, &ex)) != PTX_OK) return st;
@@ -1234,7 +1246,8 @@ ptx_status ptx_set_param(ptx_handle* h, const char* name, double value) {
         if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "tma must be 0 or 1");
         h->tma = (int)value;
     } else if (!strcmp(name, "tc")) {
-        if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "tc must be 0 or 1");
+        if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
+            return fail(PTX_ERR_INVALID_ARG, "tc must be 0 (FP32), 1 (TF32X2), 2 (BF16X3) or 3 (BF16X2)");
         h->tc = (int)value;
     } else if (!strcmp(name, "tma_gather")) {
         if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "tma_gather must be 0 or 1");

@@ -580,7 +580,10 @@ struct TileLists {
 __global__ void k_obj_gather(ProbArgs a, TileLists tl, int fuse_max);
 // Column pass with the 16-point DFT stages on the tensor cores (tcgen05, TF32
 // hi + lo split; N = 256, one mode), the split-precision form of k_col_r<256>.
-void launch_col_tc(const ProbArgs& a, int j0, int nb, cudaStream_t s);
+// Number formats of the tensor-core column pass (ptx_set_param "tc" and the
+// PTX_FORM_* cycle flags): TF32 hi + lo, BF16 hi + mid + lo, BF16 hi + lo.
+enum TcForm : int { TC_NONE = 0, TC_TF32X2 = 1, TC_BF16X3 = 2, TC_BF16X2 = 3 };
+void launch_col_tc(const ProbArgs& a, int j0, int nb, int form, cudaStream_t s);
 cudaError_t set_attrs_tc();
 // The same gather fed by 3D tensor copies (32 x 32 tiles, N >= 64).
 void launch_obj_gather_tma(const void* tm_psi, const void* tm_probe, const ProbArgs& a, const TileLists& tl,
