@@ -417,6 +417,50 @@ def run_extra_modes(dev, pk, ws, J=1500, H=2800):
                          "frac": gbs / pk["hbm_gbs"], "alg_bytes_per_cycle": b, "peak_src": pk["src"]}}
 
 
+def run_extra_batched(dev, ws, j_scale=0.25):
+    """The batched workload (16 independent scans, frame sizes 128^2 to 512^2,
+    AP and DM alternately), each scan's positions scaled by j_scale to bound the
+    set-up time: cycles of all problems through one handle (one CUDA graph per
+    cycle, schedule from the autotuner) against the same problems as 16
+    separate handles run one after the other on the stream."""
+    import torch
+    from paper_2008_11511_gb300 import Ptycho, PtychoBatch
+    from paper_2008_11511_gb300.autotune import autotune
+    from synthetic import make_scan
+    from synthetic.scans import batched_problem_specs
+    specs = batched_problem_specs(j_scale=j_scale)
+    scans = [make_scan(**d) for d in specs]
+    algos = [d["algorithm"] for d in specs]
+    items = [dict(obj=torch.tensor(s.obj0, device=dev), probe=torch.tensor(s.probe0, device=dev),
+                  iobs=torch.tensor(s.iobs, device=dev), positions=s.positions, mask=s.mask) for s in scans]
+    frames = sum(s.J for s in scans)
+    stream = torch.cuda.current_stream(dev)
+    pb = PtychoBatch(items)
+    pb.cycles(1, algos, init_psi=True)
+    best, _ = autotune(pb, algos, lanes=(1, 2), batch_frames=(0, 32), use_cache=False)
+    pb.cycles(1, algos)
+    torch.cuda.synchronize(dev)
+    ms_one = _events_ms(lambda: pb.cycles(3, algos), 3, stream) / 3
+    pb.close()
+    handles = [Ptycho(it["obj"], it["probe"], it["iobs"], it["positions"], it["mask"], with_psi=True) for it in items]
+    for h, a in zip(handles, algos):
+        h.dm(1, init_psi=True) if a == "DM" else h.ap(1)
+
+    def sep():
+        for h, a in zip(handles, algos):
+            h.dm(1) if a == "DM" else h.ap(1)
+    sep()
+    torch.cuda.synchronize(dev)
+    ms_sep = _events_ms(sep, 3, stream)
+    for h in handles:
+        h.close()
+    return {"workload": f"{len(specs)} scans, frame sizes {sorted(set(s.N for s in scans))}, {frames} frames "
+                        f"(positions x{j_scale} of the full batched workload), AP and DM alternately",
+            "ms_per_cycle_one_handle": ms_one, "frames_per_s_one_handle": frames * ws / (ms_one * 1e-3),
+            "schedule": dict(zip(("lanes", "batch_frames", "tma", "bwd_slots"), best)),
+            "ms_per_cycle_separate_handles": ms_sep, "frames_per_s_separate": frames * ws / (ms_sep * 1e-3)}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_init()
@@ -574,7 +618,8 @@ def run_ours(args):
         pb.close()
         del pb
         torch.cuda.synchronize(dev)
-        extras = {"ml256": run_extra_ml(dev, fma_peak, ws), "modes512": run_extra_modes(dev, pk, ws)}
+        extras = {"ml256": run_extra_ml(dev, fma_peak, ws), "modes512": run_extra_modes(dev, pk, ws),
+                  "batched16": run_extra_batched(dev, ws)}
         pb = None
 
     cpu = None

@@ -223,7 +223,10 @@ ptx_status ptx_accumulators(ptx_handle* h, int32_t p, void** obj_acc, size_t* ob
 /* Set a scalar parameter: "alpha_obj" or "alpha_probe" (inertia factors of the
  * normalisation, default 0.01 each, must be >= 0); "lanes" (batches in flight per
  * cycle, 1..4, default 2); "batch_frames" (upper bound on frames per batch, 0 =
- * as many as the work stack holds); "tma" (0, default: the register column pass;
+ * as many as the work stack holds); "bwd_slots" (frame slots of the row-backward
+ * pass: blocks per row band, each looping over every bwd_slots-th frame of a
+ * batch and flushing its probe sums once; 0, default: as many as are resident
+ * at once); "tma" (0, default: the register column pass;
  * 1: the AP / DM column pass of one-mode problems with N = 256 takes its inputs
  * by 2D tensor copies (cp.async.bulk.tensor) in a persistent grid of two CTAs
  * per SM).  "tma_gather" (1, default: the object numerator / denominator of

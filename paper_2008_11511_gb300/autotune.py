@@ -1,5 +1,7 @@
-"""Schedule autotuner: picks the batch lanes and the batch size of a problem (or a
-batched handle) by timing its own cycles.
+"""Schedule autotuner: picks the schedule of a problem (or a batched handle) by
+timing its own cycles: the batch lanes, the batch size, the column pass's tiling
+(register-resident lines, or tiles brought in by tensor copies) and the frame
+slots of the row-backward pass.
 
 The candidates are run on the real data for a couple of cycles each, timed with
 CUDA events on the launch stream; the object, probe and exit-wave state is
@@ -41,24 +43,32 @@ def _run(target, algorithms, n, init):
     return target.ap(n)
 
 
-def autotune(target, algorithms=("DM",), lanes=(1, 2, 3), batch_frames=(0, 32, 64), cycles: int = 2,
-             use_cache: bool = True):
-    """Time every (lanes, batch_frames) candidate and keep the fastest on ``target``
-    (a Ptycho or PtychoBatch).  Returns (best, {candidate: ms per cycle})."""
+PARAMS = ("lanes", "batch_frames", "tma", "bwd_slots")
+
+
+def _apply(target, cand):
+    for name, v in zip(PARAMS, cand):
+        target.set_param(name, v)
+
+
+def autotune(target, algorithms=("DM",), lanes=(1, 2, 3), batch_frames=(0, 32, 64), tma=(0,), bwd_slots=(0,),
+             cycles: int = 2, use_cache: bool = True):
+    """Time every (lanes, batch_frames, tma, bwd_slots) candidate and keep the
+    fastest on ``target`` (a Ptycho or PtychoBatch).  ``tma`` = 1 feeds the
+    256^2 column pass by tensor copies; ``bwd_slots`` = 0 sizes the row-backward
+    pass by occupancy.  Returns (best, {candidate: ms per cycle})."""
     algorithms = list(algorithms)
-    key = _key(target, algorithms)
+    key = _key(target, algorithms) + (tuple(lanes), tuple(batch_frames), tuple(tma), tuple(bwd_slots))
     if use_cache and key in _CACHE:
         best = _CACHE[key]
-        target.set_param("lanes", best[0])
-        target.set_param("batch_frames", best[1])
+        _apply(target, best)
         return best, {}
     saved = [t.clone() for t in _state_tensors(target)]
     stream = torch.cuda.current_stream(target.device)
     times = {}
     first = True
-    for ln, bf in itertools.product(lanes, batch_frames):
-        target.set_param("lanes", ln)
-        target.set_param("batch_frames", bf)
+    for cand in itertools.product(lanes, batch_frames, tma, bwd_slots):
+        _apply(target, cand)
         _run(target, algorithms, 1, first)  # warm-up (graph capture)
         first = False
         e0 = torch.cuda.Event(enable_timing=True)
@@ -67,11 +77,10 @@ def autotune(target, algorithms=("DM",), lanes=(1, 2, 3), batch_frames=(0, 32, 6
         _run(target, algorithms, cycles, False)
         e1.record(stream)
         e1.synchronize()
-        times[(ln, bf)] = e0.elapsed_time(e1) / cycles
+        times[cand] = e0.elapsed_time(e1) / cycles
     for t, s in zip(_state_tensors(target), saved):
         t.copy_(s)
     best = min(times, key=times.get)
-    target.set_param("lanes", best[0])
-    target.set_param("batch_frames", best[1])
+    _apply(target, best)
     _CACHE[key] = best
     return best, times

@@ -279,7 +279,7 @@ int sm_count() {
     return n > 0 ? n : 152;
 }
 
-void set_batch(ProbHost& h, size_t spec_bytes, int lanes, int cap = 0) {
+void set_batch(ProbHost& h, size_t spec_bytes, int lanes, int cap = 0, int slots = 0) {
     const ptx_problem& p = h.p;
     const size_t frame_bytes = (size_t)p.K * p.N * p.N * sizeof(float2);
     size_t B = (spec_bytes / lanes) / 256 * 256 / frame_bytes;
@@ -295,7 +295,7 @@ void set_batch(ProbHost& h, size_t spec_bytes, int lanes, int cap = 0) {
     if (per_sm <= 0) per_sm = 2;
     const int resident = per_sm * sm_count();
     const int rowblk = p.N / h.L3 * p.K;
-    int G = resident / rowblk;
+    int G = slots > 0 ? slots : resident / rowblk;
     if (G > h.B) G = h.B;
     if (G < 1) G = 1;
     h.G3 = G;
@@ -444,6 +444,7 @@ struct ptx_handle {
     // batch lanes: extra streams and fork / join events (lane 0 is the call's stream)
     int lanes = kDefaultLanes;
     int batch_cap = 0;  // ptx_set_param "batch_frames"
+    int bwd_slots = 0;  // ptx_set_param "bwd_slots": frame slots of the row-backward pass (0: by occupancy)
     int tma = 0;        // ptx_set_param "tma": column pass fed by tensor copies where available
     int tma_gather = 1; // ptx_set_param "tma_gather": object gather fed by tensor copies where available
     int tc = 0;         // ptx_set_param "tc": TcForm of the column pass's DFT stages on the tensor cores (N = 256, K = 1)
@@ -677,7 +678,7 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
     int next_lane = 0;
     for (int pi = 0; pi < np; ++pi) {
         ProbHost& ph = h->probs[pi];
-        set_batch(ph, h->spec_bytes, lanes, h->batch_cap);
+        set_batch(ph, h->spec_bytes, lanes, h->batch_cap, h->bwd_slots);
         const ProbArgs& a = ph.args;
         const KernelSet* ks = ph.ks;
         const int algo = algos[pi];
@@ -1128,7 +1129,7 @@ ptx_status enqueue_grad(ptx_handle* h, ProbHost& ph, float2* g_obj, float2* g_pr
     if (g_obj) e = cudaMemsetAsync(g_obj, 0, sizeof(float2) * (size_t)a.Ho * a.Wo, s);
     if (e == cudaSuccess && g_probe) e = cudaMemsetAsync(g_probe, 0, sizeof(float2) * (size_t)a.K * a.N * a.N, s);
     if (e != cudaSuccess) return cuda_fail(e, "gradient memset");
-    set_batch(ph, h->spec_bytes, 1, h->batch_cap);
+    set_batch(ph, h->spec_bytes, 1, h->batch_cap, h->bwd_slots);
     for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
         const int nb = std::min(ph.B, ph.p.J - j0);
         ph.ks->row_fwd(a, j0, nb, X_PHI, s);
@@ -1252,6 +1253,10 @@ ptx_status ptx_set_param(ptx_handle* h, const char* name, double value) {
     } else if (!strcmp(name, "tma_gather")) {
         if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "tma_gather must be 0 or 1");
         h->tma_gather = (int)value;
+    } else if (!strcmp(name, "bwd_slots")) {
+        if (value != (int)value || value < 0 || value > 4096)
+            return fail(PTX_ERR_INVALID_ARG, "bwd_slots must be an integer in 0..4096");
+        h->bwd_slots = (int)value;
     } else if (!strcmp(name, "batch_frames")) {
         if (value != (int)value || value > 32768)
             return fail(PTX_ERR_INVALID_ARG, "batch_frames must be an integer in 0..32768");

@@ -126,8 +126,9 @@ def test_autotune_restores_state_and_sets_a_schedule():
     pb = Ptycho(dev(o0), dev(p0), dev(s.iobs), s.positions, s.mask)
     pb.dm(1, init_psi=True)
     before = [t.clone() for t in (pb.obj, pb.probe, pb.psi)]
-    best, times = autotune(pb, ["DM"], lanes=(1, 2), batch_frames=(0, 16), use_cache=False)
-    assert best in times and len(times) == 4
+    best, times = autotune(pb, ["DM"], lanes=(1, 2), batch_frames=(0, 16), tma=(0, 1), bwd_slots=(0, 4),
+                           use_cache=False)
+    assert best in times and len(times) == 16
     for t, b in zip((pb.obj, pb.probe, pb.psi), before):
         assert torch.equal(t, b)
     # tuned schedule gives the same cycle as the default one
