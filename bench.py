@@ -575,6 +575,14 @@ def run_ours(args):
     # end to end through the public API with host buffers: every step copies its
     # intensity stack in from pinned host memory and reads the cycle's LLK back.
     e2e_value, e2e_bytes, e2e_copies = run_e2e(args, s, pb, obj, probe, iobs, params, llk_buf, stream, dev, ws)
+    e2e_f32 = None
+    if args.e2e_dtype == "auto" and "uint16" in e2e_copies:
+        # the same leg uploading float32 frames (what a caller without photon counts moves)
+        a32 = argparse.Namespace(**vars(args))
+        a32.e2e_dtype = "f32"
+        v32, b32, c32 = run_e2e(a32, s, pb, obj, probe, iobs, params, llk_buf, stream, dev, ws)
+        e2e_f32 = {"value": v32, "unit": UNIT, "h2d_bytes_per_step": int(b32), "d2h_bytes_per_step": 8,
+                   "copies": c32}
 
     # roofline: the dominant kernel by time share, against the measured FMA peak
     from paper_2008_11511_gb300 import fma_tflops
@@ -639,7 +647,10 @@ def run_ours(args):
                            "parallelism": f"replicas x{ws}",
                            "l2": "inputs larger than L2 (Psi 2.1 GB + I 1.05 GB per replica); no flush"},
                 "roofline": roof, "roofline_cycle": roof_cycle, "kernels": kstats, "other_form": other,
-                "repeats_ms": rep_ms, "fma_peak_tflops": fma_peak, "extra": extras,
+                "repeats_ms": rep_ms, "fma_peak_tflops": fma_peak, "extra": extras, "e2e_f32": e2e_f32,
+                "kernels_note": ("per-kernel times from a pass with one batch lane and direct launches (sum "
+                                 f"{sum(v['total_ms'] for v in kstats.values()) / args.steps:.3f} ms per cycle); the "
+                                 f"timed graph cycle ({ms_per_step:.3f} ms) runs two lanes whose batches overlap"),
                 "clocks": clk, "gpu_launches": gpu_launches,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(e2e_bytes),
                         "d2h_bytes_per_step": 8, "steps": max(1, min(args.steps, 10)), "copies": e2e_copies},
