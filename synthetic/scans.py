@@ -127,8 +127,8 @@ def hermite_gauss_modes(N: int, K: int, waist: float, phase_coef: float, powers)
     y = (yy - N / 2) / waist
     x = (xx - N / 2) / waist
     g = np.exp(-(x * x + y * y)) * np.exp(1j * phase_coef * ((yy - N / 2) ** 2 + (xx - N / 2) ** 2))
-    orders = [(0, 0), (1, 0), (0, 1), (1, 1), (2, 0), (0, 2)]
-    herm = [lambda t: np.ones_like(t), lambda t: 2 * t, lambda t: 4 * t * t - 2]
+    orders = [(0, 0), (1, 0), (0, 1), (1, 1), (2, 0), (0, 2), (2, 1), (1, 2), (2, 2), (3, 0)]
+    herm = [lambda t: np.ones_like(t), lambda t: 2 * t, lambda t: 4 * t * t - 2, lambda t: 8 * t ** 3 - 12 * t]
     modes = []
     for k in range(K):
         ny, nx = orders[k]
