@@ -110,7 +110,7 @@ def source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2008_11511_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
+        if f.endswith((".cu", ".cuh", ".inc")):
             h.update(_code_only(open(os.path.join(d, f), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
@@ -441,6 +441,11 @@ def run_extra_batched(dev, ws, j_scale=0.25):
     pb.cycles(1, algos)
     torch.cuda.synchronize(dev)
     ms_one = _events_ms(lambda: pb.cycles(3, algos), 3, stream) / 3
+    # the same problems as one persistent launch of their batch passes per cycle
+    pb.set_param("persistent", 1)
+    pb.cycles(1, algos)
+    torch.cuda.synchronize(dev)
+    ms_pers = _events_ms(lambda: pb.cycles(3, algos), 3, stream) / 3
     pb.close()
     handles = [Ptycho(it["obj"], it["probe"], it["iobs"], it["positions"], it["mask"], with_psi=True) for it in items]
     for h, a in zip(handles, algos):
@@ -458,6 +463,7 @@ def run_extra_batched(dev, ws, j_scale=0.25):
                         f"(positions x{j_scale} of the full batched workload), AP and DM alternately",
             "ms_per_cycle_one_handle": ms_one, "frames_per_s_one_handle": frames * ws / (ms_one * 1e-3),
             "schedule": dict(zip(("lanes", "batch_frames", "tma", "bwd_slots"), best)),
+            "ms_per_cycle_persistent": ms_pers, "frames_per_s_persistent": frames * ws / (ms_pers * 1e-3),
             "ms_per_cycle_separate_handles": ms_sep, "frames_per_s_separate": frames * ws / (ms_sep * 1e-3)}
 
 
@@ -478,6 +484,8 @@ def run_ours(args):
         params.append(("lanes", args.lanes))
     if args.batch_frames:
         params.append(("batch_frames", args.batch_frames))
+    if args.persistent:
+        params.append(("persistent", 1))
     if args.tma is not None:
         params.append(("tma", args.tma))
     if args.tma_gather is not None:
@@ -688,6 +696,8 @@ def main():
     ap.add_argument("--tc", type=int, choices=(0, 1, 2, 3), default=0,
                     help="number format of the column pass's DFT stages: 0 FP32 (CUDA cores), or on the tensor "
                          "cores 1 TF32 hi+lo, 2 BF16 hi+mid+lo, 3 BF16 hi+lo")
+    ap.add_argument("--persistent", action="store_true",
+                    help="the cycle's batch passes as one persistent launch (work list with bounded waits)")
     ap.add_argument("--batch-frames", type=int, default=0,
                     help="upper bound on frames per batch (library default when 0)")
     ap.add_argument("--repeats", type=int, default=5,

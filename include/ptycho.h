@@ -226,7 +226,15 @@ ptx_status ptx_accumulators(ptx_handle* h, int32_t p, void** obj_acc, size_t* ob
  * as many as the work stack holds); "bwd_slots" (frame slots of the row-backward
  * pass: blocks per row band, each looping over every bwd_slots-th frame of a
  * batch and flushing its probe sums once; 0, default: as many as are resident
- * at once); "tma" (0, default: the register column pass;
+ * at once); "persistent" (0, default; 1: the batch passes of every problem of
+ * the handle run as the work items of one persistent launch per cycle, in
+ * pipeline order over three work-stack slots, each item waiting (bounded)
+ * for the items it depends on; for handles whose problems all have one probe
+ * mode, N in {128, 192, 256, 384, 512}, far field and no background, others
+ * keep the per-batch launches); "persistent_selftest" (1: the persistent
+ * schedule's first column items wait for a forward item that never comes, so
+ * their bounded wait gives up: the next cycle call returns PTX_ERR_TIMEOUT
+ * once; for the tests of that failure path); "tma" (0, default: the register column pass;
  * 1: the AP / DM column pass of one-mode problems with N = 256 takes its inputs
  * by 2D tensor copies (cp.async.bulk.tensor) in a persistent grid of two CTAs
  * per SM).  "tma_gather" (1, default: the object numerator / denominator of

@@ -34,7 +34,8 @@ def nvcc():
 
 
 def _deps_mtime():
-    files = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    files = (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.inc")) +
+             glob.glob(os.path.join(INCLUDE, "*.h")))
     return max(os.path.getmtime(f) for f in files) if files else 0.0
 
 

@@ -80,7 +80,7 @@ static cudaError_t ensure_attributes() {
     cudaError_t (*fns[])() = {set_attrs_8,   set_attrs_12,  set_attrs_16,  set_attrs_32,  set_attrs_64,
                               set_attrs_128, set_attrs_192, set_attrs_256, set_attrs_384, set_attrs_512,
                               set_attrs_80,  set_attrs_160, set_attrs_224, set_attrs_400, set_attrs_448,
-                              set_attrs_gather_tma, set_attrs_tc};
+                              set_attrs_gather_tma, set_attrs_tc, set_attrs_persistent};
     for (auto f : fns)
         if ((e = f()) != cudaSuccess) return e;
     if (dev < 32) done_mask |= 1 << dev;
@@ -445,6 +445,15 @@ struct ptx_handle {
     int lanes = kDefaultLanes;
     int batch_cap = 0;  // ptx_set_param "batch_frames"
     int bwd_slots = 0;  // ptx_set_param "bwd_slots": frame slots of the row-backward pass (0: by occupancy)
+    // ptx_set_param "persistent": the batch passes of all problems as one persistent launch
+    int persistent = 0;
+    size_t pers_off = 0;
+    bool pers_dirty = true;  // tables to rebuild and upload before the next cycle
+    int pers_selftest = 0;   // ptx_set_param "persistent_selftest": a dependency that is never met
+    int pers_nitems = 0, pers_nseg = 0, pers_nbatch = 0;
+    std::vector<ProbArgs> pers_prob;
+    std::vector<PSeg> pers_seg;
+    std::vector<PBatch> pers_batch;
     int tma = 0;        // ptx_set_param "tma": column pass fed by tensor copies where available
     int tma_gather = 1; // ptx_set_param "tma_gather": object gather fed by tensor copies where available
     int tc = 0;         // ptx_set_param "tc": TcForm of the column pass's DFT stages on the tensor cores (N = 256, K = 1)
@@ -486,9 +495,37 @@ std::vector<uint32_t> mask_bits(const KernelSet* ks, int N, const uint8_t* mask)
     return t;
 }
 
-ptx_status compute_layout(std::vector<ProbHost>& probs, size_t* spec_off, size_t* ctl_off, size_t* total) {
+// Region of the persistent schedule's tables (after the control block): the
+// problems' arguments, the segments and batches of the work list, the item
+// counter and the per-(batch, pass) done counters, sized for batches of one
+// frame (the most batches any schedule can have).
+struct PersLayout {
+    size_t prob = 0, seg = 0, batch = 0, ctl = 0, done = 0, end = 0;
+    size_t max_batches = 0;
+};
+PersLayout pers_layout(size_t base, size_t nprob, size_t frames) {
+    PersLayout L;
+    L.max_batches = frames;
+    size_t o = base;
+    L.prob = o;
+    o = align_up(o + sizeof(ProbArgs) * nprob);
+    L.seg = o;
+    o = align_up(o + sizeof(PSeg) * 3 * frames);
+    L.batch = o;
+    o = align_up(o + sizeof(PBatch) * frames);
+    L.ctl = o;
+    o = align_up(o + sizeof(PCtl));
+    L.done = o;
+    o = align_up(o + sizeof(unsigned) * 3 * frames);
+    L.end = o;
+    return L;
+}
+
+ptx_status compute_layout(std::vector<ProbHost>& probs, size_t* spec_off, size_t* ctl_off, size_t* total,
+                          size_t* pers_off = nullptr) {
     size_t o = 0;
     size_t spec = 0;
+    size_t frames = 0;
     for (auto& h : probs) {
         plan_problem(h);
         size_t sz = layout_problem(h);
@@ -514,9 +551,12 @@ ptx_status compute_layout(std::vector<ProbHost>& probs, size_t* spec_off, size_t
         o += sz;
         size_t s = (size_t)h.B * kDefaultLanes * h.p.K * h.p.N * h.p.N * sizeof(float2);
         if (s > spec) spec = s;
+        frames += (size_t)h.p.J;
     }
     *ctl_off = o;
     o = align_up(o + sizeof(Ctl));
+    if (pers_off) *pers_off = o;
+    o = pers_layout(o, probs.size(), frames).end;
     *spec_off = o;
     o = align_up(o + spec);
     *total = o;
@@ -645,6 +685,117 @@ ptx_status ensure_lanes(ptx_handle* h) {
     return PTX_OK;
 }
 
+// The persistent schedule serves handles whose problems all run the
+// register-resident one-mode far-field passes of its sizes, without a
+// background; other handles keep the per-batch launches.
+bool pers_eligible(const ptx_handle* h) {
+    if (h->probs.empty() || h->probs.size() > 64) return false;
+    const size_t slot_bytes = (h->spec_bytes / kPersSlots) / 256 * 256;
+    for (const ProbHost& ph : h->probs) {
+        if (!pers_supported_N(ph.p.N) || ph.p.K != 1 || ph.p.nearfield > 0.0 || ph.p.background) return false;
+        if (slot_bytes < (size_t)ph.p.N * ph.p.N * sizeof(float2)) return false;  // a slot holds a frame
+    }
+    return true;
+}
+
+// Work list of the persistent schedule (host): the batches of every problem
+// (work-stack slots of a third of the stack each), and the segments of their
+// items in pipeline order — step s: forward items of batch s, column items of
+// s - 1, backward items of s - 2.
+void pers_build(ptx_handle* h) {
+    const size_t slot_bytes = (h->spec_bytes / kPersSlots) / 256 * 256;
+    h->pers_prob.clear();
+    h->pers_seg.clear();
+    h->pers_batch.clear();
+    for (size_t pi = 0; pi < h->probs.size(); ++pi) {
+        const ProbHost& ph = h->probs[pi];
+        const ptx_problem& p = ph.p;
+        h->pers_prob.push_back(ph.args);
+        size_t B = slot_bytes / ((size_t)p.N * p.N * sizeof(float2));
+        if (h->batch_cap > 0 && B > (size_t)h->batch_cap) B = h->batch_cap;
+        B = std::max<size_t>(1, std::min<size_t>(B, (size_t)p.J));
+        const int L = ph.ks->reg_lines, C = ph.ks->reg_cols;
+        int per_sm = ph.ks->row_bwd_per_sm();
+        if (per_sm <= 0) per_sm = 2;
+        const int G0 = h->bwd_slots > 0 ? h->bwd_slots : std::max(1, per_sm * sm_count() / (p.N / L));
+        for (int j0 = 0; j0 < p.J; j0 += (int)B) {
+            const int nb = (int)std::min<size_t>(B, (size_t)(p.J - j0));
+            const int G = std::min(G0, nb);
+            PBatch bt{};
+            bt.prob = (int)pi;
+            bt.j0 = j0;
+            bt.nb = nb;
+            bt.G = G;
+            bt.n[0] = (unsigned)((p.N / L) * nb);
+            bt.n[1] = (unsigned)((p.N / C) * nb);
+            bt.n[2] = (unsigned)((p.N / L) * G);
+            h->pers_batch.push_back(bt);
+        }
+    }
+    const int nbatch = (int)h->pers_batch.size();
+    // self-test of the bounded waits: batch 0's column items wait for one
+    // forward item more than there are, so their wait runs out
+    if (h->pers_selftest && nbatch > 0) h->pers_batch[0].n[0] += 1;
+    long long start = 0;
+    for (int st = 0; st < nbatch + 2; ++st)
+        for (int pass = 0; pass < 3; ++pass) {
+            const int g = st - pass;
+            if (g < 0 || g >= nbatch) continue;
+            h->pers_seg.push_back(PSeg{g, pass, (int)start, 0});
+            start += h->pers_batch[g].n[pass] - (h->pers_selftest && g == 0 && pass == 0 ? 1 : 0);
+        }
+    h->pers_nbatch = nbatch;
+    h->pers_nseg = (int)h->pers_seg.size();
+    h->pers_nitems = (int)start;
+}
+
+// Upload the tables (before the cycle's graph is launched; outside any capture).
+ptx_status pers_upload(ptx_handle* h, cudaStream_t s) {
+    size_t frames = 0;
+    for (const ProbHost& ph : h->probs) frames += (size_t)ph.p.J;
+    const PersLayout L = pers_layout(h->pers_off, h->probs.size(), frames);
+    pers_build(h);
+    if ((size_t)h->pers_nbatch > L.max_batches) return fail(PTX_ERR_NOT_READY, "persistent work list too long");
+    cudaError_t e = cudaMemcpyAsync(h->scratch + L.prob, h->pers_prob.data(), sizeof(ProbArgs) * h->pers_prob.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->scratch + L.seg, h->pers_seg.data(), sizeof(PSeg) * h->pers_seg.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->scratch + L.batch, h->pers_batch.data(), sizeof(PBatch) * h->pers_batch.size(),
+                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "uploading the persistent work list");
+    h->pers_dirty = false;
+    return PTX_OK;
+}
+
+// The batch passes of every problem as one persistent launch, after zeroing its counters.
+void enqueue_persistent(ptx_handle* h, const std::vector<int>& algos, bool init, cudaStream_t s) {
+    size_t frames = 0;
+    for (const ProbHost& ph : h->probs) frames += (size_t)ph.p.J;
+    const PersLayout L = pers_layout(h->pers_off, h->probs.size(), frames);
+    cudaMemsetAsync(h->scratch + L.ctl, 0, L.end - L.ctl, s);
+    PersArgs pa{};
+    pa.seg = (const PSeg*)(h->scratch + L.seg);
+    pa.nseg = h->pers_nseg;
+    pa.nitems = h->pers_nitems;
+    pa.batch = (const PBatch*)(h->scratch + L.batch);
+    pa.nbatch = h->pers_nbatch;
+    pa.prob = (const ProbArgs*)(h->scratch + L.prob);
+    pa.spec = (float2*)(h->scratch + h->spec_off);
+    pa.slot_elems = (h->spec_bytes / kPersSlots) / 256 * 256 / sizeof(float2);
+    pa.ctl = (PCtl*)(h->scratch + L.ctl);
+    pa.done = (unsigned*)(h->scratch + L.done);
+    pa.err_flag = h->err_dev;
+    pa.dm_mask = 0;
+    for (size_t i = 0; i < algos.size(); ++i)
+        if (algos[i] == ALGO_DM) pa.dm_mask |= 1ull << i;
+    pa.init = init ? 1 : 0;
+    const int per_sm = std::max(1, pers_blocks_per_sm());
+    ProfScope ps(h, PTX_KERNEL_ROW_FWD, s);
+    launch_cycle_persistent(pa, per_sm * sm_count(), s);
+}
+
 // Number format of the column pass's DFT stages for a call: a PTX_FORM_* flag,
 // else the handle's "tc" parameter.
 int tc_form(const ptx_handle* h, uint32_t flags) {
@@ -667,6 +818,23 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
     const bool init = flags & PTX_DM_INIT_PSI;
     const int np = (int)h->probs.size();
     const int lanes = h->profiling ? 1 : h->lanes;  // per-kernel timing wants kernels alone
+    const bool pers = h->persistent && !h->profiling && pers_eligible(h) && !(flags & PTX_UPDATE_BACKGROUND) &&
+                      form == TC_NONE;
+    if (pers) {
+        enqueue_persistent(h, algos, init, s);
+        for (int pi = 0; pi < np; ++pi) {
+            ProbHost& ph = h->probs[pi];
+            const ProbArgs& a = ph.args;
+            if (!(flags & PTX_NO_NORMALISE))
+                enqueue_stages(h, ph, (upd_p ? STAGE_PROBE : 0) | (upd_o ? STAGE_OBJ_GATHER | STAGE_OBJ_NORMALISE : 0),
+                               s);
+            ProfScope ps(h, PTX_KERNEL_CYCLE_END, s);
+            k_cycle_end<<<kCycleEndBlocks, 256, 0, s>>>(h->ctl, a, pi, a.N / a.C2, pi == np - 1);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+        return PTX_OK;
+    }
     if (lanes > 1) {
         ptx_status st = ensure_lanes(h);
         if (st != PTX_OK) return st;
@@ -847,6 +1015,10 @@ ptx_status run_cycles(ptx_handle* h, const std::vector<int>& algos, int ncycles,
     }
     if (ncycles == 0) return PTX_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    if (h->persistent && h->pers_dirty && pers_eligible(h)) {
+        drop_graphs(h);  // they hold the old work list's sizes
+        if ((st = pers_upload(h, s)) != PTX_OK) return st;
+    }
     k_set_ctl<<<1, 1, 0, s>>>(h->ctl, llk_dev, (int)h->probs.size());
     const bool graph = !(flags & PTX_NO_GRAPH) && !h->profiling;
     const uint32_t base = flags & (PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_NO_NORMALISE | PTX_UPDATE_BACKGROUND | forms);
@@ -901,7 +1073,8 @@ ptx_status ptx_create(ptx_handle** out, const ptx_problem* probs, int32_t nprob,
         build_tiles(v[i], probs[i].positions);
     }
     size_t spec_off, ctl_off, total;
-    compute_layout(v, &spec_off, &ctl_off, &total);
+    size_t pers_off = 0;
+    compute_layout(v, &spec_off, &ctl_off, &total, &pers_off);
     if (scratch_bytes < total)
         return fail(PTX_ERR_NOT_READY, "scratch of %zu bytes is smaller than the %zu needed", scratch_bytes, total);
     cudaError_t e = ensure_attributes();
@@ -912,6 +1085,7 @@ ptx_status ptx_create(ptx_handle** out, const ptx_problem* probs, int32_t nprob,
     h->scratch_bytes = scratch_bytes;
     h->spec_off = spec_off;
     h->ctl_off = ctl_off;
+    h->pers_off = pers_off;
     h->spec_bytes = total - spec_off;
     h->ctl = (Ctl*)(h->scratch + ctl_off);
     cudaGetDevice(&h->device);
@@ -1007,6 +1181,7 @@ ptx_status ptx_cycle_kernels(ptx_handle* h, int32_t algorithm, uint32_t flags, i
     const uint32_t f = flags & (PTX_UPDATE_OBJ | PTX_UPDATE_PROBE | PTX_NO_NORMALISE | PTX_UPDATE_BACKGROUND |
                                 PTX_DM_INIT_PSI | PTX_FORM_TF32X2 | PTX_FORM_BF16X3 | PTX_FORM_BF16X2);
     const std::vector<int> algos(h->probs.size(), algorithm);
+    if (h->persistent && h->pers_dirty && pers_eligible(h)) pers_build(h);  // sizes only; uploaded by the next cycle call
     cudaGraphExec_t ex;
     if ((st = get_graph(h, algos, f, &ex)) != PTX_OK) return st;
     GraphKey key{algos, f, h->lanes, h->tma | (h->tma_gather << 1) | (h->tc << 2)};
@@ -1257,6 +1432,12 @@ ptx_status ptx_set_param(ptx_handle* h, const char* name, double value) {
         if (value != (int)value || value < 0 || value > 4096)
             return fail(PTX_ERR_INVALID_ARG, "bwd_slots must be an integer in 0..4096");
         h->bwd_slots = (int)value;
+    } else if (!strcmp(name, "persistent")) {
+        if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "persistent must be 0 or 1");
+        h->persistent = (int)value;
+    } else if (!strcmp(name, "persistent_selftest")) {
+        if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "persistent_selftest must be 0 or 1");
+        h->pers_selftest = (int)value;
     } else if (!strcmp(name, "batch_frames")) {
         if (value != (int)value || value > 32768)
             return fail(PTX_ERR_INVALID_ARG, "batch_frames must be an integer in 0..32768");
@@ -1265,6 +1446,7 @@ ptx_status ptx_set_param(ptx_handle* h, const char* name, double value) {
         return fail(PTX_ERR_INVALID_ARG, "unknown parameter '%s'", name);
     }
     drop_graphs(h);  // the captured graphs hold the old value
+    h->pers_dirty = true;
     return PTX_OK;
 }
 

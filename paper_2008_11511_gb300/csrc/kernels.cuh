@@ -580,6 +580,47 @@ struct TileLists {
 __global__ void k_obj_gather(ProbArgs a, TileLists tl, int fuse_max);
 // Column pass with the 16-point DFT stages on the tensor cores (tcgen05, TF32
 // hi + lo split; N = 256, one mode), the split-precision form of k_col_r<256>.
+// Persistent schedule of the cycle's batch passes (persistent.cu).  A segment
+// is the run of work items of one pass of one batch; items are numbered in
+// list order and a segment's start is the number of its first item.
+constexpr int kPersSlots = 3;  // work-stack slots (batches in flight)
+struct PSeg {
+    int g;       // batch
+    int pass;    // 0 forward row pass, 1 column pass, 2 backward row pass
+    int start;   // first item
+    int pad;
+};
+struct PBatch {
+    int prob;      // problem index
+    int j0, nb;    // first frame and frame count
+    int G;         // frame slots of the backward row pass
+    unsigned n[3]; // items of each pass
+    int pad;
+};
+struct PCtl {
+    unsigned head;  // next item to hand out
+    int abort;      // set by a wait that gave up: blocks stop taking items
+};
+struct PersArgs {
+    const PSeg* seg;
+    int nseg, nitems;
+    const PBatch* batch;
+    int nbatch;
+    const ProbArgs* prob;   // [problems] (spec set per batch from its slot)
+    float2* spec;           // slot 0 of the work stack
+    size_t slot_elems;      // complex elements per slot
+    PCtl* ctl;              // zeroed before each launch
+    unsigned* done;         // [3 nbatch] finished items per (batch, pass), zeroed before each launch
+    int* err_flag;          // host-mapped error flag or null
+    unsigned long long dm_mask;  // problems whose forward pass forms 2 Phi - Psi
+    int init;               // DM's first cycle (Psi = Phi): forward passes form Phi
+};
+size_t pers_smem();
+bool pers_supported_N(int N);
+cudaError_t set_attrs_persistent();
+int pers_blocks_per_sm();
+void launch_cycle_persistent(const PersArgs& pa, int grid, cudaStream_t s);
+
 // Number formats of the tensor-core column pass (ptx_set_param "tc" and the
 // PTX_FORM_* cycle flags): TF32 hi + lo, BF16 hi + mid + lo, BF16 hi + lo.
 enum TcForm : int { TC_NONE = 0, TC_TF32X2 = 1, TC_BF16X3 = 2, TC_BF16X2 = 3 };

@@ -72,65 +72,11 @@ __device__ __forceinline__ float2 tw_get(const float2* tw, int a, int b) {
 // ---------------------------------------------------------------------------
 template <int N, bool kDM>
 __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_r(ProbArgs a, int j0) {
-    using S = RegShape<N>;
-    constexpr int R = S::R, M = S::M, L = S::L, P = S::P;
-    extern __shared__ __align__(16) float2 sm[];
-    float2* tw = sm;
-    float2* buf = sm + N;
-    load_twiddles<N>(tw);
-    const int K = a.K;
-    const int y0 = blockIdx.x * L;
-    const int b = blockIdx.y / K, k = blockIdx.y - b * K;
-    const int j = j0 + b;
-    const int2 p = a.pos[j];
-    const float2* probe = a.probe + (size_t)k * N * N;
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < S::I1; ++i) {
-        const int w = threadIdx.x + i * kThreads;
-        if (w < L * M) {
-            const int line = w / M, n1 = w - line * M;
-            const int y = y0 + line;
-            const float2* pr = probe + (size_t)y * N + n1;
-            const float2* ob = a.obj + (size_t)(p.x + y) * a.Wo + p.y + n1;
-            float2 q[kDM ? R : 1];
-            if constexpr (kDM) {
-                const float2* ps = a.psi + (((size_t)j * K + k) * N + y) * N + n1;
-                const uint64_t ef = policy_evict_first();
-#pragma unroll
-                for (int n2 = 0; n2 < R; ++n2) q[n2] = ld_hint(ps + M * n2, ef);
-            }
-            float2 v[R];
-#pragma unroll
-            for (int n2 = 0; n2 < R; ++n2) v[n2] = cmul(__ldg(pr + M * n2), ob[M * n2]);
-            if constexpr (kDM) {
-#pragma unroll
-                for (int n2 = 0; n2 < R; ++n2) v[n2] = make_float2(2.f * v[n2].x - q[n2].x, 2.f * v[n2].y - q[n2].y);
-            }
-            Dft<R, -1>::run(v);
-            float2* o = buf + line * P + n1;
-            o[0] = v[0];
-#pragma unroll
-            for (int k2 = 1; k2 < R; ++k2) o[k2 * (M + 1)] = cmul(v[k2], tw_get<N, -1>(tw, k2, n1));
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < S::I2; ++i) {
-        const int w = threadIdx.x + i * kThreads;
-        if (w < L * R) {
-            const int line = w / R, k2 = w - line * R;
-            float2 u[M];
-            const float2* src = buf + line * P + k2 * (M + 1);
-#pragma unroll
-            for (int n1 = 0; n1 < M; ++n1) u[n1] = src[n1];
-            Dft<M, -1>::run(u);
-            float2* dst = a.spec + (((size_t)b * K + k) * N + y0 + line) * N + k2;
-            const uint64_t el = policy_evict_last();
-#pragma unroll
-            for (int k1 = 0; k1 < M; ++k1) st_hint(dst + R * k1, u[k1], el);
-        }
-    }
+#define PTX_BX blockIdx.x
+#define PTX_BY blockIdx.y
+#include "body_row_fwd.inc"
+#undef PTX_BX
+#undef PTX_BY
 }
 
 // ---------------------------------------------------------------------------
@@ -143,142 +89,13 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_r(
 // comes from the argument.
 template <int N, bool kBg, bool kCycle>
 __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_r(ProbArgs a, int j0, int mode_arg) {
-    const int mode = kCycle ? (int)COL_PROJECT : mode_arg;
-    using S = RegShape<N>;
-    constexpr int R = S::R, M = S::M, C = S::C, P = S::P;
-    constexpr int I1b = (C * M + kThreads - 1) / kThreads;  // inverse pass-2 items (M per column)
-    static_assert(C % 8 == 0 && (C * P) % 2 == 0, "8- / 16-byte chunks and a 16-byte aligned stage");
-    extern __shared__ __align__(16) float2 sm[];
-    __shared__ double red_s[kThreads / 32];
-    float2* tw = sm;
-    float2* buf = sm + N;
-    load_twiddles<N>(tw);
-    const int x0 = blockIdx.x * C;
-    const int b = blockIdx.y;
-    const int j = j0 + b;
-    float2* spec = a.spec + (size_t)b * N * N + x0;
-    // intensities of this thread's pass-2 pixels (rows k2 + R k1 of column c),
-    // loaded into registers while the forward transform runs, and their mask bits
-    float io_r[S::CI2][M];
-#pragma unroll
-    for (int i = 0; i < S::CI2; ++i) {
-        const int w = threadIdx.x + i * kThreads;
-        if (w < C * R) {
-            const int k2 = w / C, c = w - k2 * C;
-            const float* ib = a.iobs + (size_t)j * N * N + (size_t)k2 * N + x0 + c;
-#pragma unroll
-            for (int k1 = 0; k1 < M; ++k1) io_r[i][k1] = __ldcs(ib + (size_t)R * k1 * N);
-        }
-    }
-    uint32_t mbits = 0u;
-    if (a.mbits) {
-        mbits = a.mbits[blockIdx.x * kThreads + threadIdx.x];
-    } else {  // callers without the table (the allocation-free entry point) read the mask bytes
-#pragma unroll
-        for (int i = 0; i < S::CI2; ++i) {
-            const int w = threadIdx.x + i * kThreads;
-            if (w < C * R) {
-                const int k2 = w / C, c = w - k2 * C;
-#pragma unroll
-                for (int k1 = 0; k1 < M; ++k1)
-                    mbits |= (a.mask[(size_t)(k2 + R * k1) * N + x0 + c] != 0) ? (1u << (i * M + k1)) : 0u;
-            }
-        }
-    }
-    __syncthreads();
-    // forward pass 1: thread (c, n1) holds rows n1 + M n2 of column c
-#pragma unroll
-    for (int i = 0; i < S::CI1; ++i) {
-        const int w = threadIdx.x + i * kThreads;
-        if (w < C * M) {
-            const int n1 = w / C, c = w - n1 * C;
-            float2 v[R];
-            const uint64_t el = policy_evict_last();
-#pragma unroll
-            for (int n2 = 0; n2 < R; ++n2) v[n2] = ld_hint(spec + (size_t)(n1 + M * n2) * N + c, el);
-            Dft<R, -1>::run(v);
-            float2* o = buf + c * P + n1;
-            o[0] = v[0];
-#pragma unroll
-            for (int k2 = 1; k2 < R; ++k2) o[k2 * (M + 1)] = cmul(v[k2], tw_get<N, -1>(tw, k2, n1));
-        }
-    }
-    __syncthreads();
-    // forward pass 2 into registers: thread (c, k2) holds X^[k2 + R k1]
-    float2 u[S::CI2][M];
-#pragma unroll
-    for (int i = 0; i < S::CI2; ++i) {
-        const int w = threadIdx.x + i * kThreads;
-        if (w < C * R) {
-            const int k2 = w / C, c = w - k2 * C;
-            const float2* src = buf + c * P + k2 * (M + 1);
-#pragma unroll
-            for (int n1 = 0; n1 < M; ++n1) u[i][n1] = src[n1];
-        }
-    }
-    __syncthreads();
-    constexpr float invN2 = 1.0f / float(N * N);
-    float llk = 0.f;  // the terms are >= 0: a plain float sum of a thread's pixels
-#pragma unroll
-    for (int i = 0; i < S::CI2; ++i) {
-        const int w = threadIdx.x + i * kThreads;
-        if (w < C * R) {
-            const int k2 = w / C, c = w - k2 * C;
-            Dft<M, -1>::run(u[i]);
-#pragma unroll
-            for (int k1 = 0; k1 < M; ++k1) {
-                float ic = cnorm(u[i][k1]) * invN2;
-                const float io = io_r[i][k1];
-                const bool masked = (mbits >> (i * M + k1)) & 1u;
-                if constexpr (kBg) {  // incoherent background: one more component of the model intensity
-                    const int pix = (k2 + R * k1) * N + x0 + c;
-                    ic += __ldg(a.bg + pix);
-                    if (a.bg_acc && !masked) atomicAdd(a.bg_acc + pix, fmaxf(io, 0.f) / fmaxf(ic, 1e-30f));
-                }
-                float f;
-                if (mode == COL_PROJECT) {
-                    float ratio;
-                    const float term = llk_term_ratio(ic, io, ratio);
-                    if (!masked) llk += term;
-                    f = masked ? 0.f : (ratio - 1.0f) * invN2;
-                } else {
-                    if (!masked) llk += llk_term_fast(ic, io);
-                    f = masked ? 0.f : 2.0f * (1.0f - __fdividef(fmaxf(io, 0.f), fmaxf(ic, 1e-30f))) * invN2;
-                }
-                u[i][k1] = cscale(u[i][k1], f);
-            }
-            if (mode != COL_LLK) {
-                // inverse pass 1: M-point codelet over k1, twiddle w_N^(+k2 k2'),
-                // y'[k2' (R+1) + k2]
-                Dft<M, +1>::run(u[i]);
-                float2* o = buf + c * P + k2;
-                o[0] = u[i][0];
-#pragma unroll
-                for (int kk = 1; kk < M; ++kk) o[kk * (R + 1)] = cmul(u[i][kk], tw_get<N, +1>(tw, k2, kk));
-            }
-        }
-    }
-    double tot = block_sum_pos<kThreads>(llk, red_s);
-    if (threadIdx.x == 0) a.llk_part[(size_t)j * gridDim.x + blockIdx.x] = tot;
-    if (mode == COL_LLK) return;
-    __syncthreads();
-    // inverse pass 2: thread (c, k2') reads y'[k2' (R+1) + n1'], R-point codelet,
-    // rows k2' + M k1'
-#pragma unroll
-    for (int i = 0; i < I1b; ++i) {
-        const int w = threadIdx.x + i * kThreads;
-        if (w < C * M) {
-            const int kk = w / C, c = w - kk * C;
-            float2 v[R];
-            const float2* src = buf + c * P + kk * (R + 1);
-#pragma unroll
-            for (int n = 0; n < R; ++n) v[n] = src[n];
-            Dft<R, +1>::run(v);
-            const uint64_t el = policy_evict_last();
-#pragma unroll
-            for (int k1 = 0; k1 < R; ++k1) st_hint(spec + (size_t)(kk + M * k1) * N + c, v[k1], el);
-        }
-    }
+#define PTX_BX blockIdx.x
+#define PTX_BY blockIdx.y
+#define PTX_GX gridDim.x
+#include "body_col.inc"
+#undef PTX_BX
+#undef PTX_BY
+#undef PTX_GX
 }
 
 // ---------------------------------------------------------------------------
@@ -478,203 +295,13 @@ __device__ __forceinline__ float2 tw_bwd(const float2* tw, int a, int b) {
 template <int N, int kForm>
 __global__ void __launch_bounds__(kThreads, 2) k_row_bwd_r(ProbArgs a, int j0, int nb, int mode_arg, int upd_obj_arg,
                                                            int upd_probe_arg) {
-    const int mode = kForm == 1 ? (int)BWD_DM : kForm == 2 ? (int)BWD_GRAD : mode_arg;
-    const int upd_probe = kForm == 1 ? 1 : kForm == 2 ? 0 : upd_probe_arg;
-    const int upd_obj = kForm == 2 ? 1 : upd_obj_arg;
-    using S = BwdShape<N>;
-    constexpr int R = S::R, M = S::M, L = S::L, P = reg_pitch<N>();
-    constexpr bool kRegAcc = S::kRegAcc;
-    constexpr int IA = kRegAcc ? S::I2 : 1, MA = kRegAcc ? M : 1;
-    extern __shared__ __align__(16) float2 sm[];
-    float2* tw = sm;
-    // object rows are staged too when the probe sums live in registers (the
-    // shared-memory budget of the large sizes has no room for them)
-    constexpr bool kStageObj = kRegAcc;
-    float2* stage = sm + N;                     // [L][N] next frame's rows (cp.async)
-    float2* ostage = stage + L * N;             // [L][N] next frame's object rows (cp.async)
-    float2* buf = ostage + (kStageObj ? L * N : 0);
-    float2* np_s = buf + L * P;                 // [L][N] when !kRegAcc
-    float* dp_s = (float*)(np_s + L * N);       // [L][N]
-    load_twiddles<N>(tw);
-    const int K = a.K;
-    const int y0 = blockIdx.x * L;
-    const int slot = blockIdx.y / K, k = blockIdx.y - slot * K;
-    const int G = gridDim.y / K;
-    const size_t mode_off = (size_t)k * N * N;  // probe mode k
-    const bool acc_p = upd_probe != 0;
-    // the rows [y0, y0 + L) of frame b are contiguous: copy them in 16-byte chunks
-    // The work-stack stage is free once pass 1 has read it; the object stage only
-    // after the update that reads it, so the two are refilled at different points.
-    auto prefetch_spec = [&](int b) {
-        const float2* src = a.spec + (((size_t)b * K + k) * N + y0) * N;
-        const uint64_t ef = policy_evict_first();  // the stack's last read
-        for (int e = threadIdx.x; e < L * N / 2; e += kThreads) cp_async16_hint(stage + 2 * e, src + 2 * e, ef);
-        cp_async_commit();
-    };
-    auto prefetch_obj = [&](int b) {
-        if (kStageObj && (mode != BWD_GRAD || acc_p)) {
-            // object patch rows: 8-byte aligned only (arbitrary column offset)
-            const int2 q = a.pos[j0 + b];
-            for (int e = threadIdx.x; e < L * N; e += kThreads) {
-                const int line = e / N, x = e - line * N;
-                cp_async8(ostage + e, a.obj + (size_t)(q.x + y0 + line) * a.Wo + q.y + x);
-            }
-        }
-        cp_async_commit();
-    };
-    if (slot < nb) {
-        prefetch_spec(slot);
-        prefetch_obj(slot);
-    }
-    const bool acc_o = upd_obj != 0;
-    float2 np_r[IA][MA];
-    float dp_r[IA][MA];
-#pragma unroll
-    for (int i = 0; i < IA; ++i)
-#pragma unroll
-        for (int k1 = 0; k1 < MA; ++k1) {
-            np_r[i][k1] = make_float2(0.f, 0.f);
-            dp_r[i][k1] = 0.f;
-        }
-    if (!kRegAcc && acc_p) {
-        for (int e = threadIdx.x; e < L * N; e += kThreads) {
-            np_s[e] = make_float2(0.f, 0.f);
-            dp_s[e] = 0.f;
-        }
-    }
-    // the block's probe rows are the same for all its frames: this thread's
-    // pass-2 pixels stay in registers (one-mode sizes with register sums)
-    // (the sizes with a 28- or 32-point first factor read it from L1 instead:
-    // their pass-1 values would push it out of the registers)
-    constexpr bool kRegProbe = kRegAcc && R < 28;
-    float2 pr_r[kRegProbe ? S::I2 : 1][kRegProbe ? M : 1];
-    if constexpr (kRegProbe) {
-#pragma unroll
-        for (int i = 0; i < S::I2; ++i) {
-            const int w = threadIdx.x + i * kThreads;
-            if (w < L * R) {
-                const int line = w / R, k2 = w - line * R;
-                const float2* pr = a.probe + mode_off + (size_t)(y0 + line) * N + k2;
-#pragma unroll
-                for (int k1 = 0; k1 < M; ++k1) pr_r[i][k1] = __ldg(pr + R * k1);
-            }
-        }
-    }
-    __syncthreads();
-    for (int b = slot; b < nb; b += G) {
-        const int j = j0 + b;
-        const int2 p = a.pos[j];
-        cp_async_wait_all();
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < S::I1; ++i) {
-            const int w = threadIdx.x + i * kThreads;
-            if (w < L * M) {
-                const int line = w / M, n1 = w - line * M;
-                const float2* src = stage + line * N + n1;
-                float2 v[R];
-#pragma unroll
-                for (int n2 = 0; n2 < R; ++n2) v[n2] = src[M * n2];
-                Dft<R, +1>::run(v);
-                float2* o = buf + line * P + n1;
-                o[0] = v[0];
-#pragma unroll
-                for (int k2 = 1; k2 < R; ++k2) o[k2 * (M + 1)] = cmul(v[k2], tw_bwd<N>(tw, k2, n1));
-            }
-        }
-        __syncthreads();
-        if (b + G < nb) prefetch_spec(b + G);  // the work-stack stage is free again
-#pragma unroll
-        for (int i = 0; i < S::I2; ++i) {
-            const int w = threadIdx.x + i * kThreads;
-            if (w < L * R) {
-                const int line = w / R, k2 = w - line * R;
-                const int y = y0 + line;
-                float2 u[M];
-                const float2* src = buf + line * P + k2 * (M + 1);
-#pragma unroll
-                for (int n1 = 0; n1 < M; ++n1) u[n1] = src[n1];
-                Dft<M, +1>::run(u);
-                const float2* pr = a.probe + mode_off + (size_t)y * N + k2;
-                const size_t orow = (size_t)(p.x + y) * a.Wo + p.y + k2;
-                const float2* ob = (kStageObj && (mode != BWD_GRAD || acc_p)) ? ostage + line * N + k2 : a.obj + orow;
-                float2* ps = (mode != BWD_GRAD) ? a.psi + (((size_t)j * K + k) * N + y) * N + k2 : nullptr;
-#pragma unroll
-                for (int k1 = 0; k1 < M; ++k1) {
-                    float2 prv;
-                    if constexpr (kRegProbe)
-                        prv = pr_r[i][k1];
-                    else
-                        prv = __ldg(pr + R * k1);
-                    const float2 obv = ob[R * k1];
-                    float2 wv;
-                    if (mode == BWD_GRAD) {
-                        wv = u[k1];
-                        if (acc_o) {
-                            const float2 t = cconjmul(prv, wv);
-                            red_add_v2(a.grad_obj + orow + R * k1, t.x, t.y);
-                        }
-                    } else {
-                        wv = cadd(cmul(prv, obv), u[k1]);
-                        __stcs(ps + R * k1, wv);
-                    }
-                    if (acc_p) {
-                        const float2 t = cconjmul(obv, wv);
-                        if constexpr (kRegAcc) {
-                            np_r[i][k1].x += t.x;
-                            np_r[i][k1].y += t.y;
-                            dp_r[i][k1] += cnorm(obv);
-                        } else {
-                            const int e = line * N + k2 + R * k1;
-                            np_s[e].x += t.x;
-                            np_s[e].y += t.y;
-                            dp_s[e] += cnorm(obv);
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        if (b + G < nb) prefetch_obj(b + G);  // the object stage is free again
-    }
-    if (acc_p) {
-        if constexpr (kRegAcc) {
-#pragma unroll
-            for (int i = 0; i < S::I2; ++i) {
-                const int w = threadIdx.x + i * kThreads;
-                if (w < L * R) {
-                    const int line = w / R, k2 = w - line * R;
-                    const size_t pidx = mode_off + (size_t)(y0 + line) * N + k2;
-#pragma unroll
-                    for (int k1 = 0; k1 < M; ++k1) {
-                        if (mode == BWD_GRAD)
-                            red_add_v2(a.grad_probe + pidx + R * k1, np_r[i][k1].x, np_r[i][k1].y);
-                        else
-                            red_add_v4(a.acc_probe + pidx + R * k1, np_r[i][k1].x, np_r[i][k1].y, dp_r[i][k1],
-                                       0.f);
-                    }
-                }
-            }
-        } else {
-            // each thread flushes the pixels it accumulated (same mapping as above)
-#pragma unroll
-            for (int i = 0; i < S::I2; ++i) {
-                const int w = threadIdx.x + i * kThreads;
-                if (w < L * R) {
-                    const int line = w / R, k2 = w - line * R;
-                    const size_t pidx = mode_off + (size_t)(y0 + line) * N + k2;
-#pragma unroll 4
-                    for (int k1 = 0; k1 < M; ++k1) {
-                        const int e = line * N + k2 + R * k1;
-                        if (mode == BWD_GRAD)
-                            red_add_v2(a.grad_probe + pidx + R * k1, np_s[e].x, np_s[e].y);
-                        else
-                            red_add_v4(a.acc_probe + pidx + R * k1, np_s[e].x, np_s[e].y, dp_s[e], 0.f);
-                    }
-                }
-            }
-        }
-    }
+#define PTX_BX blockIdx.x
+#define PTX_BY blockIdx.y
+#define PTX_GY gridDim.y
+#include "body_row_bwd.inc"
+#undef PTX_BX
+#undef PTX_BY
+#undef PTX_GY
 }
 
 // ---------------------------------------------------------------------------

@@ -138,3 +138,76 @@ def test_autotune_restores_state_and_sets_a_schedule():
     assert rel(pb.obj.cpu().numpy(), ref.obj.cpu().numpy()) < 1e-6
     pb.close()
     ref.close()
+
+
+def _cycle_kernels(pb, algo):
+    import ctypes
+    from paper_2008_11511_gb300 import _lib
+    n = ctypes.c_int64()
+    _lib.call("ptx_cycle_kernels", pb._handle(), algo, _lib.PTX_UPDATE_OBJ | _lib.PTX_UPDATE_PROBE, ctypes.byref(n))
+    return n.value
+
+
+def test_persistent_schedule_matches_oracle_per_problem():
+    """The batch passes of five scans (128^2 to 512^2, AP and DM alternately) as
+    one persistent launch per cycle: each problem against its own FP64 oracle
+    cycle, and three cycles against the per-batch launches."""
+    from paper_2008_11511_gb300 import PtychoBatch, _lib
+    probs = _problems()[:5]
+    algos = ["AP" if i % 2 == 0 else "DM" for i in range(len(probs))]
+    items = [dict(obj=dev(o0), probe=dev(p0), iobs=dev(s.iobs), positions=s.positions, mask=s.mask)
+             for s, data, o0, p0 in probs]
+    pb = PtychoBatch(items)
+    n_batches = _cycle_kernels(pb, _lib.PTX_ALGO_DM)
+    pb.set_param("persistent", 1)
+    n_pers = _cycle_kernels(pb, _lib.PTX_ALGO_DM)
+    assert n_pers < n_batches  # one launch replaces the per-batch launches
+    llk = pb.cycles(1, algos, init_psi=True).cpu().numpy()
+    for i, ((s, data, o0, p0), a) in enumerate(zip(probs, algos)):
+        if a == "AP":
+            o, p, l = oracle.ap_cycle(o0, p0, data)
+        else:
+            o, p, psi, l = oracle.dm_cycle(o0, p0, None, data, init_psi=True)
+            assert rel(pb.items[i]["psi"].cpu().numpy(), psi) < TOL1, i
+        assert rel(pb.items[i]["obj"].cpu().numpy(), o) < TOL1, (i, a)
+        assert rel(pb.items[i]["probe"].cpu().numpy(), p) < TOL1, (i, a)
+        assert abs(llk[0, i] - l) < TOL1 * abs(l), (i, llk[0, i], l)
+    pb.close()
+    # three cycles, persistent against per-batch launches, with small batches (many slots reused)
+    ref = PtychoBatch([dict(obj=dev(o0), probe=dev(p0), iobs=dev(s.iobs), positions=s.positions, mask=s.mask)
+                       for s, data, o0, p0 in probs])
+    per = PtychoBatch([dict(obj=dev(o0), probe=dev(p0), iobs=dev(s.iobs), positions=s.positions, mask=s.mask)
+                       for s, data, o0, p0 in probs])
+    per.set_param("persistent", 1)
+    per.set_param("batch_frames", 7)
+    l_ref = ref.cycles(3, algos, init_psi=True).cpu().numpy()
+    l_per = per.cycles(3, algos, init_psi=True).cpu().numpy()
+    np.testing.assert_allclose(l_per, l_ref, rtol=1e-5)
+    for i in range(len(probs)):
+        assert rel(per.items[i]["obj"].cpu().numpy(), ref.items[i]["obj"].cpu().numpy()) < 1e-5
+        assert rel(per.items[i]["probe"].cpu().numpy(), ref.items[i]["probe"].cpu().numpy()) < 1e-5
+    ref.close()
+    per.close()
+
+
+def test_persistent_schedule_wait_gives_up_and_reports():
+    """A dependency that is never met (the self-test switch) makes the
+    persistent launch's bounded wait give up: the next call reports
+    PTX_ERR_TIMEOUT once, and the handle then runs correct cycles again."""
+    from paper_2008_11511_gb300 import PtychoBatch, PtychoError
+    probs = _problems()[2:3]
+    s, data, o0, p0 = probs[0]
+    pb = PtychoBatch([dict(obj=dev(o0), probe=dev(p0), iobs=dev(s.iobs), positions=s.positions, mask=s.mask)])
+    pb.set_param("persistent", 1)
+    pb.set_param("persistent_selftest", 1)
+    pb.cycles(1, ["AP"])
+    torch.cuda.synchronize()
+    with pytest.raises(PtychoError, match="TIMEOUT"):
+        pb.cycles(1, ["AP"])
+    pb.set_param("persistent_selftest", 0)
+    pb.items[0]["obj"].copy_(dev(o0))
+    pb.items[0]["probe"].copy_(dev(p0))
+    pb.cycles(1, ["AP"])
+    o, p, _ = oracle.ap_cycle(o0, p0, data)
+    assert rel(pb.items[0]["obj"].cpu().numpy(), o) < TOL1
+    pb.close()
