@@ -405,6 +405,15 @@ def run_extra_modes(dev, pk, ws, J=1500, H=2800):
     pb.dm(2, llk=llk)
     torch.cuda.synchronize(dev)
     ms = _events_ms(lambda: pb.dm(3, llk=llk), 3, stream) / 3
+    # the same cycle with the column pass's DFT stages on the tensor cores
+    forms = []
+    for tc in (1, 2, 3):
+        pb.set_param("tc", tc)
+        pb.dm(1, llk=llk)
+        torch.cuda.synchronize(dev)
+        ms_f = _events_ms(lambda: pb.dm(3, llk=llk), 2, stream) / 3
+        forms.append({"form": FORMS[tc], "ms_per_cycle": ms_f, "frames_per_s": s.J * ws / (ms_f * 1e-3)})
+    pb.set_param("tc", 0)
     pb.close()
     px = s.N * s.N
     b = s.J * s.K * px * 16 + s.J * px * 4 + s.Ho * s.Wo * 16 + s.K * px * 16
@@ -412,7 +421,7 @@ def run_extra_modes(dev, pk, ws, J=1500, H=2800):
     return {"workload": f"DM cycle, {s.J} frames {s.N}x{s.N}, K={s.K} modes, object {s.Ho}x{s.Wo}, "
                         f"{s.photons:.0e} photons/frame (first {J} positions of the 10000-position scan)",
             "ms_per_cycle": ms, "frames_per_s": s.J * ws / (ms * 1e-3),
-            "frame_modes_per_s": s.J * s.K * ws / (ms * 1e-3),
+            "frame_modes_per_s": s.J * s.K * ws / (ms * 1e-3), "other_form": forms,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                          "frac": gbs / pk["hbm_gbs"], "alg_bytes_per_cycle": b, "peak_src": pk["src"]}}
 

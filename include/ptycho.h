@@ -55,8 +55,9 @@ typedef enum {
 #define PTX_NO_NORMALISE 0x8u  /* accumulate N_O, D_O, N_P, D_P but do not normalise (data-parallel split) */
 #define PTX_NO_GRAPH     0x10u /* enqueue kernels directly instead of replaying a captured CUDA graph */
 #define PTX_UPDATE_BACKGROUND 0x40u /* AP only: update the incoherent background of the problems that have one */
-/* Number format of the column pass's 16-point DFT stages (one-mode problems
- * with N = 256; other problems run FP32).  No PTX_FORM_* flag: the handle's
+/* Number format of the column pass's DFT stages (problems with N = 256 and one
+ * mode: two 16-point stages; N = 512 with any number of modes: a 16-point and
+ * a 32-point stage; other problems run FP32).  No PTX_FORM_* flag: the handle's
  * "tc" parameter (default FP32, the CUDA-core codelets).  At most one flag.
  * The tensor-core forms run each stage as tcgen05.mma GEMMs with the operands
  * split into terms of the narrow type and FP32 accumulation in TMEM:
@@ -241,7 +242,7 @@ ptx_status ptx_accumulators(ptx_handle* h, int32_t p, void** obj_acc, size_t* ob
  * frames with N >= 64 is gathered from boxes of Psi' and P brought into shared
  * memory by 3D tensor copies through a four-stage mbarrier ring; 0: the plain
  * gather).  "tc": the number format of the DFT stages of the AP / DM column
- * pass of one-mode problems with N = 256 (0, default: FP32 on the CUDA cores;
+ * pass of problems with N = 256 and one mode or N = 512 (0, default: FP32 on the CUDA cores;
  * 1: TF32X2, 2: BF16X3, 3: BF16X2 on the tensor cores, as the PTX_FORM_*
  * cycle flags describe); a PTX_FORM_* flag of a cycle call overrides it for
  * that call.  Each pair of variants gives the same results up to rounding

@@ -882,7 +882,7 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
                     ProfScope ps(h, PTX_KERNEL_COL, ls);
                     ks->col_nf(al, nb, -1, ls);
                 }
-            } else if (form != TC_NONE && ph.p.N == 256 && ph.p.K == 1 && !ph.p.background) {
+            } else if (form != TC_NONE && ((ph.p.N == 256 && ph.p.K == 1) || ph.p.N == 512) && !ph.p.background) {
                 ProfScope ps(h, PTX_KERNEL_COL, ls);
                 launch_col_tc(al, j0, nb, form, ls);
             } else {

@@ -658,6 +658,46 @@ def test_dm256_split_precision_forms_accuracy():
     assert 2 * max(errs["fp32"]) < max(errs["bf16x2"]) < 1e-4, errs
 
 
+@pytest.mark.parametrize("K", [1, 3])
+def test_modes512_split_precision_forms(K):
+    """The 512^2 column pass with its DFT stages on the tensor cores (a 16-point
+    and a 32-point stage, the modes in two sweeps with the common factor), each
+    number format against the FP64 oracle over one DM cycle and one AP cycle:
+    TF32 hi + lo and BF16 hi + mid + lo at the single-cycle tolerance, BF16 hi +
+    lo within its own bound.  The distances are printed."""
+    from paper_2008_11511_gb300 import _lib
+    s = make_scan(f"tc512_{K}", N=512, J=6, Ho=700, Wo=640, K=K, seed=90 + K, photons=1e7, step=51.2,
+                  probe="hg", probe_radius=51.2, mode_powers=[0.7, 0.2, 0.1][:K], mask_fraction=0.02)
+    data = data_of(s)
+    o0, p0, _ = oracle.ap_cycle(s.obj0, s.probe0, data)
+    o0, p0 = o0.astype(np.complex64), p0.astype(np.complex64)
+    o, p, psi, llk_ref = oracle.cycles("DM", o0, p0, data, 1)
+    oa, pa_, la = oracle.ap_cycle(o0, p0, data)
+    errs = {}
+    for name, flag in (("fp32", 0), ("tf32x2", _lib.PTX_FORM_TF32X2), ("bf16x3", _lib.PTX_FORM_BF16X3),
+                       ("bf16x2", _lib.PTX_FORM_BF16X2)):
+        out = torch.empty(1, dtype=torch.float64, device="cuda")
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+        f = _lib.PTX_UPDATE_OBJ | _lib.PTX_UPDATE_PROBE | flag
+        _lib.call("ptx_dm_cycles", pb._handle(), 1, f | _lib.PTX_DM_INIT_PSI, ctypes.c_void_p(out.data_ptr()), stream)
+        ill = illuminated(s, p)
+        e_dm = (rel(pb.obj.cpu().numpy()[ill], o[ill]), rel(pb.probe.cpu().numpy(), p),
+                rel(pb.psi.cpu().numpy(), psi), abs(float(out.cpu()[0]) - llk_ref[0]) / abs(llk_ref[0]))
+        pb.close()
+        pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+        _lib.call("ptx_ap_cycles", pb._handle(), 1, f, ctypes.c_void_p(out.data_ptr()), stream)
+        e_ap = (rel(pb.obj.cpu().numpy()[ill], oa[ill]), rel(pb.probe.cpu().numpy(), pa_),
+                abs(float(out.cpu()[0]) - la) / abs(la))
+        pb.close()
+        errs[name] = e_dm + e_ap
+        print(f"512^2 K={K} form {name}: DM obj {e_dm[0]:.2e} probe {e_dm[1]:.2e} psi {e_dm[2]:.2e} "
+              f"llk {e_dm[3]:.2e}; AP obj {e_ap[0]:.2e} probe {e_ap[1]:.2e} llk {e_ap[2]:.2e}")
+    for name in ("fp32", "tf32x2", "bf16x3"):
+        assert max(errs[name]) < 2 * TOL1, (name, errs[name])
+    assert max(errs["bf16x2"]) < 1e-4, errs["bf16x2"]
+
+
 @pytest.mark.parametrize("tg", [0, 1])
 @pytest.mark.parametrize("case", ["corners64", "modes512"])
 def test_object_gather_variants(tg, case):
