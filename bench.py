@@ -483,7 +483,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     from paper_2008_11511_gb300 import Ptycho, _lib
     from synthetic import make_config
-    s = make_config(WORKLOAD) if not args.frames else make_config(WORKLOAD, J=args.frames)
+    s = make_config(args.workload) if not args.frames else make_config(args.workload, J=args.frames)
     obj = torch.tensor(s.obj0, device=dev)
     probe = torch.tensor(s.probe0, device=dev)
     iobs = torch.tensor(s.iobs, device=dev)
@@ -542,8 +542,8 @@ def run_ours(args):
     if args.timing_only:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms_per_step,
-                              "frames": s.J, "steps": args.steps, "repeats_ms": rep_ms, "timing_only": True}),
-                  flush=True)
+                              "workload": args.workload, "frames": s.J, "steps": args.steps, "repeats_ms": rep_ms,
+                              "timing_only": True}), flush=True)
         pb.close()
         return
 
@@ -688,6 +688,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=("dm256", "modes512"), default=WORKLOAD,
+                    help="the scan the timed cycles run on (the JSON line's metric is defined on dm256; the other "
+                         "workloads are for profiling with --timing-only)")
     ap.add_argument("--frames", type=int, default=0,
                     help="use only the first FRAMES frames of the workload (small cases for profiling)")
     ap.add_argument("--no-form-comparison", action="store_true",
@@ -716,6 +719,8 @@ def main():
     ap.add_argument("--timing-only", action="store_true",
                     help="stop after the timed region (no per-kernel pass, e2e or CPU baseline)")
     args = ap.parse_args()
+    if args.workload != WORKLOAD and not args.timing_only:
+        raise SystemExit("--workload other than dm256 needs --timing-only")
     if args.impl == "reference":
         run_reference(args)
     else:
