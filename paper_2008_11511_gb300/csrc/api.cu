@@ -109,6 +109,19 @@ ptx_status fail(ptx_status st, const char* fmt, ...) {
 namespace ptx {
 // Lets other translation units of the library report through ptx_last_error.
 void set_last_error(const char* msg) { g_last_error = msg; }
+// SMs of the current device (152 on GB300 when it cannot be asked)
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            cudaGetLastError();
+    }
+    return n > 0 ? n : 152;
+}
 }  // namespace ptx
 
 namespace {
@@ -265,19 +278,6 @@ ptx_status check_problem(const ptx_problem& p, int idx) {
 
 // Batches of frames: `lanes` batches are in flight at once (one per stream),
 // each with its own slice of the work-stack region of `spec_bytes`.
-// SMs of the current device (152 on GB300 when it cannot be asked)
-int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0, v = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
-            n = v;
-        else
-            cudaGetLastError();
-    }
-    return n > 0 ? n : 152;
-}
 
 void set_batch(ProbHost& h, size_t spec_bytes, int lanes, int cap = 0, int slots = 0) {
     const ptx_problem& p = h.p;

@@ -2,12 +2,13 @@
 // split-precision form of the DFT stages; one probe mode, N = 256 = 16 x 16).
 //
 // Each of the four DFT stages of a block's 256 column vectors (two forward,
-// two inverse) is a real GEMM on the 5th-generation tensor cores:
-//   D[256 x 32] = A[256 x 32] B^T,   A row v = vector v (16 complex, re/im
+// two inverse) is a real GEMM on the 5th-generation tensor cores, one per
+// half of the block (128 vectors of 8 columns):
+//   D[128 x 32] = A[128 x 32] B^T,   A row v = vector v (16 complex, re/im
 //   interleaved), B = the 32 x 32 real form of the 16-point DFT matrix,
-// issued by one thread, operands in shared memory (K-major, swizzled),
-// accumulator in TMEM (2 x 128 lanes x 32 columns, FP32), read back with
-// tcgen05.ld.  FP32 accuracy comes from splitting both operands into terms of
+// issued by one thread of the half, operands in shared memory (K-major,
+// swizzled), accumulator in TMEM (128 lanes x 32 columns per half, FP32), read
+// back with tcgen05.ld.  FP32 accuracy comes from splitting both operands into terms of
 // the narrow type and summing the products of the terms that matter:
 //
 //   TF32X2  (kind::tf32): x = hi + lo, hi = x truncated to TF32 (10 explicit
@@ -20,14 +21,18 @@
 //           (3 products), about 2^-16 relative per product: the two-term
 //           split, kept to measure its accuracy.
 //
-// Vector v is owned by thread v: it writes row v of A for the first stage of
-// each transform and reads row v of D (TMEM lane v % 128 of M-tile v / 128,
-// warp v / 32 reading its lane quadrant).  Between the two stages of a
-// transform the twiddle is applied in registers and the transpose is folded
-// into the A writes of the next stage (thread (c, n1) writes element n1 of the
-// vectors (c, k2)).  The projection and the LLK run in registers as in the
-// FP32 column pass.
+// Row u of a half's tile is owned by thread u of the half: it writes row u of
+// A for the first stage of each transform and reads row u of D (TMEM lane u,
+// warp u / 32 of the half reading its lane quadrant).  Between the two stages
+// of a transform the twiddle is applied in registers and the transpose is
+// folded into the A writes of the next stage (thread (c, n1) writes element n1
+// of the vectors (c, k2), all in its own half).  The two halves synchronise
+// only at the start and the end, so one half's MMAs overlap the other half's
+// SIMT work.  The projection and the LLK run in registers as in the FP32
+// column pass.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "kernels.cuh"
 
@@ -46,13 +51,13 @@ struct Fmt {
     static constexpr int kTerms = F == TC_BF16X3 ? 3 : 2;
     static constexpr int kRow = kTf32 ? 128 : 64;            // 32 elements of 4 or 2 bytes
     static constexpr int kSteps = kTf32 ? 4 : 2;             // K = 8 (tf32) or 16 (bf16) per MMA
-    static constexpr size_t kA = (size_t)256 * kRow;         // one A term
+    static constexpr size_t kA = (size_t)128 * kRow;         // one A term of one half (128 rows)
     static constexpr size_t kB = (size_t)32 * kRow;          // one B term
-    static constexpr size_t kOffA = 0;
-    static constexpr size_t kOffB = kOffA + kTerms * kA;     // [fwd, inv][term]
+    static constexpr size_t kOffA = 0;                       // [half][term]
+    static constexpr size_t kOffB = kOffA + 2 * kTerms * kA; // [fwd, inv][term]
     static constexpr size_t kOffTw = kOffB + 2 * kTerms * kB;
-    static constexpr size_t kOffBar = kOffTw + sizeof(float2) * N;
-    static constexpr size_t kOffTmem = kOffBar + 8;
+    static constexpr size_t kOffBar = kOffTw + sizeof(float2) * N;  // one mbarrier per half
+    static constexpr size_t kOffTmem = kOffBar + 16;
     static constexpr size_t kBytes = kOffTmem + 8 + 1024;    // + room to align the base to 1024
     // instruction descriptor: D f32; A, B tf32 (2) or bf16 (1), both K-major; N = 32, M = 128
     static constexpr uint32_t kIdesc = (1u << 4) | ((kTf32 ? 2u : 1u) << 7) | ((kTf32 ? 2u : 1u) << 10) |
@@ -92,14 +97,18 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
 __device__ __forceinline__ void commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
+// Bounded wait for the phase `parity` of an mbarrier: each try_wait may
+// suspend the thread until the phase completes (at most about 65 us per try),
+// so a waiting warp issues few instructions; gives up after about 2^31 clocks.
 __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
     const long long t0 = clock64();
     while (true) {
         uint32_t ok;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(ok)
-            : "r"(bar), "r"(parity)
+            : "r"(bar), "r"(parity), "r"(65536u)
             : "memory");
         if (ok) return true;
         if (clock64() - t0 > (1ll << 31)) return false;
@@ -162,26 +171,55 @@ __device__ __forceinline__ Split<F> split2(float a, float b) {
 
 }  // namespace tc
 
+// Named barriers of the two halves (128 threads each, ids 1 and 2; immediate
+// ids, so that the kernel reserves three barriers) and their OR-reductions.
+__device__ __forceinline__ void half_sync(int h) {
+    if (h == 0)
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+    else
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+}
+__device__ __forceinline__ bool half_or(int h, bool p) {
+    uint32_t r;
+    if (h == 0)
+        asm volatile(
+            "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.or.pred po, 1, 128, pi;\n\t"
+            "selp.u32 %0, 1, 0, po;\n\t}"
+            : "=r"(r)
+            : "r"((uint32_t)p)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.or.pred po, 2, 128, pi;\n\t"
+            "selp.u32 %0, 1, 0, po;\n\t}"
+            : "=r"(r)
+            : "r"((uint32_t)p)
+            : "memory");
+    return r != 0;
+}
+
 // grid (16, frames in batch), 256 threads; same arguments and outputs as k_col_r<256>.
+// The block's 16 columns form two independent halves (threads 128 h .. 128 h +
+// 127, columns 8 h .. 8 h + 7), each with its own A tile, mbarrier, TMEM columns
+// and named barrier, so that one half's MMAs run while the other half splits,
+// twiddles and stores.  Thread u = t % 128 of half h is (column c = 8 h + u % 8,
+// q = u / 8) and owns row u of its half's tile in every stage.
 template <int F>
-__global__ void __launch_bounds__(256, 2) k_col_tc(ProbArgs a, int j0) {
+__global__ void __launch_bounds__(256, 2) k_col_tc(ProbArgs a, int j0, int nb) {
     using namespace tc;
     using Fm = Fmt<F>;
     constexpr int kRow = Fm::kRow, kT = Fm::kTerms;
     extern __shared__ unsigned char smraw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    unsigned char* A = sm + Fm::kOffA;   // [term] 256 rows
     unsigned char* Bm = sm + Fm::kOffB;  // [fwd / inv][term] 32 rows
     float2* tw = (float2*)(sm + Fm::kOffTw);
-    const uint32_t bar = su32(sm + Fm::kOffBar);
     uint32_t* tmem_slot = (uint32_t*)(sm + Fm::kOffTmem);
     __shared__ double red_s[8];
     const int t = threadIdx.x, warp = t >> 5;
+    const int h = t >> 7, u = t & 127, cl = u & 7, q = u >> 3, c = 8 * h + cl;
+    unsigned char* Ah = sm + Fm::kOffA + (size_t)h * kT * Fm::kA;  // this half's A tile, [term]
+    const uint32_t barh = su32(sm + Fm::kOffBar) + 8 * h;
     const int x0 = blockIdx.x * C;
-    const int b = blockIdx.y;
-    const int j = j0 + b;
-    const int c = t % C, q = t / C;  // pass roles: (column c, n1 / k2 / kk = q)
-    float2* spec = a.spec + (size_t)b * N * N + x0;
 
     // twiddles and the two DFT matrices in their real 32 x 32 form, split into terms;
     // thread e writes the pair of entries (n, 2 kp), (n, 2 kp + 1) of matrix inv
@@ -206,7 +244,8 @@ __global__ void __launch_bounds__(256, 2) k_col_tc(ProbArgs a, int j0) {
         }
     }
     if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(sm + Fm::kOffBar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(sm + Fm::kOffBar) + 8) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -215,162 +254,179 @@ __global__ void __launch_bounds__(256, 2) k_col_tc(ProbArgs a, int j0) {
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    // the matrices are read by either half's MMAs: every writer's stores are made
+    // visible to the tensor cores before the block barrier
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    // this thread's D row: M-tile t / 128 at column 32 (t / 128), lane t % 128
-    const uint32_t my_d = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (t >> 7));
+    // this thread's D row: lane u (warp quadrant warp % 4), columns 32 h .. 32 h + 31
+    const uint32_t my_d = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * h);
     uint32_t parity = 0;
+    // base descriptors of this half's A tile and of the matrices; a stage's
+    // operands are these plus constant offsets in their 16-byte address field
+    // (shared-memory addresses stay below 2^18, so the field does not overflow)
+    const uint64_t da = desc_sw<Fm::kTf32>(su32(Ah)), db = desc_sw<Fm::kTf32>(su32(Bm));
 
-    // one tensor-core DFT stage over the A tile: D = A B^T, B = matrix `m` (0 fwd, 1 inv).
-    // Every thread waits (bounded) for the stage's commit; the outcome is made
-    // block-uniform, so a give-up seen by any thread stops the whole block: no
-    // later stage issues MMAs, and the caller reports it and frees TMEM.
+    // one tensor-core DFT stage over this half's A tile: D = A B^T, B = matrix
+    // `m` (0 fwd, 1 inv), one thread of the half issuing.  The half's first
+    // warp waits (bounded) for the commit; the outcome is made half-uniform, so
+    // a give-up stops the half: it issues no later stage, and the end of the
+    // kernel reports it and drains the MMAs in flight.
     auto stage = [&](int m, float* out) -> bool {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        half_sync(h);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (t == 0) {
-            const uint32_t b0 = su32(Bm + (size_t)(m * kT) * Fm::kB);
+        if (u == 0) {
+            const uint32_t d = tmem + 32 * h;
             // products (term of A, term of B), smallest first: three terms keep
             // every product down to 2^-16, two terms the three largest
             constexpr int kProd = F == TC_BF16X3 ? 6 : 3;
             constexpr int pa6[6] = {2, 1, 0, 1, 0, 0}, pb6[6] = {0, 1, 2, 0, 1, 0};
             constexpr int pa3[3] = {1, 0, 0}, pb3[3] = {0, 1, 0};
 #pragma unroll
-            for (int tile = 0; tile < 2; ++tile) {
-                const uint32_t a0 = su32(A) + tile * 128 * kRow;
-                const uint32_t d = tmem + 32 * tile;
+            for (int p = 0; p < kProd; ++p) {
+                const int ta = kProd == 6 ? pa6[p] : pa3[p], tb = kProd == 6 ? pb6[p] : pb3[p];
 #pragma unroll
-                for (int p = 0; p < kProd; ++p) {
-                    const int ta = kProd == 6 ? pa6[p] : pa3[p], tb = kProd == 6 ? pb6[p] : pb3[p];
-#pragma unroll
-                    for (int k = 0; k < Fm::kSteps; ++k)
-                        mma<Fm::kTf32>(d, desc_sw<Fm::kTf32>(a0 + ta * (uint32_t)Fm::kA + 32 * k),
-                                       desc_sw<Fm::kTf32>(b0 + tb * (uint32_t)Fm::kB + 32 * k), Fm::kIdesc,
-                                       (p > 0 || k > 0) ? 1u : 0u);
-                }
+                for (int k = 0; k < Fm::kSteps; ++k)
+                    mma<Fm::kTf32>(d, da + ((ta * Fm::kA + 32 * k) >> 4),
+                                   db + (((m * kT + tb) * Fm::kB + 32 * k) >> 4), Fm::kIdesc,
+                                   (p > 0 || k > 0) ? 1u : 0u);
             }
-            commit(bar);
+            commit(barh);
         }
-        const bool mine = bar_wait(bar, parity);
-        if (__syncthreads_or(!mine)) return false;  // parity stays at the pending phase
+        // the half's first warp polls the mbarrier; the other warps wait in the
+        // named barrier, which also makes the outcome half-uniform
+        const bool mine = (u >> 5) == 0 ? bar_wait(barh, parity) : true;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (half_or(h, !mine)) return false;  // parity stays at the pending phase
         parity ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         tmem_ld32(my_d, out);
         return true;
     };
-    // write this thread's 16 complex values as its own A row (all terms)
+    // this thread's 16 complex values as its own A row u (all terms): 16-byte
+    // stores of two (TF32) or four (BF16) consecutive values
     auto put_row = [&](const float2* v) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const Split<F> sp = split2<F>(v[i].x, v[i].y);
+        for (int i = 0; i < 16; i += (Fm::kTf32 ? 2 : 4)) {
             if constexpr (Fm::kTf32) {
-                const uint32_t off = sw_off<kRow>(t, 8 * i);
-                *(float2*)(A + off) = make_float2(__uint_as_float(sp.w[0]), __uint_as_float(sp.w[1]));
-                *(float2*)(A + Fm::kA + off) = make_float2(__uint_as_float(sp.w[2]), __uint_as_float(sp.w[3]));
+                const Split<F> s0 = split2<F>(v[i].x, v[i].y), s1 = split2<F>(v[i + 1].x, v[i + 1].y);
+                const uint32_t off = (uint32_t)(u * kRow + (((i >> 1) ^ (u & 7)) << 4));
+                *(uint4*)(Ah + off) = make_uint4(s0.w[0], s0.w[1], s1.w[0], s1.w[1]);
+                *(uint4*)(Ah + Fm::kA + off) = make_uint4(s0.w[2], s0.w[3], s1.w[2], s1.w[3]);
             } else {
-                const uint32_t off = sw_off<kRow>(t, 4 * i);
+                Split<F> sp[4];
 #pragma unroll
-                for (int s = 0; s < kT; ++s) *(uint32_t*)(A + s * Fm::kA + off) = sp.w[s];
+                for (int r = 0; r < 4; ++r) sp[r] = split2<F>(v[i + r].x, v[i + r].y);
+                const uint32_t off = (uint32_t)(u * kRow + (((i >> 2) ^ ((u >> 1) & 3)) << 4));
+#pragma unroll
+                for (int s = 0; s < kT; ++s)
+                    *(uint4*)(Ah + s * Fm::kA + off) = make_uint4(sp[0].w[s], sp[1].w[s], sp[2].w[s], sp[3].w[s]);
             }
         }
     };
-    // element `e` of the vectors (c, k) for k = 0..15 (rows k * 16 + c): the folded transpose
-    auto put_col = [&](const float2* v, int e) {
+    // element q of the vectors (c, k) for k = 0..15 (rows 8 k + cl): the folded
+    // transpose; the in-row offset is the same for every k
+    auto put_col = [&](const float2* v) {
+        const uint32_t in_row = Fm::kTf32 ? (uint32_t)(cl * kRow + ((((q >> 1) ^ cl)) << 4) + 8 * (q & 1))
+                                          : (uint32_t)(cl * kRow + ((((q >> 2) ^ ((cl >> 1) & 3))) << 4) + 4 * (q & 3));
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            const int r = k * 16 + c;
             const Split<F> sp = split2<F>(v[k].x, v[k].y);
+            const uint32_t off = (uint32_t)(8 * k * kRow) + in_row;
             if constexpr (Fm::kTf32) {
-                const uint32_t off = sw_off<kRow>(r, 8 * e);
-                *(float2*)(A + off) = make_float2(__uint_as_float(sp.w[0]), __uint_as_float(sp.w[1]));
-                *(float2*)(A + Fm::kA + off) = make_float2(__uint_as_float(sp.w[2]), __uint_as_float(sp.w[3]));
+                *(uint2*)(Ah + off) = make_uint2(sp.w[0], sp.w[1]);
+                *(uint2*)(Ah + Fm::kA + off) = make_uint2(sp.w[2], sp.w[3]);
             } else {
-                const uint32_t off = sw_off<kRow>(r, 4 * e);
 #pragma unroll
-                for (int s = 0; s < kT; ++s) *(uint32_t*)(A + s * Fm::kA + off) = sp.w[s];
+                for (int s = 0; s < kT; ++s) *(uint32_t*)(Ah + s * Fm::kA + off) = sp.w[s];
             }
         }
     };
 
     float2 v[16];
     float o[32];
-    // forward stage 1: vector (c, n1 = q) = x[q + 16 n2], n2 = 0..15
-#pragma unroll
-    for (int n2 = 0; n2 < 16; ++n2) v[n2] = ld_hint(spec + (size_t)(q + 16 * n2) * N + c, policy_evict_last());
-    // intensities and mask bits of the pass-2 pixels (rows q + 16 k1 of column c)
-    float io[16];
-    {
-        const float* ib = a.iobs + (size_t)j * N * N + (size_t)q * N + x0 + c;
-#pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) io[k1] = __ldcs(ib + (size_t)16 * k1 * N);
-    }
-    const uint32_t mbits = a.mbits[blockIdx.x * 256 + t];
+    bool good = true, bad = false;
+    // mask bits of the thread's stage-2 pixels (the same for every frame); the
+    // table is laid out for the FP32 column pass's threads (k2 * 16 + c)
+    const uint32_t mbits = a.mbits[blockIdx.x * 256 + q * 16 + c];
     constexpr float invN2 = 1.0f / float(N * N);
-    KahanF llk;
-    put_row(v);
-    // `good` is block-uniform (each stage combines the threads' wait outcomes)
-    bool good = stage(0, o);
-    if (good) {
-        // twiddle w^(n1 k2) and the transpose into the vectors (c, k2)
+    for (int b = blockIdx.y; b < nb; b += gridDim.y) {
+        const int j = j0 + b;
+        float2* spec = a.spec + (size_t)b * N * N + x0;
+        // forward stage 1: vector (c, n1 = q) = x[q + 16 n2], n2 = 0..15
 #pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) {
-            const float2 y = make_float2(o[2 * k2], o[2 * k2 + 1]);
-            v[k2] = k2 == 0 ? y : cmul(y, tw_get<N, -1>(tw, k2, q));
-        }
-        // the A tile may be rewritten at once: the stage's MMAs have completed (mbarrier);
-        // the next stage's barrier orders every thread's D read before its MMAs
-        put_col(v, q);
-        good = stage(0, o);
-    }
-    if (good) {
-        // projection and LLK on X^[q + 16 k1] (thread = vector (c, k2 = q))
+        for (int n2 = 0; n2 < 16; ++n2) v[n2] = ld_hint(spec + (size_t)(q + 16 * n2) * N + c, policy_evict_last());
+        // intensities of the stage-2 pixels (rows q + 16 k1 of column c)
+        float io[16];
+        {
+            const float* ib = a.iobs + (size_t)j * N * N + (size_t)q * N + x0 + c;
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1) {
-            const float2 X = make_float2(o[2 * k1], o[2 * k1 + 1]);
-            const float ic = cnorm(X) * invN2;
-            const bool masked = (mbits >> k1) & 1u;
-            float ratio;
-            const float term = llk_term_ratio(ic, io[k1], ratio);
-            if (!masked) llk.add(term);
-            const float f = masked ? 0.f : (ratio - 1.0f) * invN2;
-            v[k1] = cscale(X, f);
+            for (int k1 = 0; k1 < 16; ++k1) io[k1] = __ldcs(ib + (size_t)16 * k1 * N);
         }
-        // inverse stage 1 over k1 on the thread's own vector, then twiddle w^(+k2 kk)
+        float llk = 0.f;  // the terms are >= 0: a plain float sum of a thread's pixels
         put_row(v);
-        good = stage(1, o);
-    }
-    if (good) {
+        // `good` is uniform over the half (each stage combines its threads' wait outcomes)
+        good = stage(0, o);
+        if (good) {
+            // twiddle w^(n1 k2) and the transpose into the vectors (c, k2)
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            const float2 y = make_float2(o[2 * kk], o[2 * kk + 1]);
-            v[kk] = kk == 0 ? y : cmul(y, tw_get<N, +1>(tw, q, kk));
-        }
-        put_col(v, q);
-        good = stage(1, o);
-    }
-    if (good) {
-        // rows kk + 16 k1' of column c (thread = vector (c, kk = q))
-        const uint64_t el = policy_evict_last();
-#pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1)
-            st_hint(spec + (size_t)(q + 16 * k1) * N + c, make_float2(o[2 * k1], o[2 * k1 + 1]), el);
-    }
-    const double tot = block_sum_double<256>(llk.value(), red_s);
-    if (t == 0) {
-        a.llk_part[(size_t)j * gridDim.x + blockIdx.x] = tot;
-        if (!good) {
-            // a stage's commit did not arrive in time: wait once more (bounded) for
-            // the MMAs in flight before TMEM is freed, and report the give-up
-            bar_wait(bar, parity);
-            if (a.err_flag) {
-                *(volatile int*)a.err_flag = 1;
-                __threadfence_system();
+            for (int k2 = 0; k2 < 16; ++k2) {
+                const float2 y = make_float2(o[2 * k2], o[2 * k2 + 1]);
+                v[k2] = k2 == 0 ? y : cmul(y, tw_get<N, -1>(tw, k2, q));
             }
+            // the A tile may be rewritten at once: the stage's MMAs have completed (mbarrier);
+            // the next stage's barrier orders every thread's D read before its MMAs
+            put_col(v);
+            good = stage(0, o);
         }
+        if (good) {
+            // projection and LLK on X^[q + 16 k1] (thread = vector (c, k2 = q))
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) {
+                const float2 X = make_float2(o[2 * k1], o[2 * k1 + 1]);
+                const float ic = cnorm(X) * invN2;
+                const bool masked = (mbits >> k1) & 1u;
+                float ratio;
+                const float term = llk_term_ratio(ic, io[k1], ratio);
+                if (!masked) llk += term;
+                const float f = masked ? 0.f : (ratio - 1.0f) * invN2;
+                v[k1] = cscale(X, f);
+            }
+            // inverse stage 1 over k1 on the thread's own vector, then twiddle w^(+k2 kk)
+            put_row(v);
+            good = stage(1, o);
+        }
+        if (good) {
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) {
+                const float2 y = make_float2(o[2 * kk], o[2 * kk + 1]);
+                v[kk] = kk == 0 ? y : cmul(y, tw_get<N, +1>(tw, q, kk));
+            }
+            put_col(v);
+            good = stage(1, o);
+        }
+        if (good) {
+            // rows kk + 16 k1' of column c (thread = vector (c, kk = q))
+            const uint64_t el = policy_evict_last();
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1)
+                st_hint(spec + (size_t)(q + 16 * k1) * N + c, make_float2(o[2 * k1], o[2 * k1 + 1]), el);
+        }
+        const double tot = block_sum_pos<256>(llk, red_s);
+        if (t == 0) a.llk_part[(size_t)j * gridDim.x + blockIdx.x] = tot;
+        bad = __syncthreads_or(!good);  // also orders thread 0's reads of red_s before the next frame
+        if (bad) break;
+    }
+    // a stage's commit did not arrive in time: wait once more (bounded) for the
+    // half's MMAs in flight before TMEM is freed, and report the give-up
+    if (!good && u == 0) bar_wait(barh, parity);
+    if (bad && t == 0 && a.err_flag) {
+        *(volatile int*)a.err_flag = 1;
+        __threadfence_system();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -495,8 +551,8 @@ __global__ void __launch_bounds__(512, 1) k_col_tc512(ProbArgs a, int j0) {
     uint32_t parity = 0;
 
     // one stage: `big` = stage B (two tiles, N = 64, K in two planes), else stage A
-    // (four tiles, N = 32); dir 0 forward, 1 inverse.  The wait outcome is
-    // block-uniform; a give-up stops the block's MMAs.
+    // (four tiles, N = 32); dir 0 forward, 1 inverse.  Warp 0 waits for the
+    // commit; the outcome is made block-uniform; a give-up stops the block's MMAs.
     auto stage = [&](bool big, int dir, float* out) -> bool {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -529,7 +585,9 @@ __global__ void __launch_bounds__(512, 1) k_col_tc512(ProbArgs a, int j0) {
             }
             commit(bar);
         }
-        const bool mine = bar_wait(bar, parity);
+        // warp 0 polls the mbarrier; the other warps wait in the block barrier
+        const bool mine = warp == 0 ? bar_wait(bar, parity) : true;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         if (__syncthreads_or(!mine)) return false;
         parity ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -652,13 +710,17 @@ void launch_col_tc(const ProbArgs& a, int j0, int nb, int form, cudaStream_t s) 
             k_col_tc512<TC_TF32X2><<<grid, 512, tc::Fmt512<TC_TF32X2>::kBytes, s>>>(a, j0);
         return;
     }
-    dim3 grid(tc::N / tc::C, nb);
+    // two blocks per SM; each block runs its 16 columns of about nb / G frames
+    // (the matrices, twiddles and TMEM set up once per block)
+    const int slots = std::max(1, 2 * sm_count() / (tc::N / tc::C));
+    const int per = (nb + slots - 1) / slots;
+    dim3 grid(tc::N / tc::C, (nb + per - 1) / per);
     if (form == TC_BF16X3)
-        k_col_tc<TC_BF16X3><<<grid, 256, tc::Fmt<TC_BF16X3>::kBytes, s>>>(a, j0);
+        k_col_tc<TC_BF16X3><<<grid, 256, tc::Fmt<TC_BF16X3>::kBytes, s>>>(a, j0, nb);
     else if (form == TC_BF16X2)
-        k_col_tc<TC_BF16X2><<<grid, 256, tc::Fmt<TC_BF16X2>::kBytes, s>>>(a, j0);
+        k_col_tc<TC_BF16X2><<<grid, 256, tc::Fmt<TC_BF16X2>::kBytes, s>>>(a, j0, nb);
     else
-        k_col_tc<TC_TF32X2><<<grid, 256, tc::Fmt<TC_TF32X2>::kBytes, s>>>(a, j0);
+        k_col_tc<TC_TF32X2><<<grid, 256, tc::Fmt<TC_TF32X2>::kBytes, s>>>(a, j0, nb);
 }
 template <int F>
 static cudaError_t set_attrs_tc_f() {

@@ -626,6 +626,8 @@ void launch_cycle_persistent(const PersArgs& pa, int grid, cudaStream_t s);
 enum TcForm : int { TC_NONE = 0, TC_TF32X2 = 1, TC_BF16X3 = 2, TC_BF16X2 = 3 };
 void launch_col_tc(const ProbArgs& a, int j0, int nb, int form, cudaStream_t s);
 cudaError_t set_attrs_tc();
+// SMs of the current device (api.cu)
+int sm_count();
 // The same gather fed by 3D tensor copies (32 x 32 tiles, N >= 64).
 void launch_obj_gather_tma(const void* tm_psi, const void* tm_probe, const ProbArgs& a, const TileLists& tl,
                            int ntiles, int fuse_max, cudaStream_t s);
