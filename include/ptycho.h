@@ -235,7 +235,10 @@ ptx_status ptx_accumulators(ptx_handle* h, int32_t p, void** obj_acc, size_t* ob
  * keep the per-batch launches); "persistent_selftest" (1: the persistent
  * schedule's first column items wait for a forward item that never comes, so
  * their bounded wait gives up: the next cycle call returns PTX_ERR_TIMEOUT
- * once; for the tests of that failure path); "tma" (0, default: the register column pass;
+ * once; for the tests of that failure path); "tc_selftest" (1: in the 256^2
+ * tensor-core column pass one stage of the first frame issues no MMAs, so its
+ * bounded wait (about 2^31 SM clocks) gives up and the next cycle call returns
+ * PTX_ERR_TIMEOUT once; for the tests of that failure path); "tma" (0, default: the register column pass;
  * 1: the AP / DM column pass of one-mode problems with N = 256 takes its inputs
  * by 2D tensor copies (cp.async.bulk.tensor) in a persistent grid of two CTAs
  * per SM).  "tma_gather" (1, default: the object numerator / denominator of

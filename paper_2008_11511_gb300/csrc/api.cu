@@ -459,6 +459,7 @@ struct ptx_handle {
     size_t pers_off = 0;
     bool pers_dirty = true;  // tables to rebuild and upload before the next cycle
     int pers_selftest = 0;   // ptx_set_param "persistent_selftest": a dependency that is never met
+    int tc_selftest = 0;     // ptx_set_param "tc_selftest": a tensor-core stage whose commit never comes
     int pers_nitems = 0, pers_nseg = 0, pers_nbatch = 0;
     std::vector<ProbArgs> pers_prob;
     std::vector<PSeg> pers_seg;
@@ -893,7 +894,7 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
                 }
             } else if (form != TC_NONE && ((ph.p.N == 256 && ph.p.K == 1) || ph.p.N == 512) && !ph.p.background) {
                 ProfScope ps(h, PTX_KERNEL_COL, ls);
-                launch_col_tc(al, j0, nb, form, ls);
+                launch_col_tc(al, j0, nb, form, h->tc_selftest, ls);
             } else {
                 ProfScope ps(h, PTX_KERNEL_COL, ls);
                 CUtensorMap tm_spec;
@@ -1447,6 +1448,9 @@ ptx_status ptx_set_param(ptx_handle* h, const char* name, double value) {
     } else if (!strcmp(name, "persistent_selftest")) {
         if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "persistent_selftest must be 0 or 1");
         h->pers_selftest = (int)value;
+    } else if (!strcmp(name, "tc_selftest")) {
+        if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "tc_selftest must be 0 or 1");
+        h->tc_selftest = (int)value;
     } else if (!strcmp(name, "batch_frames")) {
         if (value != (int)value || value > 32768)
             return fail(PTX_ERR_INVALID_ARG, "batch_frames must be an integer in 0..32768");

@@ -624,7 +624,9 @@ void launch_cycle_persistent(const PersArgs& pa, int grid, cudaStream_t s);
 // Number formats of the tensor-core column pass (ptx_set_param "tc" and the
 // PTX_FORM_* cycle flags): TF32 hi + lo, BF16 hi + mid + lo, BF16 hi + lo.
 enum TcForm : int { TC_NONE = 0, TC_TF32X2 = 1, TC_BF16X3 = 2, TC_BF16X2 = 3 };
-void launch_col_tc(const ProbArgs& a, int j0, int nb, int form, cudaStream_t s);
+// selftest != 0 (256^2 forms): one stage of the first frame issues no MMAs, so
+// its bounded wait runs out and the launch reports through err_flag.
+void launch_col_tc(const ProbArgs& a, int j0, int nb, int form, int selftest, cudaStream_t s);
 cudaError_t set_attrs_tc();
 // SMs of the current device (api.cu)
 int sm_count();

@@ -1,11 +1,13 @@
 """Failure detection without a GPU fault.
 
 The library's device-side waits (tensor-copy arrivals in the object gather and
-the column pass) are bounded: a wait that runs out records the fact in the
-handle's error flag (mapped host memory) and the kernel returns, so the
-context stays usable, and the next cycle call reports PTX_ERR_TIMEOUT once.
-Here the wait that runs out is ptx_wait_selftest's, on a flag that nothing
-sets; no GPU fault, trap or hang is involved.
+the column pass, MMA commits in the tensor-core column pass) are bounded: a
+wait that runs out records the fact in the handle's error flag (mapped host
+memory) and the kernel returns, so the context stays usable, and the next
+cycle call reports PTX_ERR_TIMEOUT once.  Here the waits that run out are
+ptx_wait_selftest's, on a flag that nothing sets, and a tensor-core stage's,
+on an mbarrier whose commit is never issued (with no MMA in flight); no GPU
+fault, trap or hang is involved.
 """
 import ctypes
 
@@ -96,3 +98,34 @@ def test_counts_to_float_rejects_misaligned_pointers():
         _lib.call("ptx_counts_to_float", ctypes.c_void_p(buf.data_ptr() + 4), ctypes.c_void_p(src.data_ptr()),
                   ctypes.c_size_t(8), None)
     assert ei.value.status_name == "PTX_ERR_INVALID_ARG"
+
+
+def test_tensor_core_stage_wait_gives_up_and_reports():
+    """A tensor-core stage whose MMAs and commit are never issued (the
+    "tc_selftest" switch) makes its half's bounded mbarrier wait run out while
+    every other half of the launch completes normally: the next call reports
+    PTX_ERR_TIMEOUT once, and the handle then runs cycles that match the oracle."""
+    from paper_2008_11511_gb300 import Ptycho, PtychoError
+    s = make_config("dm256", J=24, Ho=512, Wo=512)
+    data = oracle.Data.make(s.iobs, s.positions, s.mask)
+    o0, p0, _ = oracle.ap_cycle(s.obj0, s.probe0, data)
+    o0, p0 = o0.astype(np.complex64), p0.astype(np.complex64)
+    pb = Ptycho(torch.tensor(o0, device="cuda"), torch.tensor(p0, device="cuda"),
+                torch.tensor(s.iobs, device="cuda"), s.positions, s.mask)
+    pb.set_param("tc", 1)
+    pb.set_param("tc_selftest", 1)
+    pb.ap(1)
+    torch.cuda.synchronize()
+    with pytest.raises(PtychoError, match="TIMEOUT"):
+        pb.ap(1)
+    pb.set_param("tc_selftest", 0)
+    pb.obj.copy_(torch.tensor(o0, device="cuda"))
+    pb.probe.copy_(torch.tensor(p0, device="cuda"))
+    pb.ap(1)
+    o, p, _ = oracle.ap_cycle(o0, p0, data)
+    d = oracle.object_denominator(p, s.positions, (s.Ho, s.Wo))
+    ill = d > 1e-3 * d.max()
+    obj = pb.obj.cpu().numpy()
+    assert np.linalg.norm(obj[ill] - o[ill]) / np.linalg.norm(o[ill]) < 2e-5
+    assert np.linalg.norm(pb.probe.cpu().numpy() - p) / np.linalg.norm(p) < 2e-5
+    pb.close()
