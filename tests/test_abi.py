@@ -86,6 +86,32 @@ def test_workspace_bytes_and_argument_checks(lib):
     assert STATUS_NAMES[_ws(lib, p8)[0]] == "PTX_ERR_INVALID_ARG"
 
 
+def test_work_stack_sizing(lib):
+    """The Fourier work stack: 64 MB for frames of less than 4 MB of spectra
+    (two lanes of 64 frames at 256^2), at least 21 frames per lane for larger
+    ones (three-mode 512^2 frames of 6 MB: 252 MB); a scan of fewer frames
+    takes only what its frames need."""
+    mb = 1 << 20
+    f512k3 = 3 * 512 * 512 * 8
+
+    def ws(N, K, Ho, Wo, positions):
+        p, pos = _problem(N=N, K=K, Ho=Ho, Wo=Wo, positions=positions)  # pos must outlive the call
+        st, n = _ws(lib, p)
+        assert st == 0
+        return n
+
+    pos256 = [[(7 * i) % 200, (13 * i) % 200] for i in range(200)]
+    n256 = ws(256, 1, 456, 456, pos256)
+    assert 64 * mb < n256 < 96 * mb
+    pos512 = [[(7 * i) % 80, (13 * i) % 80] for i in range(60)]
+    n512k3 = ws(512, 3, 592, 592, pos512)
+    assert 2 * 21 * f512k3 < n512k3 < 2 * 21 * f512k3 + 64 * mb
+    n512k3s = ws(512, 3, 592, 592, pos512[:4])  # four frames: a stack of four frames per lane
+    assert 2 * 4 * f512k3 < n512k3s < 2 * 4 * f512k3 + 64 * mb
+    n512k1 = ws(512, 1, 592, 592, pos512)  # 2 MB frames keep the 64 MB stack
+    assert 64 * mb < n512k1 < 96 * mb
+
+
 def test_null_handle_calls_fail_cleanly(lib):
     from paper_2008_11511_gb300._lib import STATUS_NAMES
     assert STATUS_NAMES[lib.ptx_ap_cycles(None, 1, 3, None, None)] == "PTX_ERR_INVALID_ARG"
