@@ -264,12 +264,13 @@ def run_e2e(args, s, pb, obj, probe, iobs, params, llk_buf, stream, dev, ws):
     stack from pinned memory, the DM cycle, the LLK read back; the upload of
     step k + 1 runs on copy streams while step k computes.
 
-    Photon counts (the synthetic intensities are Poisson counts) go up as
-    uint16 and are widened into the problem's float32 array on the device by
-    ``counts_to_float`` before the cycle (half the bytes of a float32 upload);
-    otherwise float32 frames go up into the other of two device buffers, each
-    with its own handle sharing the object, the probe and the exit waves.
-    Returns (frames/s, bytes uploaded per step, description)."""
+    The intensities go into the other of two device buffers, each with its own
+    handle sharing the object, the probe and the exit waves.  Photon counts
+    (the synthetic intensities are Poisson counts) go up as uint16 and are
+    widened into that float32 buffer by ``counts_to_float`` on the copy stream
+    (half the bytes of a float32 upload, and the widening overlaps the previous
+    cycle); otherwise float32 frames go up directly.
+    Returns (frames/s, bytes uploaded per step, description, runs)."""
     import torch
     from paper_2008_11511_gb300 import Ptycho, counts_to_float
     counts = exact_counts(s.iobs) if args.e2e_dtype in ("auto", "u16") else None
@@ -281,29 +282,35 @@ def run_e2e(args, s, pb, obj, probe, iobs, params, llk_buf, stream, dev, ws):
     copy_streams = [torch.cuda.Stream(dev) for _ in range(n_copy)]
     copied = [[torch.cuda.Event() for _ in range(n_copy)] for _ in range(2)]
     used = [torch.cuda.Event(), torch.cuda.Event()]
-    extra = None
+    iobs2 = torch.empty_like(iobs)
+    extra = Ptycho(obj, probe, iobs2, s.positions, s.mask, psi=pb.psi)
+    for name, val in params:
+        extra.set_param(name, val)
+    iobs2.copy_(iobs)
+    extra.dm(1, llk=llk_buf)  # graph capture outside the timed region
+    bufs, handles = [iobs, iobs2], (pb, extra)
     if counts is not None:
         host = torch.from_numpy(counts).pin_memory()
         stage = [torch.empty(counts.shape, dtype=torch.uint16, device=dev) for _ in range(2)]
-        handles, desc = (pb, pb), "uint16 photon counts (exact) from pinned host memory, widened to float32 on the device"
+        desc = ("uint16 photon counts (exact) from pinned host memory, widened to float32 on the device on the copy "
+                "stream, into two device buffers")
     else:
         host = torch.from_numpy(s.iobs).pin_memory()
-        iobs2 = torch.empty_like(iobs)
-        extra = Ptycho(obj, probe, iobs2, s.positions, s.mask, psi=pb.psi)
-        for name, val in params:
-            extra.set_param(name, val)
-        iobs2.copy_(iobs)
-        extra.dm(1, llk=llk_buf)  # graph capture outside the timed region
-        stage = [iobs, iobs2]
-        handles, desc = (pb, extra), "float32 frames from pinned host memory into two device buffers"
+        stage = None
+        desc = "float32 frames from pinned host memory into two device buffers"
     desc += f", on {n_copy} copy stream(s) one step ahead"
 
     def upload(nb, wait_used):
         for c, cs in enumerate(copy_streams):
+            lo, hi = bounds[c], bounds[c + 1]
             with torch.cuda.stream(cs):
                 if wait_used:
                     cs.wait_event(used[nb])
-                stage[nb][bounds[c]:bounds[c + 1]].copy_(host[bounds[c]:bounds[c + 1]], non_blocking=True)
+                if counts is not None:
+                    stage[nb][lo:hi].copy_(host[lo:hi], non_blocking=True)
+                    counts_to_float(bufs[nb][lo:hi], stage[nb][lo:hi])
+                else:
+                    bufs[nb][lo:hi].copy_(host[lo:hi], non_blocking=True)
                 copied[nb][c].record(cs)
 
     # the host-to-device path is shared with the rest of the machine: the leg
@@ -321,13 +328,8 @@ def run_e2e(args, s, pb, obj, probe, iobs, params, llk_buf, stream, dev, ws):
                 upload(1 - b, k >= 1)
             for ev in copied[b]:
                 stream.wait_event(ev)
-            if counts is not None:
-                counts_to_float(iobs, stage[b])
-                used[b].record(stream)
-                l = pb.dm(1, llk=llk_buf)
-            else:
-                l = handles[b].dm(1, llk=llk_buf)
-                used[b].record(stream)
+            l = handles[b].dm(1, llk=llk_buf)
+            used[b].record(stream)
             host_llk.copy_(l[:1], non_blocking=True)
         stream.synchronize()
         for cs in copy_streams:
@@ -336,11 +338,8 @@ def run_e2e(args, s, pb, obj, probe, iobs, params, llk_buf, stream, dev, ws):
         barrier(ws)
         el = max_over_ranks(el, ws)
         runs.append(s.J * e_steps * ws / el)
-    if extra is not None:
-        extra.close()
-    if counts is not None:  # the device array holds the same values again
-        counts_to_float(iobs, stage[0])
-        torch.cuda.synchronize(dev)
+    torch.cuda.synchronize(dev)
+    extra.close()  # both buffers hold the same values (the one host array, uploaded every step)
     desc += f"; median of {len(runs)} timed runs of {e_steps} steps"
     return statistics.median(runs), host.numel() * host.element_size(), desc, runs
 
