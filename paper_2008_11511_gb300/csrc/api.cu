@@ -736,8 +736,9 @@ void pers_build(ptx_handle* h) {
             bt.j0 = j0;
             bt.nb = nb;
             bt.G = G;
-            bt.n[0] = (unsigned)((p.N / L) * nb);
-            bt.n[1] = (unsigned)((p.N / C) * nb);
+            const int fgroups = (nb + kPersFrames - 1) / kPersFrames;  // frames per row / column item
+            bt.n[0] = (unsigned)((p.N / L) * fgroups);
+            bt.n[1] = (unsigned)((p.N / C) * fgroups);
             bt.n[2] = (unsigned)((p.N / L) * G);
             h->pers_batch.push_back(bt);
         }

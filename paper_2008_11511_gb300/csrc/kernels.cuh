@@ -584,6 +584,7 @@ __global__ void k_obj_gather(ProbArgs a, TileLists tl, int fuse_max);
 // is the run of work items of one pass of one batch; items are numbered in
 // list order and a segment's start is the number of its first item.
 constexpr int kPersSlots = 3;  // work-stack slots (batches in flight)
+constexpr int kPersFrames = 4;  // frames per forward-row and column item
 struct PSeg {
     int g;       // batch
     int pass;    // 0 forward row pass, 1 column pass, 2 backward row pass

@@ -7,17 +7,19 @@
 // Work list.  The batches of all problems are numbered g = 0 .. nbatch - 1;
 // batch g uses work-stack slot g mod kSlots.  The items are handed out in
 // pipeline order, step s = 0 .. nbatch + 1: the row items of batch s, the
-// column items of batch s - 1, the backward items of batch s - 2.  A block
-// takes the next item index from a global counter, finds its segment (batch,
-// pass) by binary search over the segment starts, and waits until the items
-// it depends on are done:
+// column items of batch s - 1, the backward items of batch s - 2.  A forward
+// row or column item covers kPersFrames frames of one band or column block.
+// A block takes item indices from a global counter (the next one while the
+// current item runs), finds the segment (batch, pass) by scanning forward from
+// its last one, and waits until the items it depends on are done:
 //   column items of g   after every forward row item of g,
 //   backward items of g after every column item of g,
 //   forward items of g  after every backward item of g - kSlots (the slot's
 //                       previous batch has been read out).
 // Each dependency is on items earlier in the list, which running blocks have
-// taken and will finish (a block waits only on items taken before its own),
-// so the schedule cannot deadlock.  Every wait is bounded (about 2^31 SM
+// taken and will finish: the lowest unfinished item's dependencies are all
+// done, and its block is working on it (a block's other index, the one taken
+// ahead, is higher), so the schedule cannot deadlock.  Every wait is bounded (about 2^31 SM
 // clocks); a wait that runs out sets the abort flag, which every block checks
 // before taking an item, and the handle's error flag, and the launch drains.
 //
@@ -71,17 +73,30 @@ __device__ __noinline__ void row_bwd(const ProbArgs& a, int j0, int nb, int pbx,
 #undef PTX_GY
 }
 
+// A forward-row or column item covers kPersFrames consecutive frames of one
+// row band or column block (the bodies run one after the other; the block
+// synchronises between them, as the next body rewrites the shared twiddles).
 template <int N>
 __device__ __forceinline__ void run_item(const ProbArgs& a, const PBatch& bt, int pass, int k, bool dm_fwd) {
     if (pass == 0) {
         constexpr int nbx = N / RegShape<N>::L;
-        if (dm_fwd)
-            row_fwd<N, true>(a, bt.j0, k % nbx, k / nbx);
-        else
-            row_fwd<N, false>(a, bt.j0, k % nbx, k / nbx);
+        const int bx = k % nbx, f0 = (k / nbx) * kPersFrames;
+        const int f1 = f0 + kPersFrames < bt.nb ? f0 + kPersFrames : bt.nb;
+        for (int f = f0; f < f1; ++f) {
+            if (f > f0) __syncthreads();
+            if (dm_fwd)
+                row_fwd<N, true>(a, bt.j0, bx, f);
+            else
+                row_fwd<N, false>(a, bt.j0, bx, f);
+        }
     } else if (pass == 1) {
         constexpr int nbx = N / RegShape<N>::C;
-        col<N>(a, bt.j0, k % nbx, k / nbx);
+        const int bx = k % nbx, f0 = (k / nbx) * kPersFrames;
+        const int f1 = f0 + kPersFrames < bt.nb ? f0 + kPersFrames : bt.nb;
+        for (int f = f0; f < f1; ++f) {
+            if (f > f0) __syncthreads();
+            col<N>(a, bt.j0, bx, f);
+        }
     } else {
         constexpr int nbx = N / BwdShape<N>::L;
         row_bwd<N>(a, bt.j0, bt.nb, k % nbx, k / nbx, bt.G);
@@ -101,58 +116,64 @@ __global__ void __launch_bounds__(kThreads, 2) k_cycle_persistent(PersArgs pa) {
     __shared__ int s_item[3];  // segment, item within the segment, or -1
     __shared__ ProbArgs s_a;   // the item's problem, its work stack at the batch's slot
     __shared__ PBatch s_bt;
+    // thread 0's view of the list: the segment of the last item (items are
+    // taken in increasing order, so the search only moves forward), the batch
+    // and problem whose arguments are in shared memory, and the next item index
+    // (taken while the current item runs)
+    int seg_at = 0, g_at = -1, prob_at = -1;
+    unsigned next = 0;
+    if (threadIdx.x == 0 && !*(volatile int*)&pa.ctl->abort) next = atomicAdd(&pa.ctl->head, 1u);
     for (;;) {
         if (threadIdx.x == 0) {
             int seg = -1, k = 0;
-            if (!*(volatile int*)&pa.ctl->abort) {
-                const unsigned i = atomicAdd(&pa.ctl->head, 1u);
-                if (i < (unsigned)pa.nitems) {
-                    int lo = 0, hi = pa.nseg - 1;  // last segment whose start <= i
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if ((unsigned)pa.seg[mid].start <= i) lo = mid; else hi = mid - 1;
-                    }
-                    seg = lo;
-                    k = (int)(i - (unsigned)pa.seg[lo].start);
-                    const PSeg sg = pa.seg[lo];
-                    // the items this one depends on (earlier in the list)
-                    const unsigned* dep = nullptr;
-                    unsigned target = 0;
-                    if (sg.pass == 1) {
-                        dep = &pa.done[3 * sg.g + 0];
-                        target = pa.batch[sg.g].n[0];
-                    } else if (sg.pass == 2) {
-                        dep = &pa.done[3 * sg.g + 1];
-                        target = pa.batch[sg.g].n[1];
-                    } else if (sg.g >= kSlots) {
-                        dep = &pa.done[3 * (sg.g - kSlots) + 2];
-                        target = pa.batch[sg.g - kSlots].n[2];
-                    }
-                    if (dep) {
-                        const long long t0 = clock64();
-                        while (ld_acquire(dep) < target) {
-                            if (*(volatile int*)&pa.ctl->abort || clock64() - t0 > (1ll << 31)) {
-                                atomicExch(&pa.ctl->abort, 1);
-                                if (pa.err_flag) {
-                                    *(volatile int*)pa.err_flag = 1;
-                                    __threadfence_system();
-                                }
-                                seg = -1;
-                                break;
+            const unsigned i = next;
+            if (!*(volatile int*)&pa.ctl->abort && i < (unsigned)pa.nitems) {
+                while (seg_at + 1 < pa.nseg && (unsigned)pa.seg[seg_at + 1].start <= i) ++seg_at;
+                seg = seg_at;
+                k = (int)(i - (unsigned)pa.seg[seg].start);
+                const PSeg sg = pa.seg[seg];
+                // the items this one depends on (earlier in the list)
+                const unsigned* dep = nullptr;
+                unsigned target = 0;
+                if (sg.pass == 1) {
+                    dep = &pa.done[3 * sg.g + 0];
+                    target = pa.batch[sg.g].n[0];
+                } else if (sg.pass == 2) {
+                    dep = &pa.done[3 * sg.g + 1];
+                    target = pa.batch[sg.g].n[1];
+                } else if (sg.g >= kSlots) {
+                    dep = &pa.done[3 * (sg.g - kSlots) + 2];
+                    target = pa.batch[sg.g - kSlots].n[2];
+                }
+                if (dep) {
+                    const long long t0 = clock64();
+                    while (ld_acquire(dep) < target) {
+                        if (*(volatile int*)&pa.ctl->abort || clock64() - t0 > (1ll << 31)) {
+                            atomicExch(&pa.ctl->abort, 1);
+                            if (pa.err_flag) {
+                                *(volatile int*)pa.err_flag = 1;
+                                __threadfence_system();
                             }
-                            __nanosleep(64);
+                            seg = -1;
+                            break;
                         }
+                        __nanosleep(64);
                     }
                 }
+                if (seg >= 0 && sg.g != g_at) {
+                    s_bt = pa.batch[sg.g];
+                    if (s_bt.prob != prob_at) {
+                        s_a = pa.prob[s_bt.prob];
+                        prob_at = s_bt.prob;
+                    }
+                    s_a.spec = pa.spec + (size_t)(sg.g % kSlots) * pa.slot_elems;
+                    g_at = sg.g;
+                }
+                // the next item index, while this one runs
+                if (seg >= 0) next = atomicAdd(&pa.ctl->head, 1u);
             }
             s_item[0] = seg;
             s_item[1] = k;
-            if (seg >= 0) {
-                const int g = pa.seg[seg].g;
-                s_bt = pa.batch[g];
-                s_a = pa.prob[s_bt.prob];
-                s_a.spec = pa.spec + (size_t)(g % kSlots) * pa.slot_elems;
-            }
         }
         __syncthreads();
         const int seg = s_item[0], k = s_item[1];
