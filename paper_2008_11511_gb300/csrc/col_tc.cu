@@ -27,9 +27,10 @@
 // of a transform the twiddle is applied in registers and the transpose is
 // folded into the A writes of the next stage (thread (c, n1) writes element n1
 // of the vectors (c, k2), all in its own half).  The two halves synchronise
-// only at the start and the end, so one half's MMAs overlap the other half's
-// SIMT work.  The projection and the LLK run in registers as in the FP32
-// column pass.
+// only at each frame's LLK reduction, so within a frame one half's MMAs
+// overlap the other half's SIMT work.  A block loops over about nb / 19
+// frames with the matrices, twiddles and TMEM set up once.  The projection
+// and the LLK run in registers as in the FP32 column pass.
 #include <cuda_bf16.h>
 
 #include <algorithm>
