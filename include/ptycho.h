@@ -340,6 +340,32 @@ ptx_status ptx_llk_static(int32_t N, int32_t K, int32_t J, int32_t Ho, int32_t W
  * PTX_ERR_INVALID_ARG for a null or misaligned pointer. */
 ptx_status ptx_counts_to_float(float* dst, const uint16_t* src, size_t n, void* stream);
 
+/* Photon counts in one byte each plus an escape list: the compact exact form
+ * of count frames whose counts are mostly below 255 (far-field frames are
+ * mostly dark: at 1e6 photons per 256^2 frame 1.6 % of the pixels reach 255,
+ * so the form moves 56 % of the bytes of uint16 counts).
+ *
+ * Host side (synchronous, no device work): out8[i] = min(src[i], 255) for
+ * i < n, and for every i with src[i] >= 255, in increasing i, the escape
+ * (esc_index[k], esc_value[k]) = (i, src[i]); *n_esc = the number of escapes.
+ * src: host uint16 [n]; out8: host uint8 [n]; esc_index: host uint32 [cap];
+ * esc_value: host uint16 [cap].  With cap = 0 and null out8, esc_index and
+ * esc_value the call only counts the escapes.  PTX_ERR_OUT_OF_BOUNDS when the
+ * escapes exceed cap (*n_esc still set, cap entries written);
+ * PTX_ERR_INVALID_ARG for null arrays that are needed or n >= 2^32. */
+ptx_status ptx_encode_counts8(const uint16_t* src, size_t n, uint8_t* out8, uint32_t* esc_index,
+                              uint16_t* esc_value, size_t cap, size_t* n_esc);
+
+/* Device side, asynchronous on the stream: dst[i] = (float)src8[i] for i < n,
+ * then dst[esc_index[k]] = (float)esc_value[k] for k < n_esc (two kernels in
+ * stream order), which restores the counts exactly.  dst: device float32 [n]
+ * (e.g. a problem's iobs array), src8: device uint8 [n], both 16-byte
+ * aligned; esc_index (uint32, indices < n) and esc_value (uint16): device
+ * [n_esc], may be null when n_esc = 0.  n = 0 does nothing.
+ * PTX_ERR_INVALID_ARG for a null or misaligned pointer or n >= 2^32. */
+ptx_status ptx_counts8_to_float(float* dst, const uint8_t* src8, size_t n, const uint32_t* esc_index,
+                                const uint16_t* esc_value, size_t n_esc, void* stream);
+
 /* Self-test of the failure path of the bounded device waits (no GPU fault is
  * involved): enqueues one kernel whose single waiting thread waits for a flag
  * that nothing sets, for at most limit_us microseconds of the GPU's global

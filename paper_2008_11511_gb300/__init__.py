@@ -10,7 +10,8 @@ import importlib
 
 from ._lib import PtychoError, SUPPORTED_SIZES, load  # noqa: F401
 
-_LAZY = ("Ptycho", "PtychoBatch", "PtychoLLK", "fft2", "counts_to_float", "fma_tflops")
+_LAZY = ("Ptycho", "PtychoBatch", "PtychoLLK", "fft2", "counts_to_float", "encode_counts8", "counts8_to_float",
+         "fma_tflops")
 
 
 def __getattr__(name):

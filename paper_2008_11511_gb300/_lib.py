@@ -43,7 +43,8 @@ EXPORTS = (
     "ptx_workspace_bytes", "ptx_create", "ptx_ap_cycles", "ptx_dm_cycles", "ptx_cycles", "ptx_llk", "ptx_ml_grad",
     "ptx_ml_cycles", "ptx_ml_line_coeffs", "ptx_position_shifts", "ptx_set_positions",
     "ptx_normalise", "ptx_accumulators", "ptx_set_param", "ptx_fft2", "ptx_profile_enable", "ptx_profile_read",
-    "ptx_llk_static", "ptx_counts_to_float", "ptx_wait_selftest", "ptx_fma_peak", "ptx_accumulate_shifts", "ptx_cycle_kernels",
+    "ptx_llk_static", "ptx_counts_to_float", "ptx_encode_counts8", "ptx_counts8_to_float", "ptx_wait_selftest",
+    "ptx_fma_peak", "ptx_accumulate_shifts", "ptx_cycle_kernels",
     "ptx_last_error", "ptx_destroy",
 )
 KERNEL_KINDS = ("row_fwd", "col", "row_bwd", "den_max", "normalise", "cycle_end", "obj_gather")
@@ -116,6 +117,8 @@ def load(path: str | None = None):
         "ptx_profile_read": (st, [vp, i32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
         "ptx_llk_static": (st, [i32, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]),
         "ptx_counts_to_float": (st, [vp, vp, sz, vp]),
+        "ptx_encode_counts8": (st, [vp, sz, vp, vp, vp, sz, ctypes.POINTER(sz)]),
+        "ptx_counts8_to_float": (st, [vp, vp, sz, vp, vp, sz, vp]),
         "ptx_wait_selftest": (st, [vp, i32, vp]),
         "ptx_fma_peak": (st, [i32, i32, vp, ctypes.POINTER(ctypes.c_double), vp]),
         "ptx_cycle_kernels": (st, [vp, i32, u32, ctypes.POINTER(ctypes.c_int64)]),

@@ -1488,6 +1488,51 @@ ptx_status ptx_counts_to_float(float* dst, const uint16_t* src, size_t n, void* 
     return PTX_OK;
 }
 
+ptx_status ptx_encode_counts8(const uint16_t* src, size_t n, uint8_t* out8, uint32_t* esc_index,
+                              uint16_t* esc_value, size_t cap, size_t* n_esc) {
+    if (!n_esc) return fail(PTX_ERR_INVALID_ARG, "n_esc is null");
+    *n_esc = 0;
+    if (n >= ((size_t)1 << 32)) return fail(PTX_ERR_INVALID_ARG, "n must be below 2^32");
+    if (n == 0) return PTX_OK;
+    const bool count_only = cap == 0 && !out8 && !esc_index && !esc_value;
+    if (!src || (!count_only && (!out8 || (cap > 0 && (!esc_index || !esc_value)))))
+        return fail(PTX_ERR_INVALID_ARG, "null array");
+    size_t k = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const uint16_t c = src[i];
+        if (!count_only) out8[i] = c < 255 ? (uint8_t)c : (uint8_t)255;
+        if (c >= 255) {
+            if (!count_only && k < cap) {
+                esc_index[k] = (uint32_t)i;
+                esc_value[k] = c;
+            }
+            ++k;
+        }
+    }
+    *n_esc = k;
+    if (!count_only && k > cap) return fail(PTX_ERR_OUT_OF_BOUNDS, "%zu escapes exceed the capacity %zu", k, cap);
+    return PTX_OK;
+}
+
+ptx_status ptx_counts8_to_float(float* dst, const uint8_t* src8, size_t n, const uint32_t* esc_index,
+                                const uint16_t* esc_value, size_t n_esc, void* stream) {
+    if (n == 0) return PTX_OK;
+    if (!dst || !src8) return fail(PTX_ERR_INVALID_ARG, "null dst or src8");
+    if (n >= ((size_t)1 << 32)) return fail(PTX_ERR_INVALID_ARG, "n must be below 2^32");
+    if ((uintptr_t)dst % 16 || (uintptr_t)src8 % 16)
+        return fail(PTX_ERR_INVALID_ARG, "dst and src8 must be 16-byte aligned");
+    if (n_esc > 0 && (!esc_index || !esc_value)) return fail(PTX_ERR_INVALID_ARG, "null escape arrays");
+    cudaStream_t s = (cudaStream_t)stream;
+    k_counts8_to_float<<<4 * 152, 256, 0, s>>>(src8, dst, n);
+    if (n_esc > 0) {
+        const int blocks = (int)std::min<size_t>((n_esc + 255) / 256, 4 * 152);
+        k_counts8_escapes<<<blocks, 256, 0, s>>>(esc_index, esc_value, dst, n_esc);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "ptx_counts8_to_float launch");
+    return PTX_OK;
+}
+
 ptx_status ptx_fma_peak(int32_t blocks, int32_t iters, float* sink, double* flops, void* stream) {
     if (blocks < 1 || iters < 1 || !sink || !flops)
         return fail(PTX_ERR_INVALID_ARG, "blocks and iters must be >= 1, sink and flops non-null");

@@ -264,6 +264,31 @@ __global__ void k_counts_to_float(const uint16_t* __restrict__ src, float* __res
     for (size_t i = 8 * n8 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = (float)src[i];
 }
 
+// One-byte counts to float32: 16 counts (16 bytes) per thread and step.
+__global__ void k_counts8_to_float(const uint8_t* __restrict__ src, float* __restrict__ dst, size_t n) {
+    const size_t n16 = n / 16;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(src) + i);
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        float4* d = reinterpret_cast<float4*>(dst) + 4 * i;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            d[q] = make_float4((float)(w[q] & 0xffu), (float)((w[q] >> 8) & 0xffu), (float)((w[q] >> 16) & 0xffu),
+                               (float)(w[q] >> 24));
+    }
+    // the tail (n not a multiple of 16)
+    for (size_t i = 16 * n16 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = (float)src[i];
+}
+
+// The escapes of the one-byte form: dst[index[k]] = value[k].
+__global__ void k_counts8_escapes(const uint32_t* __restrict__ index, const uint16_t* __restrict__ value,
+                                  float* __restrict__ dst, size_t n_esc) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_esc; k += stride)
+        dst[index[k]] = (float)value[k];
+}
+
 __global__ void k_set_ctl(Ctl* ctl, double* llk_out, int nprob) {
     ctl->llk_out = llk_out;
     ctl->cycle = 0;

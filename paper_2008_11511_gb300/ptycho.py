@@ -408,6 +408,49 @@ def counts_to_float(dst: torch.Tensor, counts: torch.Tensor) -> torch.Tensor:
     return dst
 
 
+def encode_counts8(counts) -> tuple:
+    """Host side of the one-byte count form (ptx_encode_counts8): ``counts``
+    is a uint16 array (any shape); returns (uint8 array of the same shape with
+    the counts clipped at 255, uint32 flat indices and uint16 values of the
+    counts >= 255, in increasing index)."""
+    import numpy as np
+    c = np.ascontiguousarray(counts, dtype=np.uint16)
+    n = c.size
+    n_esc = ctypes.c_size_t(0)
+    _lib.call("ptx_encode_counts8", ctypes.c_void_p(c.ctypes.data), ctypes.c_size_t(n), None, None, None,
+              ctypes.c_size_t(0), ctypes.byref(n_esc))
+    out8 = np.empty(c.shape, dtype=np.uint8)
+    idx = np.empty(n_esc.value, dtype=np.uint32)
+    val = np.empty(n_esc.value, dtype=np.uint16)
+    _lib.call("ptx_encode_counts8", ctypes.c_void_p(c.ctypes.data), ctypes.c_size_t(n),
+              ctypes.c_void_p(out8.ctypes.data), ctypes.c_void_p(idx.ctypes.data), ctypes.c_void_p(val.ctypes.data),
+              ctypes.c_size_t(n_esc.value), ctypes.byref(n_esc))
+    return out8, idx, val
+
+
+def counts8_to_float(dst: torch.Tensor, counts8: torch.Tensor, esc_index: torch.Tensor,
+                     esc_value: torch.Tensor) -> torch.Tensor:
+    """dst[...] = the counts of the one-byte form, on the GPU: the uint8
+    counts widened to float32, then the escapes (uint32 flat indices into dst,
+    uint16 values) written over them.  CUDA tensors; returns ``dst``."""
+    _require_cuda(dst, "dst", torch.float32)
+    _require_cuda(counts8, "counts8", torch.uint8)
+    if counts8.numel() != dst.numel():
+        raise ValueError("counts8 and dst must have the same number of elements")
+    if esc_index.numel() != esc_value.numel():
+        raise ValueError("esc_index and esc_value must have the same length")
+    n_esc = esc_index.numel()
+    if n_esc:
+        _require_cuda(esc_index, "esc_index", torch.uint32)
+        _require_cuda(esc_value, "esc_value", torch.uint16)
+    with torch.cuda.device(dst.device):
+        _lib.call("ptx_counts8_to_float", ctypes.c_void_p(dst.data_ptr()), ctypes.c_void_p(counts8.data_ptr()),
+                  ctypes.c_size_t(dst.numel()), ctypes.c_void_p(esc_index.data_ptr() if n_esc else None),
+                  ctypes.c_void_p(esc_value.data_ptr() if n_esc else None), ctypes.c_size_t(n_esc),
+                  _stream_ptr(dst.device))
+    return dst
+
+
 class PtychoLLK(torch.autograd.Function):
     """L(O, P) = Poisson LLK as a differentiable function of the object and the
     probe.  ``forward`` copies (obj, probe) into the problem's buffers and calls

@@ -112,6 +112,45 @@ def test_work_stack_sizing(lib):
     assert 64 * mb < n512k1 < 96 * mb
 
 
+def test_encode_counts8_matches_its_definition(lib):
+    """ptx_encode_counts8 (host): out8 = min(c, 255), escapes = every index
+    with c >= 255 in increasing order with its count; boundaries 254 / 255 /
+    256 / 65535, an empty input, the count-only query and a too-small
+    capacity."""
+    from paper_2008_11511_gb300._lib import STATUS_NAMES
+    from paper_2008_11511_gb300 import encode_counts8
+    rng = np.random.default_rng(7)
+    c = rng.poisson(3.0, size=(5, 37, 41)).astype(np.uint16)
+    c[0, 0, :6] = [0, 254, 255, 256, 65535, 1]
+    c[4, -1, -3:] = [255, 65534, 300]
+    out8, idx, val = encode_counts8(c)
+    flat = c.ravel()
+    want_idx = np.nonzero(flat >= 255)[0]
+    assert out8.dtype == np.uint8 and out8.shape == c.shape
+    np.testing.assert_array_equal(out8, np.minimum(c, 255).astype(np.uint8))
+    np.testing.assert_array_equal(idx, want_idx.astype(np.uint32))
+    np.testing.assert_array_equal(val, flat[want_idx])
+    # decoding on the host by the definition gives the counts back
+    dec = out8.ravel().astype(np.uint32)
+    dec[idx] = val
+    np.testing.assert_array_equal(dec, flat)
+    # empty input; count-only query; too small a capacity
+    o0, i0, v0 = encode_counts8(np.zeros((0,), dtype=np.uint16))
+    assert o0.size == 0 and i0.size == 0 and v0.size == 0
+    n_esc = ctypes.c_size_t(0)
+    assert lib.ptx_encode_counts8(flat.ctypes.data, flat.size, None, None, None, 0, ctypes.byref(n_esc)) == 0
+    assert n_esc.value == want_idx.size
+    o = np.empty(flat.size, dtype=np.uint8)
+    ib = np.empty(2, dtype=np.uint32)
+    vb = np.empty(2, dtype=np.uint16)
+    st = lib.ptx_encode_counts8(flat.ctypes.data, flat.size, o.ctypes.data, ib.ctypes.data, vb.ctypes.data, 2,
+                                ctypes.byref(n_esc))
+    assert STATUS_NAMES[st] == "PTX_ERR_OUT_OF_BOUNDS" and n_esc.value == want_idx.size
+    np.testing.assert_array_equal(ib, want_idx[:2].astype(np.uint32))
+    assert STATUS_NAMES[lib.ptx_encode_counts8(None, 10, None, None, None, 0, ctypes.byref(n_esc))] == \
+        "PTX_ERR_INVALID_ARG"
+
+
 def test_null_handle_calls_fail_cleanly(lib):
     from paper_2008_11511_gb300._lib import STATUS_NAMES
     assert STATUS_NAMES[lib.ptx_ap_cycles(None, 1, 3, None, None)] == "PTX_ERR_INVALID_ARG"

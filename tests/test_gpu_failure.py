@@ -129,3 +129,38 @@ def test_tensor_core_stage_wait_gives_up_and_reports():
     assert np.linalg.norm(obj[ill] - o[ill]) / np.linalg.norm(o[ill]) < 2e-5
     assert np.linalg.norm(pb.probe.cpu().numpy() - p) / np.linalg.norm(p) < 2e-5
     pb.close()
+
+
+def test_counts8_round_trip_is_exact_with_a_ragged_tail():
+    """The one-byte count form: host encoding, device decoding (uint8 widened,
+    then the escapes written over them) restores every count exactly; n not a
+    multiple of the 16 counts a thread converts at once; also without escapes."""
+    from paper_2008_11511_gb300 import counts8_to_float, encode_counts8
+    rng = np.random.default_rng(11)
+    n = 1_000_003
+    c = rng.poisson(40.0, size=n).astype(np.uint16)
+    hot = rng.choice(n, size=20_000, replace=False)
+    c[hot] = rng.integers(255, 65536, size=hot.size, dtype=np.uint16)
+    c[:4] = (0, 254, 255, 65535)
+    c[-2:] = (256, 255)
+    out8, idx, val = encode_counts8(c)
+    dst = torch.full((n,), -1.0, dtype=torch.float32, device="cuda")
+    counts8_to_float(dst, torch.from_numpy(out8).cuda(), torch.from_numpy(idx).cuda(), torch.from_numpy(val).cuda())
+    assert np.array_equal(dst.cpu().numpy(), c.astype(np.float32))
+    small = np.minimum(c, 200).astype(np.uint16)
+    o8, i8, v8 = encode_counts8(small)
+    assert i8.size == 0
+    dst.fill_(-1.0)
+    counts8_to_float(dst, torch.from_numpy(o8).cuda(), torch.from_numpy(i8).cuda(), torch.from_numpy(v8).cuda())
+    assert np.array_equal(dst.cpu().numpy(), small.astype(np.float32))
+
+
+def test_counts8_to_float_rejects_misaligned_pointers():
+    from paper_2008_11511_gb300 import _lib
+    from paper_2008_11511_gb300._lib import PtychoError
+    buf = torch.zeros(64, dtype=torch.float32, device="cuda")
+    src = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(PtychoError) as ei:
+        _lib.call("ptx_counts8_to_float", ctypes.c_void_p(buf.data_ptr() + 4), ctypes.c_void_p(src.data_ptr()),
+                  ctypes.c_size_t(16), None, None, ctypes.c_size_t(0), None)
+    assert ei.value.status_name == "PTX_ERR_INVALID_ARG"
