@@ -257,8 +257,8 @@ __global__ void k_counts_to_float(const uint16_t* __restrict__ src, float* __res
         hi.x = (float)(w[2] & 0xffffu); hi.y = (float)(w[2] >> 16);
         hi.z = (float)(w[3] & 0xffffu); hi.w = (float)(w[3] >> 16);
         float4* d = reinterpret_cast<float4*>(dst) + 2 * i;
-        d[0] = lo;
-        d[1] = hi;
+        __stcs(d, lo);  // streaming stores: the intensities are read a cycle later,
+        __stcs(d + 1, hi);  // they should not push the work stack out of L2
     }
     // the tail (n not a multiple of 8)
     for (size_t i = 8 * n8 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = (float)src[i];
@@ -273,9 +273,9 @@ __global__ void k_counts8_to_float(const uint8_t* __restrict__ src, float* __res
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
         float4* d = reinterpret_cast<float4*>(dst) + 4 * i;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            d[q] = make_float4((float)(w[q] & 0xffu), (float)((w[q] >> 8) & 0xffu), (float)((w[q] >> 16) & 0xffu),
-                               (float)(w[q] >> 24));
+        for (int q = 0; q < 4; ++q)  // streaming stores, as in k_counts_to_float
+            __stcs(d + q, make_float4((float)(w[q] & 0xffu), (float)((w[q] >> 8) & 0xffu),
+                                      (float)((w[q] >> 16) & 0xffu), (float)(w[q] >> 24)));
     }
     // the tail (n not a multiple of 16)
     for (size_t i = 16 * n16 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = (float)src[i];
