@@ -40,6 +40,9 @@ FORMS = {0: "fp32 (plain)",
          1: "tf32 hi+lo tensor-core DFT stages in the column pass, fp32 elsewhere",
          2: "bf16 hi+mid+lo tensor-core DFT stages in the column pass, fp32 elsewhere",
          3: "bf16 hi+lo tensor-core DFT stages in the column pass (below fp32 accuracy), fp32 elsewhere"}
+FORMS_ALL = {1: "tf32 hi+lo tensor-core DFT stages in every pass (column and rows)",
+             2: "bf16 hi+mid+lo tensor-core DFT stages in every pass (column and rows)",
+             3: "bf16 hi+lo tensor-core DFT stages in every pass (below fp32 accuracy)"}
 PROFILES = os.path.join(ROOT, "profiles")
 
 
@@ -598,10 +601,10 @@ def run_ours(args):
     other = None
     if not args.no_form_comparison and s.N == 256 and s.K == 1:
         other = []
-        for tc_other in range(4):
-            if tc_other == args.tc:
-                continue
+        variants = [(f, 0) for f in range(4) if f != args.tc] + [(f, 1) for f in (1, 2, 3)]
+        for tc_other, rows in variants:
             pb.set_param("tc", tc_other)
+            pb.set_param("tc_rows", rows)
             pb.dm(2, llk=llk_buf)  # capture the other form's graph
             torch.cuda.synchronize(dev)
             n_other = max(1, min(args.steps, 10))
@@ -612,9 +615,10 @@ def run_ours(args):
             f1.record(stream)
             torch.cuda.synchronize(dev)
             ms_o = max_over_ranks(f0.elapsed_time(f1), ws) / n_other
-            other.append({"form": FORMS[tc_other], "value": s.J * ws / (ms_o / 1e3), "ms_per_step": ms_o,
-                          "steps": n_other})
+            other.append({"form": FORMS_ALL[tc_other] if rows else FORMS[tc_other], "value": s.J * ws / (ms_o / 1e3),
+                          "ms_per_step": ms_o, "steps": n_other})
         pb.set_param("tc", args.tc)
+        pb.set_param("tc_rows", 0)
         pb.dm(1, llk=llk_buf)
         torch.cuda.synchronize(dev)
 

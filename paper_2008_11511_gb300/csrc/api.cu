@@ -80,7 +80,7 @@ static cudaError_t ensure_attributes() {
     cudaError_t (*fns[])() = {set_attrs_8,   set_attrs_12,  set_attrs_16,  set_attrs_32,  set_attrs_64,
                               set_attrs_128, set_attrs_192, set_attrs_256, set_attrs_384, set_attrs_512,
                               set_attrs_80,  set_attrs_160, set_attrs_224, set_attrs_400, set_attrs_448,
-                              set_attrs_gather_tma, set_attrs_tc, set_attrs_persistent};
+                              set_attrs_gather_tma, set_attrs_tc, set_attrs_row_tc, set_attrs_persistent};
     for (auto f : fns)
         if ((e = f()) != cudaSuccess) return e;
     if (dev < 32) done_mask |= 1 << dev;
@@ -460,6 +460,7 @@ struct ptx_handle {
     bool pers_dirty = true;  // tables to rebuild and upload before the next cycle
     int pers_selftest = 0;   // ptx_set_param "persistent_selftest": a dependency that is never met
     int tc_selftest = 0;     // ptx_set_param "tc_selftest": a tensor-core stage whose commit never comes
+    int tc_rows = 0;         // ptx_set_param "tc_rows": the row passes' DFT stages on the tensor cores too
     int pers_nitems = 0, pers_nseg = 0, pers_nbatch = 0;
     std::vector<ProbArgs> pers_prob;
     std::vector<PSeg> pers_seg;
@@ -864,6 +865,10 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
         const bool upd_bg = (flags & PTX_UPDATE_BACKGROUND) && algo == ALGO_AP && ph.p.background;
         const int fwd_mode = (algo == ALGO_DM && !init) ? X_DM : X_PHI;
         const int bwd_mode = (algo == ALGO_DM) ? BWD_DM : BWD_AP;
+        // the row passes' DFT stages on the tensor cores (with a tensor-core form,
+        // "tc_rows", 256^2 far-field frames of one mode without a background)
+        const bool tc_rows = form != TC_NONE && h->tc_rows && ph.p.N == 256 && ph.p.K == 1 &&
+                             ph.p.nearfield <= 0.0 && !ph.p.background;
         bool used[kMaxLanes] = {};
         for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
             const int nb = std::min(ph.B, ph.p.J - j0);
@@ -877,7 +882,10 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
             if (upd_bg) al.bg_acc = (float*)(h->scratch + ph.lay.bg_acc);
             {
                 ProfScope ps(h, PTX_KERNEL_ROW_FWD, ls);
-                ks->row_fwd(al, j0, nb, fwd_mode, ls);
+                if (tc_rows)
+                    launch_row_fwd_tc(al, j0, nb, fwd_mode == X_DM, form, ls);
+                else
+                    ks->row_fwd(al, j0, nb, fwd_mode, ls);
             }
             if (ph.p.nearfield > 0.0) {
                 // propagate, project at the detector, propagate back
@@ -908,7 +916,10 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
             }
             {
                 ProfScope ps(h, PTX_KERNEL_ROW_BWD, ls);
-                ks->row_bwd(al, j0, nb, G, bwd_mode, 0, upd_p, ls);
+                if (tc_rows)
+                    launch_row_bwd_tc(al, j0, nb, G, upd_p ? 1 : 0, form, ls);
+                else
+                    ks->row_bwd(al, j0, nb, G, bwd_mode, 0, upd_p, ls);
             }
         }
         if (lanes > 1)
@@ -1449,6 +1460,9 @@ ptx_status ptx_set_param(ptx_handle* h, const char* name, double value) {
     } else if (!strcmp(name, "persistent_selftest")) {
         if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "persistent_selftest must be 0 or 1");
         h->pers_selftest = (int)value;
+    } else if (!strcmp(name, "tc_rows")) {
+        if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "tc_rows must be 0 or 1");
+        h->tc_rows = (int)value;
     } else if (!strcmp(name, "tc_selftest")) {
         if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "tc_selftest must be 0 or 1");
         h->tc_selftest = (int)value;

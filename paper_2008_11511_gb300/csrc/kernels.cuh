@@ -629,6 +629,11 @@ enum TcForm : int { TC_NONE = 0, TC_TF32X2 = 1, TC_BF16X3 = 2, TC_BF16X2 = 3 };
 // its bounded wait runs out and the launch reports through err_flag.
 void launch_col_tc(const ProbArgs& a, int j0, int nb, int form, int selftest, cudaStream_t s);
 cudaError_t set_attrs_tc();
+// The row passes with their DFT stages on the tensor cores (256^2, one mode):
+// the same work-stack layout as k_row_fwd_r<256> / k_row_bwd_r<256, 1>.
+void launch_row_fwd_tc(const ProbArgs& a, int j0, int nb, bool dm, int form, cudaStream_t s);
+void launch_row_bwd_tc(const ProbArgs& a, int j0, int nb, int G, int upd_probe, int form, cudaStream_t s);
+cudaError_t set_attrs_row_tc();
 // SMs of the current device (api.cu)
 int sm_count();
 // The same gather fed by 3D tensor copies (32 x 32 tiles, N >= 64).

@@ -1,0 +1,211 @@
+// Forward and backward row passes of the cycle with the two 16-point DFT
+// stages of each 256-point row transform on the tensor cores (the
+// split-precision form of the paper's FT / IFT operators on the rows; 256^2
+// frames, one probe mode).  Same inputs, outputs and work-stack layout as the
+// register passes k_row_fwd_r<256> and k_row_bwd_r<256, 1>, so either can run
+// beside the FP32 or the tensor-core column pass.
+//
+// A block holds a band of 16 rows as two independent halves of 8 rows
+// (tc::Pipe256: own A tile, mbarrier, TMEM columns and named barrier).  Thread
+// u of half h is (row 8 h + u / 16 of the band, index q = u % 16) and owns row
+// u of its half's tile in every stage; the stage-2 vectors of a row are the 16
+// tile rows of that row (16 (u / 16) + k).  A block loops over frames (the
+// matrices, twiddles and TMEM set up once).
+#include <algorithm>
+
+#include "tc.cuh"
+
+namespace ptx {
+
+// grid (16 bands, frame slots), 256 threads.  X = P O (AP, and the
+// initialising DM cycle) or 2 P O - Psi (DM) along row y of each frame, its
+// 256-point row DFT written to the work stack (unnormalised, as the FP32 pass).
+template <int F, bool kDM>
+__global__ void __launch_bounds__(256, 2) k_row_fwd_tc(ProbArgs a, int j0, int nb) {
+    using namespace tc;
+    extern __shared__ unsigned char smraw[];
+    const int t = threadIdx.x, h = t >> 7, u = t & 127, cl = u >> 4, q = u & 15;
+    const int y = blockIdx.x * 16 + 8 * h + cl;
+    Pipe256<F> pp;
+    pp.setup(smraw, false);
+    const float2* tw = pp.tw;
+    const float2* pr = a.probe + (size_t)y * N + q;  // probe row y, columns q + 16 n2
+    float2 v[16];
+    float o[32];
+    bool good = true, bad = false;
+    for (int b = blockIdx.y; b < nb; b += gridDim.y) {
+        const int j = j0 + b;
+        const int2 p = a.pos[j];
+        // stage-1 vector (row y, n1 = q): X[q + 16 n2], n2 = 0..15
+        const float2* ob = a.obj + (size_t)(p.x + y) * a.Wo + p.y + q;
+        if constexpr (kDM) {
+            const float2* ps = a.psi + ((size_t)j * N + y) * N + q;
+            const uint64_t ef = policy_evict_first();
+#pragma unroll
+            for (int n2 = 0; n2 < 16; ++n2) v[n2] = ld_hint(ps + 16 * n2, ef);
+#pragma unroll
+            for (int n2 = 0; n2 < 16; ++n2) {
+                const float2 phi = cmul(__ldg(pr + 16 * n2), ob[16 * n2]);
+                v[n2] = make_float2(2.f * phi.x - v[n2].x, 2.f * phi.y - v[n2].y);
+            }
+        } else {
+#pragma unroll
+            for (int n2 = 0; n2 < 16; ++n2) v[n2] = cmul(__ldg(pr + 16 * n2), ob[16 * n2]);
+        }
+        pp.put_row(v);
+        good = pp.stage(0, o);
+        if (good) {
+            // twiddle w^(n1 k2) and the transpose into the vectors (row, k2): tile rows 16 cl + k2
+#pragma unroll
+            for (int k2 = 0; k2 < 16; ++k2) {
+                const float2 yv = make_float2(o[2 * k2], o[2 * k2 + 1]);
+                v[k2] = k2 == 0 ? yv : cmul(yv, tw_get<N, -1>(tw, k2, q));
+            }
+            pp.template put_col<1>(v, 16 * cl, q);
+            good = pp.stage(0, o);
+        }
+        if (good) {
+            // X^[k2 + 16 k1] of row y (thread = vector (row, k2 = q))
+            float2* dst = a.spec + ((size_t)b * N + y) * N + q;
+            const uint64_t el = policy_evict_last();
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) st_hint(dst + 16 * k1, make_float2(o[2 * k1], o[2 * k1 + 1]), el);
+        }
+        bad = __syncthreads_or(!good);
+        if (bad) break;
+    }
+    pp.finish(good, bad, a.err_flag);
+}
+
+// grid (16 bands, G frame slots), 256 threads.  The inverse row DFT of the
+// work stack's row y gives the correction D; Psi' = P O + D is stored (AP and
+// DM alike), and with upd_probe the probe numerator conj(O) Psi' and
+// denominator |O|^2 of the thread's 16 pixels are summed in registers over the
+// block's frames (slot, slot + G, ...) and added to the accumulator once.
+template <int F>
+__global__ void __launch_bounds__(256, 2) k_row_bwd_tc(ProbArgs a, int j0, int nb, int upd_probe) {
+    using namespace tc;
+    extern __shared__ unsigned char smraw[];
+    const int t = threadIdx.x, h = t >> 7, u = t & 127, cl = u >> 4, q = u & 15;
+    const int y = blockIdx.x * 16 + 8 * h + cl;
+    Pipe256<F> pp;
+    pp.setup(smraw, false);
+    const float2* tw = pp.tw;
+    const float2* pr = a.probe + (size_t)y * N + q;  // probe row y, columns q + 16 k1
+    float2 np[16];
+    float dp[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        np[k] = make_float2(0.f, 0.f);
+        dp[k] = 0.f;
+    }
+    float2 v[16];
+    float o[32];
+    bool good = true, bad = false;
+    for (int b = blockIdx.y; b < nb; b += gridDim.y) {
+        const int j = j0 + b;
+        const int2 p = a.pos[j];
+        // stage-1 vector (row y, k2 = q): the work stack's D^[q + 16 k1], its last read
+        {
+            const float2* src = a.spec + ((size_t)b * N + y) * N + q;
+            const uint64_t ef = policy_evict_first();
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) v[k1] = ld_hint(src + 16 * k1, ef);
+        }
+        pp.put_row(v);
+        good = pp.stage(1, o);
+        if (good) {
+            // twiddle w^(+k2 kk) and the transpose into the vectors (row, kk): tile rows 16 cl + kk
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) {
+                const float2 yv = make_float2(o[2 * kk], o[2 * kk + 1]);
+                v[kk] = kk == 0 ? yv : cmul(yv, tw_get<N, +1>(tw, q, kk));
+            }
+            pp.template put_col<1>(v, 16 * cl, q);
+            good = pp.stage(1, o);
+        }
+        if (good) {
+            // D at the pixels kk + 16 k1' of row y (thread = vector (row, kk = q))
+            const float2* ob = a.obj + (size_t)(p.x + y) * a.Wo + p.y + q;
+            float2* ps = a.psi + ((size_t)j * N + y) * N + q;
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1) {
+                const float2 obv = ob[16 * k1];
+                const float2 wv = cadd(cmul(__ldg(pr + 16 * k1), obv), make_float2(o[2 * k1], o[2 * k1 + 1]));
+                __stcs(ps + 16 * k1, wv);
+                if (upd_probe) {
+                    const float2 tt = cconjmul(obv, wv);
+                    np[k1].x += tt.x;
+                    np[k1].y += tt.y;
+                    dp[k1] += cnorm(obv);
+                }
+            }
+        }
+        bad = __syncthreads_or(!good);
+        if (bad) break;
+    }
+    if (upd_probe && !bad) {
+        float4* acc = a.acc_probe + (size_t)y * N + q;
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) red_add_v4(acc + 16 * k1, np[k1].x, np[k1].y, dp[k1], 0.f);
+    }
+    pp.finish(good, bad, a.err_flag);
+}
+
+// Frame slots of the tensor-core row passes: two blocks per SM over the 16
+// bands; each block runs about nb / slots frames.
+static int tc_row_slots(int nb) {
+    const int slots = std::max(1, 2 * sm_count() / 16);
+    const int per = (nb + slots - 1) / slots;
+    return (nb + per - 1) / per;
+}
+
+void launch_row_fwd_tc(const ProbArgs& a, int j0, int nb, bool dm, int form, cudaStream_t s) {
+    dim3 grid(16, tc_row_slots(nb));
+    using namespace tc;
+    if (form == TC_BF16X3) {
+        if (dm)
+            k_row_fwd_tc<TC_BF16X3, true><<<grid, 256, Fmt<TC_BF16X3>::kBytes, s>>>(a, j0, nb);
+        else
+            k_row_fwd_tc<TC_BF16X3, false><<<grid, 256, Fmt<TC_BF16X3>::kBytes, s>>>(a, j0, nb);
+    } else if (form == TC_BF16X2) {
+        if (dm)
+            k_row_fwd_tc<TC_BF16X2, true><<<grid, 256, Fmt<TC_BF16X2>::kBytes, s>>>(a, j0, nb);
+        else
+            k_row_fwd_tc<TC_BF16X2, false><<<grid, 256, Fmt<TC_BF16X2>::kBytes, s>>>(a, j0, nb);
+    } else {
+        if (dm)
+            k_row_fwd_tc<TC_TF32X2, true><<<grid, 256, Fmt<TC_TF32X2>::kBytes, s>>>(a, j0, nb);
+        else
+            k_row_fwd_tc<TC_TF32X2, false><<<grid, 256, Fmt<TC_TF32X2>::kBytes, s>>>(a, j0, nb);
+    }
+}
+
+void launch_row_bwd_tc(const ProbArgs& a, int j0, int nb, int G, int upd_probe, int form, cudaStream_t s) {
+    dim3 grid(16, std::max(1, std::min(G, nb)));
+    using namespace tc;
+    if (form == TC_BF16X3)
+        k_row_bwd_tc<TC_BF16X3><<<grid, 256, Fmt<TC_BF16X3>::kBytes, s>>>(a, j0, nb, upd_probe);
+    else if (form == TC_BF16X2)
+        k_row_bwd_tc<TC_BF16X2><<<grid, 256, Fmt<TC_BF16X2>::kBytes, s>>>(a, j0, nb, upd_probe);
+    else
+        k_row_bwd_tc<TC_TF32X2><<<grid, 256, Fmt<TC_TF32X2>::kBytes, s>>>(a, j0, nb, upd_probe);
+}
+
+template <int F>
+static cudaError_t set_attrs_row_tc_f() {
+    const int bytes = (int)tc::Fmt<F>::kBytes;
+    cudaError_t e = cudaFuncSetAttribute(k_row_fwd_tc<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_row_fwd_tc<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_row_bwd_tc<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+cudaError_t set_attrs_row_tc() {
+    cudaError_t e = set_attrs_row_tc_f<TC_TF32X2>();
+    if (e == cudaSuccess) e = set_attrs_row_tc_f<TC_BF16X3>();
+    if (e == cudaSuccess) e = set_attrs_row_tc_f<TC_BF16X2>();
+    return e;
+}
+
+}  // namespace ptx

@@ -658,6 +658,38 @@ def test_dm256_split_precision_forms_accuracy():
     assert 2 * max(errs["fp32"]) < max(errs["bf16x2"]) < 1e-4, errs
 
 
+@pytest.mark.parametrize("form", [1, 2, 3])
+@pytest.mark.parametrize("lanes,batch", [(2, 0), (1, 37)])
+def test_dm256_all_dft_stages_on_tensor_cores(form, lanes, batch):
+    """With "tc_rows" the forward and backward row passes run their DFT stages
+    on the tensor cores too (every DFT stage of the cycle in the split form):
+    three DM cycles and one AP cycle against the FP64 oracle, in two lanes and
+    in one lane with ragged 37-frame batches; TF32 hi + lo and BF16 hi + mid +
+    lo at the FP32 tolerance, BF16 hi + lo within 1e-4."""
+    tol = TOL1 * 3 if form in (1, 2) else 1e-4
+    s, o0, p0 = warm("dm256", J=150, Ho=640, Wo=640)
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    pb.set_param("tc", form)
+    pb.set_param("tc_rows", 1)
+    pb.set_param("lanes", lanes)
+    pb.set_param("batch_frames", batch)
+    llk = pb.dm(3, init_psi=True).cpu().numpy()
+    o, p, psi, llk_ref = oracle.cycles("DM", o0, p0, data_of(s), 3)
+    _compare_cycle_state(s, pb, o, p, tol, psi_ref=psi)
+    np.testing.assert_allclose(llk, llk_ref, rtol=tol)
+    pb.close()
+    pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+    pb.set_param("tc", form)
+    pb.set_param("tc_rows", 1)
+    pb.set_param("lanes", lanes)
+    pb.set_param("batch_frames", batch)
+    l1 = pb.ap(1).cpu().numpy()
+    o, p, l = oracle.ap_cycle(o0, p0, data_of(s))
+    _compare_cycle_state(s, pb, o, p, tol)
+    assert abs(l1[0] - l) / abs(l) < tol
+    pb.close()
+
+
 @pytest.mark.parametrize("K", [1, 3])
 def test_modes512_split_precision_forms(K):
     """The 512^2 column pass with its DFT stages on the tensor cores (a 16-point
