@@ -549,6 +549,8 @@ def run_ours(args):
         params.append(("tma_gather", args.tma_gather))
     if args.tc:
         params.append(("tc", args.tc))
+    if args.tc_rows:
+        params.append(("tc_rows", 1))
     for name, val in params:
         pb.set_param(name, val)
     stream = torch.cuda.current_stream(dev)
@@ -618,7 +620,7 @@ def run_ours(args):
             other.append({"form": FORMS_ALL[tc_other] if rows else FORMS[tc_other], "value": s.J * ws / (ms_o / 1e3),
                           "ms_per_step": ms_o, "steps": n_other})
         pb.set_param("tc", args.tc)
-        pb.set_param("tc_rows", 0)
+        pb.set_param("tc_rows", 1 if args.tc_rows else 0)
         pb.dm(1, llk=llk_buf)
         torch.cuda.synchronize(dev)
 
@@ -764,6 +766,8 @@ def main():
     ap.add_argument("--tc", type=int, choices=(0, 1, 2, 3), default=0,
                     help="number format of the column pass's DFT stages: 0 FP32 (CUDA cores), or on the tensor "
                          "cores 1 TF32 hi+lo, 2 BF16 hi+mid+lo, 3 BF16 hi+lo")
+    ap.add_argument("--tc-rows", action="store_true",
+                    help="with --tc F, the row passes' DFT stages on the tensor cores too (timing-only profiling)")
     ap.add_argument("--persistent", action="store_true",
                     help="the cycle's batch passes as one persistent launch (work list with bounded waits)")
     ap.add_argument("--batch-frames", type=int, default=0,
