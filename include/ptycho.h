@@ -363,8 +363,9 @@ ptx_status ptx_encode_counts8(const uint16_t* src, size_t n, uint8_t* out8, uint
  * then dst[esc_index[k]] = (float)esc_value[k] for k < n_esc (two kernels in
  * stream order), which restores the counts exactly.  dst: device float32 [n]
  * (e.g. a problem's iobs array), src8: device uint8 [n], both 16-byte
- * aligned; esc_index (uint32, indices < n) and esc_value (uint16): device
- * [n_esc], may be null when n_esc = 0.  n = 0 does nothing.
+ * aligned; esc_index (uint32) and esc_value (uint16): device [n_esc], may be
+ * null when n_esc = 0; an escape whose index is not below n is skipped.
+ * n = 0 does nothing.
  * PTX_ERR_INVALID_ARG for a null or misaligned pointer or n >= 2^32. */
 ptx_status ptx_counts8_to_float(float* dst, const uint8_t* src8, size_t n, const uint32_t* esc_index,
                                 const uint16_t* esc_value, size_t n_esc, void* stream);

@@ -1540,7 +1540,7 @@ ptx_status ptx_counts8_to_float(float* dst, const uint8_t* src8, size_t n, const
     k_counts8_to_float<<<4 * 152, 256, 0, s>>>(src8, dst, n);
     if (n_esc > 0) {
         const int blocks = (int)std::min<size_t>((n_esc + 255) / 256, 4 * 152);
-        k_counts8_escapes<<<blocks, 256, 0, s>>>(esc_index, esc_value, dst, n_esc);
+        k_counts8_escapes<<<blocks, 256, 0, s>>>(esc_index, esc_value, dst, n_esc, n);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "ptx_counts8_to_float launch");

@@ -281,12 +281,15 @@ __global__ void k_counts8_to_float(const uint8_t* __restrict__ src, float* __res
     for (size_t i = 16 * n16 + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = (float)src[i];
 }
 
-// The escapes of the one-byte form: dst[index[k]] = value[k].
+// The escapes of the one-byte form: dst[index[k]] = value[k] for the indices
+// inside the n elements of dst (others are skipped).
 __global__ void k_counts8_escapes(const uint32_t* __restrict__ index, const uint16_t* __restrict__ value,
-                                  float* __restrict__ dst, size_t n_esc) {
+                                  float* __restrict__ dst, size_t n_esc, size_t n) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_esc; k += stride)
-        dst[index[k]] = (float)value[k];
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_esc; k += stride) {
+        const uint32_t i = index[k];
+        if (i < n) dst[i] = (float)value[k];
+    }
 }
 
 __global__ void k_set_ctl(Ctl* ctl, double* llk_out, int nprob) {

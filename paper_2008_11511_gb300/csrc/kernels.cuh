@@ -669,7 +669,7 @@ __global__ void k_wait_selftest(int* err_flag, unsigned long long limit_ns);
 __global__ void k_counts_to_float(const uint16_t* __restrict__ src, float* __restrict__ dst, size_t n);
 __global__ void k_counts8_to_float(const uint8_t* __restrict__ src, float* __restrict__ dst, size_t n);
 __global__ void k_counts8_escapes(const uint32_t* __restrict__ index, const uint16_t* __restrict__ value,
-                                  float* __restrict__ dst, size_t n_esc);
+                                  float* __restrict__ dst, size_t n_esc, size_t n);
 __global__ void k_fma_peak(float* __restrict__ sink, int iters, float a, float b);
 __global__ void k_cg_dots(CgArgs c);
 __global__ void k_cg_reduce(CgArgs c);
