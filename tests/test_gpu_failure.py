@@ -147,6 +147,13 @@ def test_counts8_round_trip_is_exact_with_a_ragged_tail():
     dst = torch.full((n,), -1.0, dtype=torch.float32, device="cuda")
     counts8_to_float(dst, torch.from_numpy(out8).cuda(), torch.from_numpy(idx).cuda(), torch.from_numpy(val).cuda())
     assert np.array_equal(dst.cpu().numpy(), c.astype(np.float32))
+    # an escape whose index lies outside the array is skipped
+    guard = torch.full((n + 16,), -1.0, dtype=torch.float32, device="cuda")
+    counts8_to_float(guard[:n], torch.from_numpy(out8).cuda(),
+                     torch.from_numpy(np.append(idx, np.uint32(n))).cuda(),
+                     torch.from_numpy(np.append(val, np.uint16(7))).cuda())
+    g = guard.cpu().numpy()
+    assert np.array_equal(g[:n], c.astype(np.float32)) and np.all(g[n:] == -1.0)
     small = np.minimum(c, 200).astype(np.uint16)
     o8, i8, v8 = encode_counts8(small)
     assert i8.size == 0
