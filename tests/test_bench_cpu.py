@@ -67,3 +67,25 @@ def test_code_hash_ignores_comments_only(bench):
     assert bench._code_only(a) == bench._code_only(b)
     assert bench._code_only(a) != bench._code_only(c)
     assert '"// kept"' in bench._code_only(a)
+
+
+def test_end_to_end_upload_form(bench):
+    """The end-to-end leg's upload form: exact counts with few values >= 255
+    go up in the one-byte form, exact counts with many large values as uint16,
+    anything else as float32; an explicit choice is honoured or refused."""
+    rng = np.random.default_rng(5)
+    low = rng.poisson(3.0, size=(8, 16, 16)).astype(np.float32)
+    low[0, 0, :5] = 300.0                                   # 5 of 2048 escapes
+    high = rng.integers(200, 60000, size=(8, 16, 16)).astype(np.float32)
+    frac = low.copy()
+    frac[1, 2, 3] = 0.5
+    args = lambda d: types.SimpleNamespace(e2e_dtype=d)
+    scan = lambda x: types.SimpleNamespace(iobs=x)
+    assert bench.e2e_form(args("auto"), scan(low)) == "u8"
+    assert bench.e2e_form(args("auto"), scan(high)) == "u16"
+    assert bench.e2e_form(args("auto"), scan(frac)) == "f32"
+    assert bench.e2e_form(args("u16"), scan(low)) == "u16"
+    assert bench.e2e_form(args("u8"), scan(high)) == "u8"
+    assert bench.e2e_form(args("f32"), scan(low)) == "f32"
+    with pytest.raises(SystemExit):
+        bench.e2e_form(args("u8"), scan(frac))
