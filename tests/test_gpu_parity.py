@@ -764,7 +764,9 @@ def test_full_size_dm256_cycle_in_bench_configuration():
     2 % mask — in bench.py's launch configuration (CUDA graph, two batch lanes):
     one DM cycle from an exit-wave stack Psi = P O + 10 % noise (well-conditioned
     in float32), against the FP64 oracle: every frame's Psi', the probe, the
-    object (illuminated region) and the cycle's LLK."""
+    object (illuminated region) and the cycle's LLK.  The same cycle with every
+    DFT stage on the tensor cores in the FP32-accurate splits (TF32 hi + lo,
+    BF16 hi + mid + lo) meets the same tolerance."""
     s = make_config("dm256")
     data = data_of(s)
     rng = np.random.default_rng(30)
@@ -773,12 +775,15 @@ def test_full_size_dm256_cycle_in_bench_configuration():
     psi0 = (phi + scale * (rng.standard_normal(phi.shape) + 1j * rng.standard_normal(phi.shape))).astype(np.complex64)
     del phi
     from paper_2008_11511_gb300 import Ptycho
-    pb = Ptycho(to_dev(s.obj0), to_dev(s.probe0), to_dev(s.iobs), s.positions, s.mask, psi=to_dev(psi0))
-    llk = pb.dm(1).cpu().numpy()
     o, p, psi, l = oracle.dm_cycle(s.obj0, s.probe0, psi0, data)
-    _compare_cycle_state(s, pb, o, p, TOL1, psi_ref=psi)
-    assert abs(llk[0] - l) / abs(l) < TOL1
-    pb.close()
+    for form, rows in ((0, 0), (1, 1), (2, 1)):
+        pb = Ptycho(to_dev(s.obj0), to_dev(s.probe0), to_dev(s.iobs), s.positions, s.mask, psi=to_dev(psi0))
+        pb.set_param("tc", form)
+        pb.set_param("tc_rows", rows)
+        llk = pb.dm(1).cpu().numpy()
+        _compare_cycle_state(s, pb, o, p, TOL1, psi_ref=psi)
+        assert abs(llk[0] - l) / abs(l) < TOL1, (form, llk[0], l)
+        pb.close()
 
 
 
