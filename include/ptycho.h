@@ -240,8 +240,9 @@ ptx_status ptx_accumulators(ptx_handle* h, int32_t p, void** obj_acc, size_t* ob
  * bounded wait (about 2^31 SM clocks) gives up and the next cycle call returns
  * PTX_ERR_TIMEOUT once; for the tests of that failure path); "tc_rows" (0,
  * default; 1: with a tensor-core form, the forward and backward row passes of
- * problems with N = 256 and one mode run their DFT stages on the tensor cores
- * too, so that every DFT stage of the cycle is in that form); "tma" (0, default: the register column pass;
+ * problems with N = 256 and one mode, or N = 512 and any number of modes, run
+ * their DFT stages on the tensor cores too, so that every DFT stage of the
+ * cycle is in that form); "tma" (0, default: the register column pass;
  * 1: the AP / DM column pass of one-mode problems with N = 256 takes its inputs
  * by 2D tensor copies (cp.async.bulk.tensor) in a persistent grid of two CTAs
  * per SM).  "tma_gather" (1, default: the object numerator / denominator of

@@ -866,8 +866,9 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
         const int fwd_mode = (algo == ALGO_DM && !init) ? X_DM : X_PHI;
         const int bwd_mode = (algo == ALGO_DM) ? BWD_DM : BWD_AP;
         // the row passes' DFT stages on the tensor cores (with a tensor-core form,
-        // "tc_rows", 256^2 far-field frames of one mode without a background)
-        const bool tc_rows = form != TC_NONE && h->tc_rows && ph.p.N == 256 && ph.p.K == 1 &&
+        // "tc_rows": 256^2 frames of one mode and 512^2 frames of any number of
+        // modes, far field, without a background)
+        const bool tc_rows = form != TC_NONE && h->tc_rows && ((ph.p.N == 256 && ph.p.K == 1) || ph.p.N == 512) &&
                              ph.p.nearfield <= 0.0 && !ph.p.background;
         bool used[kMaxLanes] = {};
         for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {

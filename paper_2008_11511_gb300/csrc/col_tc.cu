@@ -154,45 +154,14 @@ __global__ void __launch_bounds__(256, 2) k_col_tc(ProbArgs a, int j0, int nb, i
 // thread's own pixels, sum_k |X^_k|^2 kept in registers), then per pixel the
 // common factor and the LLK, then per mode the reload, scale and inverse.
 // ---------------------------------------------------------------------------
-namespace tc {
-template <int F>
-struct Fmt512 {
-    using Base = Fmt<F>;
-    static constexpr int kRow = Base::kRow, kTerms = Base::kTerms;
-    static constexpr size_t kA = (size_t)512 * kRow;                 // one term: 512 rows (stage A) or 2 planes x 256 rows
-    static constexpr size_t kPlaneA = (size_t)256 * kRow;            // one K-plane of stage B's A
-    static constexpr size_t kB16 = (size_t)32 * kRow;                // one term of the 16-point matrix
-    static constexpr size_t kPlaneB = (size_t)64 * kRow;             // one K-plane of the 32-point matrix
-    static constexpr size_t kB32 = 2 * kPlaneB;                      // one term of the 32-point matrix
-    static constexpr size_t kOffA = 0;
-    static constexpr size_t kOffB16 = kOffA + kTerms * kA;           // [dir][term]
-    static constexpr size_t kOffB32 = kOffB16 + 2 * kTerms * kB16;   // [dir][term][plane]
-    static constexpr size_t kOffTw = kOffB32 + 2 * kTerms * kB32;
-    static constexpr size_t kOffBar = kOffTw + sizeof(float2) * 512;
-    static constexpr size_t kOffTmem = kOffBar + 8;
-    static constexpr size_t kBytes = kOffTmem + 8 + 1024;
-    static constexpr uint32_t kIdesc32 = Base::kIdesc;               // N = 32
-    static constexpr uint32_t kIdesc64 = (Base::kIdesc & ~(0x3Fu << 17)) | ((64u >> 3) << 17);
-};
-}  // namespace tc
 
 template <int F>
 __global__ void __launch_bounds__(512, 1) k_col_tc512(ProbArgs a, int j0) {
     using namespace tc;
-    using Fm = Fmt512<F>;
-    constexpr int N = 512, C = 16, kRow = Fm::kRow, kT = Fm::kTerms;
-    constexpr bool kTf = Fmt<F>::kTf32;
-    constexpr int kSteps = Fmt<F>::kSteps;   // k-steps per 32-element K-plane
+    constexpr int N = 512, C = 16;
     extern __shared__ unsigned char smraw[];
-    unsigned char* sm = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    unsigned char* A = sm + Fm::kOffA;
-    unsigned char* B16 = sm + Fm::kOffB16;
-    unsigned char* B32 = sm + Fm::kOffB32;
-    float2* tw = (float2*)(sm + Fm::kOffTw);
-    const uint32_t bar = su32(sm + Fm::kOffBar);
-    uint32_t* tmem_slot = (uint32_t*)(sm + Fm::kOffTmem);
     __shared__ double red_s[16];
-    const int t = threadIdx.x, warp = t >> 5;
+    const int t = threadIdx.x;
     const int x0 = blockIdx.x * C;
     const int b = blockIdx.y;
     const int j = j0 + b;
@@ -200,116 +169,9 @@ __global__ void __launch_bounds__(512, 1) k_col_tc512(ProbArgs a, int j0) {
     const int c1 = t % C, n1 = t / C;            // stage-A vector (column, n1); also (column, kk) at the end
     const int r2 = t & 255, h = t >> 8;          // stage-B row and half
     const int k2 = r2 / C, c2 = r2 % C;
-
-    // twiddles and the DFT matrices (real forms, split into terms); entries in pairs
-    load_twiddles<N>(tw);
-    for (int e = t; e < 2 * 32 * 16; e += 512) {  // 16-point: [inv][row n 0..31][pair kp 0..15]
-        const int inv = e >> 9, n = (e >> 4) & 31, kp = e & 15;
-        float s, co;
-        sincospif((inv ? 2.0f : -2.0f) * (float)(((n >> 1) * kp) & 15) / 16.0f, &s, &co);
-        const Split<F> sp = split2<F>((n & 1) == 0 ? co : s, (n & 1) == 0 ? -s : co);
-        unsigned char* base = B16 + (size_t)(inv * kT) * Fm::kB16;
-        if constexpr (kTf) {
-            *(float2*)(base + sw_off<kRow>(n, 8 * kp)) = make_float2(__uint_as_float(sp.w[0]), __uint_as_float(sp.w[1]));
-            *(float2*)(base + Fm::kB16 + sw_off<kRow>(n, 8 * kp)) =
-                make_float2(__uint_as_float(sp.w[2]), __uint_as_float(sp.w[3]));
-        } else {
-#pragma unroll
-            for (int i = 0; i < kT; ++i) *(uint32_t*)(base + i * Fm::kB16 + sw_off<kRow>(n, 4 * kp)) = sp.w[i];
-        }
-    }
-    for (int e = t; e < 2 * 64 * 32; e += 512) {  // 32-point: [inv][row n 0..63][pair kp 0..31]
-        const int inv = e >> 11, n = (e >> 5) & 63, kp = e & 31;
-        float s, co;
-        sincospif((inv ? 2.0f : -2.0f) * (float)(((n >> 1) * kp) & 31) / 32.0f, &s, &co);
-        const Split<F> sp = split2<F>((n & 1) == 0 ? co : s, (n & 1) == 0 ? -s : co);
-        const int plane = kp >> 4, kq = kp & 15;
-        unsigned char* base = B32 + (size_t)(inv * kT) * Fm::kB32 + (size_t)plane * Fm::kPlaneB;
-        if constexpr (kTf) {
-            *(float2*)(base + sw_off<kRow>(n, 8 * kq)) = make_float2(__uint_as_float(sp.w[0]), __uint_as_float(sp.w[1]));
-            *(float2*)(base + Fm::kB32 + sw_off<kRow>(n, 8 * kq)) =
-                make_float2(__uint_as_float(sp.w[2]), __uint_as_float(sp.w[3]));
-        } else {
-#pragma unroll
-            for (int i = 0; i < kT; ++i) *(uint32_t*)(base + i * Fm::kB32 + sw_off<kRow>(n, 4 * kq)) = sp.w[i];
-        }
-    }
-    if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                     "r"(128u)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tmem_slot;
-    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    const uint32_t dA = tmem + lane_base + (uint32_t)(32 * (t >> 7));                   // stage A: tile t / 128
-    const uint32_t dB = tmem + lane_base + (uint32_t)(64 * (r2 >> 7)) + (uint32_t)(32 * h);  // stage B
-    uint32_t parity = 0;
-
-    // one stage: `big` = stage B (two tiles, N = 64, K in two planes), else stage A
-    // (four tiles, N = 32); dir 0 forward, 1 inverse.  Warp 0 waits for the
-    // commit; the outcome is made block-uniform; a give-up stops the block's MMAs.
-    auto stage = [&](bool big, int dir, float* out) -> bool {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (t == 0) {
-            constexpr int kProd = F == TC_BF16X3 ? 6 : 3;
-            constexpr int pa6[6] = {2, 1, 0, 1, 0, 0}, pb6[6] = {0, 1, 2, 0, 1, 0};
-            constexpr int pa3[3] = {1, 0, 0}, pb3[3] = {0, 1, 0};
-            const int tiles = big ? 2 : 4, planes = big ? 2 : 1;
-            const uint32_t idesc = big ? Fm::kIdesc64 : Fm::kIdesc32;
-            for (int tile = 0; tile < tiles; ++tile) {
-                const uint32_t d = tmem + (uint32_t)((big ? 64 : 32) * tile);
-                bool first = true;
-#pragma unroll
-                for (int p = 0; p < kProd; ++p) {
-                    const int ta = kProd == 6 ? pa6[p] : pa3[p], tb = kProd == 6 ? pb6[p] : pb3[p];
-                    for (int pl = 0; pl < planes; ++pl) {
-                        const uint32_t a0 = su32(A) + (uint32_t)(ta * Fm::kA) +
-                                            (big ? (uint32_t)(pl * Fm::kPlaneA) + tile * 128 * kRow : tile * 128 * kRow);
-                        const uint32_t b0 = big ? su32(B32) + (uint32_t)((dir * kT + tb) * Fm::kB32 + pl * Fm::kPlaneB)
-                                                : su32(B16) + (uint32_t)((dir * kT + tb) * Fm::kB16);
-#pragma unroll
-                        for (int k = 0; k < kSteps; ++k) {
-                            mma<kTf>(d, desc_sw<kTf>(a0 + 32 * k), desc_sw<kTf>(b0 + 32 * k), idesc, first ? 0u : 1u);
-                            first = false;
-                        }
-                    }
-                }
-            }
-            commit(bar);
-        }
-        // warp 0 polls the mbarrier; the other warps wait in the block barrier
-        const bool mine = warp == 0 ? bar_wait(bar, parity) : true;
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        if (__syncthreads_or(!mine)) return false;
-        parity ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        tmem_ld32(big ? dB : dA, out);
-        return true;
-    };
-    // one complex value into element `el` (0..15) of row r of a K-plane base
-    auto put = [&](unsigned char* base, size_t term_stride, int r, int el, float2 v) {
-        const Split<F> sp = split2<F>(v.x, v.y);
-        if constexpr (kTf) {
-            const uint32_t off = sw_off<kRow>(r, 8 * el);
-            *(float2*)(base + off) = make_float2(__uint_as_float(sp.w[0]), __uint_as_float(sp.w[1]));
-            *(float2*)(base + term_stride + off) = make_float2(__uint_as_float(sp.w[2]), __uint_as_float(sp.w[3]));
-        } else {
-            const uint32_t off = sw_off<kRow>(r, 4 * el);
-#pragma unroll
-            for (int s = 0; s < kT; ++s) *(uint32_t*)(base + s * term_stride + off) = sp.w[s];
-        }
-    };
+    Pipe512<F> pp;
+    pp.setup(smraw);
+    const float2* tw = pp.tw;
 
     constexpr float invN2 = 1.0f / float(N * N);
     float2 v[16];
@@ -324,17 +186,17 @@ __global__ void __launch_bounds__(512, 1) k_col_tc512(ProbArgs a, int j0) {
 #pragma unroll
         for (int n2 = 0; n2 < 16; ++n2) v[n2] = ld_hint(spec + (size_t)(n1 + 32 * n2) * N + c1, policy_evict_last());
 #pragma unroll
-        for (int i = 0; i < 16; ++i) put(A, Fm::kA, t, i, v[i]);  // stage-A row t
-        good = stage(false, 0, o);
+        for (int i = 0; i < 16; ++i) pp.put(0, t, i, v[i]);  // stage-A row t
+        good = pp.stage(false, 0, o);
         if (!good) break;
         // twiddle w^(n1 k2) and the transpose into the stage-B rows (k2, c)
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
             const float2 y = make_float2(o[2 * kk], o[2 * kk + 1]);
             const float2 yt = kk == 0 ? y : cmul(y, tw_get<N, -1>(tw, kk, n1));
-            put(A + (size_t)(n1 >> 4) * Fm::kPlaneA, Fm::kA, kk * C + c1, n1 & 15, yt);
+            pp.put(n1 >> 4, kk * C + c1, n1 & 15, yt);
         }
-        good = stage(true, 0, o);
+        good = pp.stage(true, 0, o);
         if (!good) break;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
@@ -368,17 +230,17 @@ __global__ void __launch_bounds__(512, 1) k_col_tc512(ProbArgs a, int j0) {
         }
         // stage-B row r2, half h: elements k1 = 16 h + i
 #pragma unroll
-        for (int i = 0; i < 16; ++i) put(A + (size_t)h * Fm::kPlaneA, Fm::kA, r2, i, cscale(v[i], ic[i]));
-        good = stage(true, 1, o);
+        for (int i = 0; i < 16; ++i) pp.put(h, r2, i, cscale(v[i], ic[i]));
+        good = pp.stage(true, 1, o);
         if (!good) break;
         // twiddle w^(+k2 kk), kk = 16 h + i, and the transpose into the stage-A rows (kk, c)
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const int kk = 16 * h + i;
             const float2 y = make_float2(o[2 * i], o[2 * i + 1]);
-            put(A, Fm::kA, kk * C + c2, k2, (k2 == 0 || kk == 0) ? y : cmul(y, tw_get<N, +1>(tw, k2, kk)));
+            pp.put(0, kk * C + c2, k2, (k2 == 0 || kk == 0) ? y : cmul(y, tw_get<N, +1>(tw, k2, kk)));
         }
-        good = stage(false, 1, o);
+        good = pp.stage(false, 1, o);
         if (!good) break;
         // rows kk + 32 k1' of column c (thread = stage-A row t = (c1, kk = n1))
         const uint64_t el = policy_evict_last();
@@ -387,19 +249,8 @@ __global__ void __launch_bounds__(512, 1) k_col_tc512(ProbArgs a, int j0) {
             st_hint(spec + (size_t)(n1 + 32 * i) * N + c1, make_float2(o[2 * i], o[2 * i + 1]), el);
     }
     const double tot = block_sum_double<512>(llk.value(), red_s);
-    if (t == 0) {
-        a.llk_part[(size_t)j * gridDim.x + blockIdx.x] = tot;
-        if (!good) {
-            bar_wait(bar, parity);
-            if (a.err_flag) {
-                *(volatile int*)a.err_flag = 1;
-                __threadfence_system();
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+    if (t == 0) a.llk_part[(size_t)j * gridDim.x + blockIdx.x] = tot;
+    pp.finish(good, a.err_flag);
 }
 
 void launch_col_tc(const ProbArgs& a, int j0, int nb, int form, int selftest, cudaStream_t s) {

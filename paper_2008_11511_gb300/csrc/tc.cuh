@@ -363,5 +363,186 @@ struct Pipe256 {
     }
 };
 
+template <int F>
+struct Fmt512 {
+    using Base = Fmt<F>;
+    static constexpr int kRow = Base::kRow, kTerms = Base::kTerms;
+    static constexpr size_t kA = (size_t)512 * kRow;                 // one term: 512 rows (stage A) or 2 planes x 256 rows
+    static constexpr size_t kPlaneA = (size_t)256 * kRow;            // one K-plane of stage B's A
+    static constexpr size_t kB16 = (size_t)32 * kRow;                // one term of the 16-point matrix
+    static constexpr size_t kPlaneB = (size_t)64 * kRow;             // one K-plane of the 32-point matrix
+    static constexpr size_t kB32 = 2 * kPlaneB;                      // one term of the 32-point matrix
+    static constexpr size_t kOffA = 0;
+    static constexpr size_t kOffB16 = kOffA + kTerms * kA;           // [dir][term]
+    static constexpr size_t kOffB32 = kOffB16 + 2 * kTerms * kB16;   // [dir][term][plane]
+    static constexpr size_t kOffTw = kOffB32 + 2 * kTerms * kB32;
+    static constexpr size_t kOffBar = kOffTw + sizeof(float2) * 512;
+    static constexpr size_t kOffTmem = kOffBar + 8;
+    static constexpr size_t kBytes = kOffTmem + 8 + 1024;
+    static constexpr uint32_t kIdesc32 = Base::kIdesc;               // N = 32
+    static constexpr uint32_t kIdesc64 = (Base::kIdesc & ~(0x3Fu << 17)) | ((64u >> 3) << 17);
+};
+
+// The 512-point transforms (512 = 16 x 32: x[n1 + 32 n2], X[k2 + 16 k1]) run by
+// a 512-thread block: stage A (16-point DFT over n2) is D[512 x 32] = A[512 x
+// 32] B16^T in four 128-row tiles, stage B (32-point DFT over n1) is D[256 x
+// 64] = A[256 x 64] B32^T in two 128-row tiles with K = 64 stored as two
+// 32-element K-planes.  Thread t owns stage-A row t and reads row t of D;
+// in stage B it reads half h = t / 256 (outputs 16 h .. 16 h + 15) of row
+// t % 256.  One thread issues, warp 0 waits (bounded), the outcome is
+// block-uniform.  setup(), stage() and finish() are block-wide.
+template <int F>
+struct Pipe512 {
+    using Fm = Fmt512<F>;
+    static constexpr int kRow = Fm::kRow, kT = Fm::kTerms;
+    static constexpr bool kTf = Fmt<F>::kTf32;
+    static constexpr int kSteps = Fmt<F>::kSteps;  // k-steps per 32-element K-plane
+    unsigned char* A;  // the operand buffer (1024-byte aligned base of the dynamic shared memory)
+    float2* tw;        // the 512-point twiddle table
+    uint32_t bar, tmem, parity;
+
+    __device__ __forceinline__ void setup(unsigned char* smraw) {
+        A = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+        unsigned char* B16 = A + Fm::kOffB16;
+        unsigned char* B32 = A + Fm::kOffB32;
+        tw = (float2*)(A + Fm::kOffTw);
+        bar = su32(A + Fm::kOffBar);
+        uint32_t* tmem_slot = (uint32_t*)(A + Fm::kOffTmem);
+        const int t = threadIdx.x, warp = t >> 5;
+        load_twiddles<512>(tw);
+        for (int e = t; e < 2 * 32 * 16; e += 512) {  // 16-point: [inv][row n 0..31][pair kp 0..15]
+            const int inv = e >> 9, n = (e >> 4) & 31, kp = e & 15;
+            float s, co;
+            sincospif((inv ? 2.0f : -2.0f) * (float)(((n >> 1) * kp) & 15) / 16.0f, &s, &co);
+            const Split<F> sp = split2<F>((n & 1) == 0 ? co : s, (n & 1) == 0 ? -s : co);
+            unsigned char* base = B16 + (size_t)(inv * kT) * Fm::kB16;
+            if constexpr (kTf) {
+                *(float2*)(base + sw_off<kRow>(n, 8 * kp)) =
+                    make_float2(__uint_as_float(sp.w[0]), __uint_as_float(sp.w[1]));
+                *(float2*)(base + Fm::kB16 + sw_off<kRow>(n, 8 * kp)) =
+                    make_float2(__uint_as_float(sp.w[2]), __uint_as_float(sp.w[3]));
+            } else {
+#pragma unroll
+                for (int i = 0; i < kT; ++i) *(uint32_t*)(base + i * Fm::kB16 + sw_off<kRow>(n, 4 * kp)) = sp.w[i];
+            }
+        }
+        for (int e = t; e < 2 * 64 * 32; e += 512) {  // 32-point: [inv][row n 0..63][pair kp 0..31]
+            const int inv = e >> 11, n = (e >> 5) & 63, kp = e & 31;
+            float s, co;
+            sincospif((inv ? 2.0f : -2.0f) * (float)(((n >> 1) * kp) & 31) / 32.0f, &s, &co);
+            const Split<F> sp = split2<F>((n & 1) == 0 ? co : s, (n & 1) == 0 ? -s : co);
+            const int plane = kp >> 4, kq = kp & 15;
+            unsigned char* base = B32 + (size_t)(inv * kT) * Fm::kB32 + (size_t)plane * Fm::kPlaneB;
+            if constexpr (kTf) {
+                *(float2*)(base + sw_off<kRow>(n, 8 * kq)) =
+                    make_float2(__uint_as_float(sp.w[0]), __uint_as_float(sp.w[1]));
+                *(float2*)(base + Fm::kB32 + sw_off<kRow>(n, 8 * kq)) =
+                    make_float2(__uint_as_float(sp.w[2]), __uint_as_float(sp.w[3]));
+            } else {
+#pragma unroll
+                for (int i = 0; i < kT; ++i) *(uint32_t*)(base + i * Fm::kB32 + sw_off<kRow>(n, 4 * kq)) = sp.w[i];
+            }
+        }
+        if (t == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        if (warp == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                         "r"(128u)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tmem = *tmem_slot;
+        parity = 0;
+    }
+
+    // One stage: `big` = stage B (two tiles, N = 64, K in two planes), else
+    // stage A (four tiles, N = 32); dir 0 forward, 1 inverse.
+    __device__ __forceinline__ bool stage(bool big, int dir, float* out) {
+        const int t = threadIdx.x, warp = t >> 5;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (t == 0) {
+            constexpr int kProd = F == TC_BF16X3 ? 6 : 3;
+            constexpr int pa6[6] = {2, 1, 0, 1, 0, 0}, pb6[6] = {0, 1, 2, 0, 1, 0};
+            constexpr int pa3[3] = {1, 0, 0}, pb3[3] = {0, 1, 0};
+            const int tiles = big ? 2 : 4, planes = big ? 2 : 1;
+            const uint32_t idesc = big ? Fm::kIdesc64 : Fm::kIdesc32;
+            const uint32_t sa = su32(A), s16 = su32(A + Fm::kOffB16), s32 = su32(A + Fm::kOffB32);
+            for (int tile = 0; tile < tiles; ++tile) {
+                const uint32_t d = tmem + (uint32_t)((big ? 64 : 32) * tile);
+                bool first = true;
+#pragma unroll
+                for (int p = 0; p < kProd; ++p) {
+                    const int ta = kProd == 6 ? pa6[p] : pa3[p], tb = kProd == 6 ? pb6[p] : pb3[p];
+                    for (int pl = 0; pl < planes; ++pl) {
+                        const uint32_t a0 = sa + (uint32_t)(ta * Fm::kA) +
+                                            (big ? (uint32_t)(pl * Fm::kPlaneA) + tile * 128 * kRow : tile * 128 * kRow);
+                        const uint32_t b0 = big ? s32 + (uint32_t)((dir * kT + tb) * Fm::kB32 + pl * Fm::kPlaneB)
+                                                : s16 + (uint32_t)((dir * kT + tb) * Fm::kB16);
+#pragma unroll
+                        for (int k = 0; k < kSteps; ++k) {
+                            mma<kTf>(d, desc_sw<kTf>(a0 + 32 * k), desc_sw<kTf>(b0 + 32 * k), idesc, first ? 0u : 1u);
+                            first = false;
+                        }
+                    }
+                }
+            }
+            commit(bar);
+        }
+        // warp 0 polls the mbarrier; the other warps wait in the block barrier
+        const bool mine = warp == 0 ? bar_wait(bar, parity) : true;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (__syncthreads_or(!mine)) return false;
+        parity ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        const int r2 = t & 255, h = t >> 8;
+        tmem_ld32(big ? tmem + lane_base + (uint32_t)(64 * (r2 >> 7)) + (uint32_t)(32 * h)
+                      : tmem + lane_base + (uint32_t)(32 * (t >> 7)),
+                  out);
+        return true;
+    }
+
+    // One complex value into element `el` (0..15) of row r of the K-plane at
+    // `plane` (stage A: plane 0, rows 0..511; stage B: planes 0 and 1, rows 0..255).
+    __device__ __forceinline__ void put(int plane, int r, int el, float2 v) {
+        unsigned char* base = A + (size_t)plane * Fm::kPlaneA;
+        const Split<F> sp = split2<F>(v.x, v.y);
+        if constexpr (kTf) {
+            const uint32_t off = sw_off<kRow>(r, 8 * el);
+            *(float2*)(base + off) = make_float2(__uint_as_float(sp.w[0]), __uint_as_float(sp.w[1]));
+            *(float2*)(base + Fm::kA + off) = make_float2(__uint_as_float(sp.w[2]), __uint_as_float(sp.w[3]));
+        } else {
+            const uint32_t off = sw_off<kRow>(r, 4 * el);
+#pragma unroll
+            for (int s = 0; s < kT; ++s) *(uint32_t*)(base + s * Fm::kA + off) = sp.w[s];
+        }
+    }
+
+    // Block-wide end: after a give-up, thread 0 waits once more (bounded) for
+    // the MMAs in flight and sets the error flag; then TMEM is freed.
+    __device__ __forceinline__ void finish(bool good, int* err_flag) {
+        if (threadIdx.x == 0 && !good) {
+            bar_wait(bar, parity);
+            if (err_flag) {
+                *(volatile int*)err_flag = 1;
+                __threadfence_system();
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if ((threadIdx.x >> 5) == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u) : "memory");
+    }
+};
+
 }  // namespace tc
 }  // namespace ptx

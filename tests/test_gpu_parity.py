@@ -692,13 +692,15 @@ def test_dm256_all_dft_stages_on_tensor_cores(form, lanes, batch):
     pb.close()
 
 
+@pytest.mark.parametrize("rows", [0, 1], ids=["column_pass", "every_stage"])
 @pytest.mark.parametrize("K", [1, 3])
-def test_modes512_split_precision_forms(K):
+def test_modes512_split_precision_forms(K, rows):
     """The 512^2 column pass with its DFT stages on the tensor cores (a 16-point
-    and a 32-point stage, the modes in two sweeps with the common factor), each
-    number format against the FP64 oracle over one DM cycle and one AP cycle:
-    TF32 hi + lo and BF16 hi + mid + lo at the single-cycle tolerance, BF16 hi +
-    lo within its own bound.  The distances are printed."""
+    and a 32-point stage, the modes in two sweeps with the common factor), and
+    with "tc_rows" the forward and backward row passes too (every DFT stage of
+    the cycle), each number format against the FP64 oracle over one DM cycle
+    and one AP cycle: TF32 hi + lo and BF16 hi + mid + lo at the single-cycle
+    tolerance, BF16 hi + lo within its own bound.  The distances are printed."""
     from paper_2008_11511_gb300 import _lib
     s = make_scan(f"tc512_{K}", N=512, J=6, Ho=700, Wo=640, K=K, seed=90 + K, photons=1e7, step=51.2,
                   probe="hg", probe_radius=51.2, mode_powers=[0.7, 0.2, 0.1][:K], mask_fraction=0.02)
@@ -713,6 +715,7 @@ def test_modes512_split_precision_forms(K):
         out = torch.empty(1, dtype=torch.float64, device="cuda")
         stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
         pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+        pb.set_param("tc_rows", rows)
         f = _lib.PTX_UPDATE_OBJ | _lib.PTX_UPDATE_PROBE | flag
         _lib.call("ptx_dm_cycles", pb._handle(), 1, f | _lib.PTX_DM_INIT_PSI, ctypes.c_void_p(out.data_ptr()), stream)
         ill = illuminated(s, p)
@@ -720,12 +723,13 @@ def test_modes512_split_precision_forms(K):
                 rel(pb.psi.cpu().numpy(), psi), abs(float(out.cpu()[0]) - llk_ref[0]) / abs(llk_ref[0]))
         pb.close()
         pb = gpu_problem(s, with_psi=True, obj=o0, probe=p0)
+        pb.set_param("tc_rows", rows)
         _lib.call("ptx_ap_cycles", pb._handle(), 1, f, ctypes.c_void_p(out.data_ptr()), stream)
         e_ap = (rel(pb.obj.cpu().numpy()[ill], oa[ill]), rel(pb.probe.cpu().numpy(), pa_),
                 abs(float(out.cpu()[0]) - la) / abs(la))
         pb.close()
         errs[name] = e_dm + e_ap
-        print(f"512^2 K={K} form {name}: DM obj {e_dm[0]:.2e} probe {e_dm[1]:.2e} psi {e_dm[2]:.2e} "
+        print(f"512^2 K={K} rows={rows} form {name}: DM obj {e_dm[0]:.2e} probe {e_dm[1]:.2e} psi {e_dm[2]:.2e} "
               f"llk {e_dm[3]:.2e}; AP obj {e_ap[0]:.2e} probe {e_ap[1]:.2e} llk {e_ap[2]:.2e}")
     for name in ("fp32", "tf32x2", "bf16x3"):
         assert max(errs[name]) < 2 * TOL1, (name, errs[name])
