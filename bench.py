@@ -455,13 +455,16 @@ def run_extra_modes(dev, pk, ws, J=1500, H=2800):
     ms = _events_ms(lambda: pb.dm(3, llk=llk), 3, stream) / 3
     # the same cycle with the column pass's DFT stages on the tensor cores
     forms = []
-    for tc in (1, 2, 3):
+    for tc, rows in ((1, 0), (2, 0), (3, 0), (1, 1), (2, 1), (3, 1)):
         pb.set_param("tc", tc)
+        pb.set_param("tc_rows", rows)
         pb.dm(1, llk=llk)
         torch.cuda.synchronize(dev)
         ms_f = _events_ms(lambda: pb.dm(3, llk=llk), 2, stream) / 3
-        forms.append({"form": FORMS[tc], "ms_per_cycle": ms_f, "frames_per_s": s.J * ws / (ms_f * 1e-3)})
+        forms.append({"form": FORMS_ALL[tc] if rows else FORMS[tc], "ms_per_cycle": ms_f,
+                      "frames_per_s": s.J * ws / (ms_f * 1e-3)})
     pb.set_param("tc", 0)
+    pb.set_param("tc_rows", 0)
     pb.close()
     px = s.N * s.N
     b = s.J * s.K * px * 16 + s.J * px * 4 + s.Ho * s.Wo * 16 + s.K * px * 16
