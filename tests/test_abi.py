@@ -230,3 +230,16 @@ def test_accumulate_shifts_matches_the_oracle(lib):
         assert moved.value == int(np.any(ipos != before, axis=1).sum())
     assert lib.ptx_accumulate_shifts(-1, None, ctypes.c_double(1.0), ctypes.c_double(1.0), 1, 1, None, None,
                                      ctypes.byref(moved)) == 1
+
+
+def test_every_parameter_name_is_documented_and_checked(lib):
+    """Every name ptx_set_param accepts is documented in include/ptycho.h, and
+    a call without a handle is refused on the host."""
+    from paper_2008_11511_gb300._lib import STATUS_NAMES
+    api = open(os.path.join(ROOT, "paper_2008_11511_gb300", "csrc", "api.cu")).read()
+    names = re.findall(r'strcmp\(name, "([a-z_0-9]+)"\)', api)
+    header = open(HEADER).read()
+    assert len(names) >= 12
+    missing = [n for n in names if f'"{n}"' not in header]
+    assert not missing, missing
+    assert STATUS_NAMES[lib.ptx_set_param(None, b"lanes", ctypes.c_double(2.0))] == "PTX_ERR_INVALID_ARG"
