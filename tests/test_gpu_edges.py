@@ -155,3 +155,26 @@ def test_zero_cycles_do_nothing():
         assert torch.equal(t, b)
     assert buf.cpu().tolist() == [7.0, 7.0]
     pb.close()
+
+
+def test_set_param_refuses_bad_names_and_values_and_keeps_the_handle():
+    """ptx_set_param on a live handle: unknown names and values outside each
+    parameter's range come back as PTX_ERR_INVALID_ARG, change nothing, and the
+    handle then runs a cycle that matches the oracle."""
+    from paper_2008_11511_gb300 import PtychoError
+    s = make_config("ap64", J=10)
+    data, o0, p0 = _warm(s)
+    pb = _problem(s, o0, p0)
+    bad = [("no_such_parameter", 1.0), ("lanes", 0.0), ("lanes", 5.0), ("lanes", 1.5), ("tc", 4.0),
+           ("tc_rows", 2.0), ("persistent", 0.5), ("tma", 2.0), ("batch_frames", 1.5), ("bwd_slots", 5000.0),
+           ("alpha_obj", -1.0), ("alpha_probe", float("nan")), ("tc_selftest", 3.0)]
+    for name, value in bad:
+        with pytest.raises(PtychoError) as ei:
+            pb.set_param(name, value)
+        assert ei.value.status_name == "PTX_ERR_INVALID_ARG", (name, value)
+    for name, value in [("lanes", 3.0), ("lanes", 2.0), ("tc", 0.0), ("tc_rows", 0.0), ("batch_frames", 0.0)]:
+        pb.set_param(name, value)
+    pb.ap(1)
+    o, p, _ = oracle.ap_cycle(o0, p0, data)
+    _check(s, pb, o, p, TOL1)
+    pb.close()
