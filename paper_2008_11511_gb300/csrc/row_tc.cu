@@ -1,11 +1,12 @@
-// Forward and backward row passes of the cycle with the two 16-point DFT
-// stages of each 256-point row transform on the tensor cores (the
-// split-precision form of the paper's FT / IFT operators on the rows; 256^2
-// frames, one probe mode).  Same inputs, outputs and work-stack layout as the
-// register passes k_row_fwd_r<256> and k_row_bwd_r<256, 1>, so either can run
-// beside the FP32 or the tensor-core column pass.
+// Forward and backward row passes of the cycle with the DFT stages of each
+// row transform on the tensor cores (the split-precision form of the paper's
+// FT / IFT operators on the rows): 256^2 frames with one probe mode (two
+// 16-point stages) and 512^2 frames with any number of modes (a 16-point and a
+// 32-point stage, at the end of this file).  Same inputs, outputs and
+// work-stack layout as the register row passes, so either can run beside the
+// FP32 or the tensor-core column pass.
 //
-// A block holds a band of 16 rows as two independent halves of 8 rows
+// At 256^2 a block holds a band of 16 rows as two independent halves of 8 rows
 // (tc::Pipe256: own A tile, mbarrier, TMEM columns and named barrier).  Thread
 // u of half h is (row 8 h + u / 16 of the band, index q = u % 16) and owns row
 // u of its half's tile in every stage; the stage-2 vectors of a row are the 16
