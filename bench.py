@@ -554,6 +554,8 @@ def run_ours(args):
         params.append(("tc", args.tc))
     if args.tc_rows:
         params.append(("tc_rows", 1))
+    if args.pdl is not None:
+        params.append(("pdl", args.pdl))
     for name, val in params:
         pb.set_param(name, val)
     stream = torch.cuda.current_stream(dev)
@@ -766,6 +768,8 @@ def main():
                     help="column pass staged by tensor copies (1) or the register column pass (0, the library default)")
     ap.add_argument("--tma-gather", type=int, choices=(0, 1), default=None,
                     help="object gather fed by tensor copies (1, the library default) or the plain gather (0)")
+    ap.add_argument("--pdl", type=int, choices=(0, 1), default=None,
+                    help="batch passes launched as programmatic dependents (1, the library default) or plainly (0)")
     ap.add_argument("--tc", type=int, choices=(0, 1, 2, 3), default=0,
                     help="number format of the column pass's DFT stages: 0 FP32 (CUDA cores), or on the tensor "
                          "cores 1 TF32 hi+lo, 2 BF16 hi+mid+lo, 3 BF16 hi+lo")

@@ -461,6 +461,7 @@ struct ptx_handle {
     int pers_selftest = 0;   // ptx_set_param "persistent_selftest": a dependency that is never met
     int tc_selftest = 0;     // ptx_set_param "tc_selftest": a tensor-core stage whose commit never comes
     int tc_rows = 0;         // ptx_set_param "tc_rows": the row passes' DFT stages on the tensor cores too
+    int pdl = 1;             // ptx_set_param "pdl": batch passes launched as programmatic dependents
     int pers_nitems = 0, pers_nseg = 0, pers_nbatch = 0;
     std::vector<ProbArgs> pers_prob;
     std::vector<PSeg> pers_seg;
@@ -871,11 +872,19 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
         const bool tc_rows = form != TC_NONE && h->tc_rows && ((ph.p.N == 256 && ph.p.K == 1) || ph.p.N == 512) &&
                              ph.p.nearfield <= 0.0 && !ph.p.background;
         bool used[kMaxLanes] = {};
+        // programmatic dependent launches: the three register passes of a far-field
+        // problem with one mode and no background, each after another of them on
+        // the same lane (the first forward pass of a lane follows event waits or
+        // the previous problem's kernels and is launched plainly); not while
+        // profiling, whose events sit between the launches
+        const bool pdl = h->pdl && !h->profiling && !tc_rows && form == TC_NONE && ph.p.nearfield <= 0.0 &&
+                         ph.p.K == 1 && !ph.p.background && use_reg_kernels(ks, ph.p.K);
         for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
             const int nb = std::min(ph.B, ph.p.J - j0);
             const int G = std::min(ph.G3, nb);
             const int lane = next_lane;
             next_lane = (next_lane + 1) % lanes;
+            const bool pdl_fwd = pdl && used[lane];
             used[lane] = true;
             cudaStream_t ls = lanes == 1 ? s : h->lane_stream[lane];
             ProbArgs al = a;
@@ -886,8 +895,9 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
                 if (tc_rows)
                     launch_row_fwd_tc(al, j0, nb, fwd_mode == X_DM, form, ls);
                 else
-                    ks->row_fwd(al, j0, nb, fwd_mode, ls);
+                    ks->row_fwd(al, j0, nb, fwd_mode, ls, pdl_fwd);
             }
+            bool col_plain = true;  // the column pass is the register kernel (not the tensor-copy one)
             if (ph.p.nearfield > 0.0) {
                 // propagate, project at the detector, propagate back
                 {
@@ -910,17 +920,19 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
                 CUtensorMap tm_spec;
                 const int grid = (h->tma && ph.tma_io && ks->col_tma && !ph.p.background) ? ks->col_tma_grid() : 0;
                 if (grid > 0 && encode_2d(&tm_spec, 8, al.spec, ph.p.N, (uint64_t)ph.B * ph.p.N,
-                                          (uint32_t)ks->reg_lines, (uint32_t)ph.p.N))
+                                          (uint32_t)ks->reg_lines, (uint32_t)ph.p.N)) {
                     ks->col_tma(&tm_spec, &ph.tm_io, &ph.tm_mask, al, j0, nb, grid, ls);
-                else
-                    ks->col(al, j0, nb, COL_PROJECT, ls);
+                    col_plain = false;
+                } else {
+                    ks->col(al, j0, nb, COL_PROJECT, ls, pdl);
+                }
             }
             {
                 ProfScope ps(h, PTX_KERNEL_ROW_BWD, ls);
                 if (tc_rows)
                     launch_row_bwd_tc(al, j0, nb, G, upd_p ? 1 : 0, form, ls);
                 else
-                    ks->row_bwd(al, j0, nb, G, bwd_mode, 0, upd_p, ls);
+                    ks->row_bwd(al, j0, nb, G, bwd_mode, 0, upd_p, ls, pdl && col_plain);
             }
         }
         if (lanes > 1)
@@ -1228,12 +1240,12 @@ ptx_status ptx_llk(ptx_handle* h, double* llk_dev, void* stream) {
         ProbHost& ph = h->probs[pi];
         for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
             const int nb = std::min(ph.B, ph.p.J - j0);
-            ph.ks->row_fwd(ph.args, j0, nb, X_PHI, s);
+            ph.ks->row_fwd(ph.args, j0, nb, X_PHI, s, false);
             if (ph.p.nearfield > 0.0) {
                 ph.ks->col_nf(ph.args, nb, +1, s);
                 ph.ks->row_proj(ph.args, j0, nb, 1, s);
             } else {
-                ph.ks->col(ph.args, j0, nb, COL_LLK, s);
+                ph.ks->col(ph.args, j0, nb, COL_LLK, s, false);
             }
         }
         k_llk_reduce<<<1, 1024, 0, s>>>(ph.args, ph.p.N / ph.C2, llk_dev + pi);
@@ -1261,10 +1273,11 @@ ptx_status ptx_ml_grad(ptx_handle* h, void* grad_obj, void* grad_probe, double* 
     if (e != cudaSuccess) return cuda_fail(e, "ptx_ml_grad memset");
     for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
         const int nb = std::min(ph.B, ph.p.J - j0);
-        ph.ks->row_fwd(a, j0, nb, X_PHI, s);
-        ph.ks->col(a, j0, nb, COL_GRAD, s);
+        ph.ks->row_fwd(a, j0, nb, X_PHI, s, false);
+        ph.ks->col(a, j0, nb, COL_GRAD, s, false);
         if (grad_obj || grad_probe)
-            ph.ks->row_bwd(a, j0, nb, std::min(ph.G3, nb), BWD_GRAD, grad_obj != nullptr, grad_probe != nullptr, s);
+            ph.ks->row_bwd(a, j0, nb, std::min(ph.G3, nb), BWD_GRAD, grad_obj != nullptr, grad_probe != nullptr, s,
+                            false);
     }
     if (llk_dev) k_llk_reduce<<<1, 1024, 0, s>>>(a, a.N / a.C2, llk_dev);
     e = cudaGetLastError();
@@ -1330,10 +1343,10 @@ ptx_status enqueue_grad(ptx_handle* h, ProbHost& ph, float2* g_obj, float2* g_pr
     set_batch(ph, h->spec_bytes, 1, h->batch_cap, h->bwd_slots);
     for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
         const int nb = std::min(ph.B, ph.p.J - j0);
-        ph.ks->row_fwd(a, j0, nb, X_PHI, s);
-        ph.ks->col(a, j0, nb, COL_GRAD, s);
+        ph.ks->row_fwd(a, j0, nb, X_PHI, s, false);
+        ph.ks->col(a, j0, nb, COL_GRAD, s, false);
         if (g_obj || g_probe)
-            ph.ks->row_bwd(a, j0, nb, std::min(ph.G3, nb), BWD_GRAD, g_obj != nullptr, g_probe != nullptr, s);
+            ph.ks->row_bwd(a, j0, nb, std::min(ph.G3, nb), BWD_GRAD, g_obj != nullptr, g_probe != nullptr, s, false);
     }
     if (llk_out) k_llk_reduce<<<1, 1024, 0, s>>>(a, a.N / a.C2, llk_out);
     e = cudaGetLastError();
@@ -1467,6 +1480,9 @@ ptx_status ptx_set_param(ptx_handle* h, const char* name, double value) {
     } else if (!strcmp(name, "tc_selftest")) {
         if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "tc_selftest must be 0 or 1");
         h->tc_selftest = (int)value;
+    } else if (!strcmp(name, "pdl")) {
+        if (value != 0.0 && value != 1.0) return fail(PTX_ERR_INVALID_ARG, "pdl must be 0 or 1");
+        h->pdl = (int)value;
     } else if (!strcmp(name, "batch_frames")) {
         if (value != (int)value || value > 32768)
             return fail(PTX_ERR_INVALID_ARG, "batch_frames must be an integer in 0..32768");

@@ -82,6 +82,15 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialisation attribute may start while the previous kernel of its
+// stream runs; it signals its own dependents early (launch_dependents) and
+// waits for the previous kernel's completion and memory (wait) before its
+// first access to what that kernel writes or reads.  Both are no-ops in a
+// kernel launched without the attribute.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ float2 ld_hint(const float2* ptr, uint64_t pol) {
     float2 v;
     asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(ptr), "l"(pol));
@@ -721,9 +730,13 @@ __global__ void __launch_bounds__(kThreads) k_fft_cols(float2* data, int C) {
 // sizes 8, 12 and 16.
 struct KernelSet {
     int N;
-    void (*row_fwd)(const ProbArgs&, int j0, int nb, int mode, cudaStream_t);
-    void (*col)(const ProbArgs&, int j0, int nb, int mode, cudaStream_t);
-    void (*row_bwd)(const ProbArgs&, int j0, int nb, int G, int mode, int upd_obj, int upd_probe, cudaStream_t);
+    // pdl: launch as a programmatic dependent of the previous kernel of the
+    // stream (register kernels only, whose bodies wait for it before touching
+    // the work stack); the caller sets it only where that kernel is a batch pass
+    void (*row_fwd)(const ProbArgs&, int j0, int nb, int mode, cudaStream_t, bool pdl);
+    void (*col)(const ProbArgs&, int j0, int nb, int mode, cudaStream_t, bool pdl);
+    void (*row_bwd)(const ProbArgs&, int j0, int nb, int G, int mode, int upd_obj, int upd_probe, cudaStream_t,
+                    bool pdl);
     void (*fft2)(float2* data, int nframes, int dir, cudaStream_t);
     void (*row_fwd_ls)(const ProbArgs&, int j0, int nb, int unused, cudaStream_t);
     void (*col_ls)(const ProbArgs&, int j0, int nb, int unused, cudaStream_t);
@@ -768,21 +781,42 @@ template <int N>
 constexpr bool has_reg() { return Plan<N>::M > 1; }
 
 
+// Launch k with kThreads threads, as a programmatic dependent of the previous
+// kernel of the stream when pdl is set.
+template <typename... KArgs, typename... Args>
+void launch_dep(void (*k)(KArgs...), dim3 grid, size_t smem, cudaStream_t s, bool pdl, Args... args) {
+    if (!pdl) {
+        k<<<grid, kThreads, smem, s>>>(args...);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <int N>
-void launch_row_fwd(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s) {
+void launch_row_fwd(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s, bool pdl) {
     if constexpr (has_reg<N>()) {
         dim3 grid(N / RegShape<N>::L, nb * a.K);
         if (mode == X_DM)
-            k_row_fwd_r<N, true><<<grid, kThreads, smem_row_fwd_r<N>(), s>>>(a, j0);
+            launch_dep(k_row_fwd_r<N, true>, grid, smem_row_fwd_r<N>(), s, pdl, a, j0);
         else
-            k_row_fwd_r<N, false><<<grid, kThreads, smem_row_fwd_r<N>(), s>>>(a, j0);
+            launch_dep(k_row_fwd_r<N, false>, grid, smem_row_fwd_r<N>(), s, pdl, a, j0);
         return;
     }
     dim3 grid(N / a.L1, nb);
     k_row_fwd<N><<<grid, kThreads, smem_row_fwd_t<N>(a.K, a.L1), s>>>(a, j0, mode);
 }
 template <int N>
-void launch_col(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s) {
+void launch_col(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s, bool pdl) {
     if constexpr (has_reg<N>()) {
         dim3 grid(N / RegShape<N>::C, nb);
         if (a.K > 1) {
@@ -795,24 +829,26 @@ void launch_col(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s) {
         else if (a.bg)
             k_col_r<N, true, false><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, mode);
         else if (mode == COL_PROJECT)
-            k_col_r<N, false, true><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, mode);
+            launch_dep(k_col_r<N, false, true>, grid, smem_col_r<N>(), s, pdl, a, j0, mode);
         else
-            k_col_r<N, false, false><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, mode);
+            launch_dep(k_col_r<N, false, false>, grid, smem_col_r<N>(), s, pdl, a, j0, mode);
         return;
     }
     dim3 grid(N / a.C2, nb);
     k_col<N><<<grid, kThreads, smem_col_t<N>(a.K, a.C2), s>>>(a, j0, mode);
 }
 template <int N>
-void launch_row_bwd(const ProbArgs& a, int j0, int nb, int G, int mode, int upd_obj, int upd_probe, cudaStream_t s) {
+void launch_row_bwd(const ProbArgs& a, int j0, int nb, int G, int mode, int upd_obj, int upd_probe, cudaStream_t s,
+                    bool pdl) {
     if constexpr (has_reg<N>()) {
         dim3 grid(N / RegShape<N>::L, G * a.K);  // G frame slots per probe mode
+        const size_t sm = smem_row_bwd_r<N>();
         if (mode != BWD_GRAD && upd_probe)  // AP and DM store Psi' alike
-            k_row_bwd_r<N, 1><<<grid, kThreads, smem_row_bwd_r<N>(), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
+            launch_dep(k_row_bwd_r<N, 1>, grid, sm, s, pdl, a, j0, nb, mode, upd_obj, upd_probe);
         else if (mode == BWD_GRAD && upd_obj && !upd_probe)
-            k_row_bwd_r<N, 2><<<grid, kThreads, smem_row_bwd_r<N>(), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
+            launch_dep(k_row_bwd_r<N, 2>, grid, sm, s, pdl, a, j0, nb, mode, upd_obj, upd_probe);
         else
-            k_row_bwd_r<N, 0><<<grid, kThreads, smem_row_bwd_r<N>(), s>>>(a, j0, nb, mode, upd_obj, upd_probe);
+            launch_dep(k_row_bwd_r<N, 0>, grid, sm, s, pdl, a, j0, nb, mode, upd_obj, upd_probe);
         return;
     }
     dim3 grid(N / a.L3, G);

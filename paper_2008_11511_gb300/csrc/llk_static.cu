@@ -182,8 +182,8 @@ extern "C" ptx_status ptx_llk_static(int32_t N, int32_t K, int32_t J, int32_t Ho
     if (B > 32768) B = 32768;
     for (int j0 = 0; j0 < J; j0 += (int)B) {
         const int nb = (int)std::min<size_t>(B, (size_t)(J - j0));
-        ks->row_fwd(a, j0, nb, ptx::X_PHI, s);
-        ks->col(a, j0, nb, ptx::COL_LLK, s);
+        ks->row_fwd(a, j0, nb, ptx::X_PHI, s, false);
+        ks->col(a, j0, nb, ptx::COL_LLK, s, false);
     }
     ptx::k_llk_reduce<<<1, 1024, 0, s>>>(a, (int)nparts, llk_dev);
     if (mask) e = cudaMemsetAsync(base + kMaskOff, 0, (size_t)N * N, s);

@@ -166,8 +166,8 @@ def test_set_param_refuses_bad_names_and_values_and_keeps_the_handle():
     data, o0, p0 = _warm(s)
     pb = _problem(s, o0, p0)
     bad = [("no_such_parameter", 1.0), ("lanes", 0.0), ("lanes", 5.0), ("lanes", 1.5), ("tc", 4.0),
-           ("tc_rows", 2.0), ("persistent", 0.5), ("tma", 2.0), ("batch_frames", 1.5), ("bwd_slots", 5000.0),
-           ("alpha_obj", -1.0), ("alpha_probe", float("nan")), ("tc_selftest", 3.0)]
+           ("tc_rows", 2.0), ("persistent", 0.5), ("tma", 2.0), ("pdl", 0.5), ("batch_frames", 1.5),
+           ("bwd_slots", 5000.0), ("alpha_obj", -1.0), ("alpha_probe", float("nan")), ("tc_selftest", 3.0)]
     for name, value in bad:
         with pytest.raises(PtychoError) as ei:
             pb.set_param(name, value)
