@@ -621,6 +621,15 @@ enum Stage { STAGE_PROBE = 0x100, STAGE_OBJ_GATHER = 0x200, STAGE_OBJ_NORMALISE 
 
 enum Algo { ALGO_AP = 0, ALGO_DM = 1 };
 
+// Whether the register batch passes of a problem go out as programmatic
+// dependents of the pass before them on the same stream: far field, one mode,
+// no background, not while profiling (whose events sit between the launches).
+// The caller launches the first forward pass of a stream plainly.
+bool pass_pdl(const ptx_handle* h, const ProbHost& ph) {
+    return h->pdl && !h->profiling && ph.p.nearfield <= 0.0 && ph.p.K == 1 && !ph.p.background &&
+           use_reg_kernels(ph.ks, ph.p.K);
+}
+
 // Bracket one launch with profiling events when profiling is on.
 struct ProfScope {
     ptx_handle* h;
@@ -872,13 +881,10 @@ ptx_status enqueue_cycle(ptx_handle* h, const std::vector<int>& algos, uint32_t 
         const bool tc_rows = form != TC_NONE && h->tc_rows && ((ph.p.N == 256 && ph.p.K == 1) || ph.p.N == 512) &&
                              ph.p.nearfield <= 0.0 && !ph.p.background;
         bool used[kMaxLanes] = {};
-        // programmatic dependent launches: the three register passes of a far-field
-        // problem with one mode and no background, each after another of them on
-        // the same lane (the first forward pass of a lane follows event waits or
-        // the previous problem's kernels and is launched plainly); not while
-        // profiling, whose events sit between the launches
-        const bool pdl = h->pdl && !h->profiling && !tc_rows && form == TC_NONE && ph.p.nearfield <= 0.0 &&
-                         ph.p.K == 1 && !ph.p.background && use_reg_kernels(ks, ph.p.K);
+        // programmatic dependent launches of the FP32 register passes, each after
+        // another of them on the same lane (the first forward pass of a lane
+        // follows event waits or the previous problem's kernels)
+        const bool pdl = pass_pdl(h, ph) && !tc_rows && form == TC_NONE;
         for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
             const int nb = std::min(ph.B, ph.p.J - j0);
             const int G = std::min(ph.G3, nb);
@@ -1238,14 +1244,15 @@ ptx_status ptx_llk(ptx_handle* h, double* llk_dev, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     for (size_t pi = 0; pi < h->probs.size(); ++pi) {
         ProbHost& ph = h->probs[pi];
+        const bool pdl = pass_pdl(h, ph);
         for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
             const int nb = std::min(ph.B, ph.p.J - j0);
-            ph.ks->row_fwd(ph.args, j0, nb, X_PHI, s, false);
+            ph.ks->row_fwd(ph.args, j0, nb, X_PHI, s, pdl && j0 > 0);
             if (ph.p.nearfield > 0.0) {
                 ph.ks->col_nf(ph.args, nb, +1, s);
                 ph.ks->row_proj(ph.args, j0, nb, 1, s);
             } else {
-                ph.ks->col(ph.args, j0, nb, COL_LLK, s, false);
+                ph.ks->col(ph.args, j0, nb, COL_LLK, s, pdl);
             }
         }
         k_llk_reduce<<<1, 1024, 0, s>>>(ph.args, ph.p.N / ph.C2, llk_dev + pi);
@@ -1271,13 +1278,14 @@ ptx_status ptx_ml_grad(ptx_handle* h, void* grad_obj, void* grad_probe, double* 
     if (grad_obj) e = cudaMemsetAsync(grad_obj, 0, sizeof(float2) * (size_t)a.Ho * a.Wo, s);
     if (e == cudaSuccess && grad_probe) e = cudaMemsetAsync(grad_probe, 0, sizeof(float2) * (size_t)a.K * a.N * a.N, s);
     if (e != cudaSuccess) return cuda_fail(e, "ptx_ml_grad memset");
+    const bool pdl = pass_pdl(h, ph);
     for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
         const int nb = std::min(ph.B, ph.p.J - j0);
-        ph.ks->row_fwd(a, j0, nb, X_PHI, s, false);
-        ph.ks->col(a, j0, nb, COL_GRAD, s, false);
+        ph.ks->row_fwd(a, j0, nb, X_PHI, s, pdl && j0 > 0);
+        ph.ks->col(a, j0, nb, COL_GRAD, s, pdl);
         if (grad_obj || grad_probe)
             ph.ks->row_bwd(a, j0, nb, std::min(ph.G3, nb), BWD_GRAD, grad_obj != nullptr, grad_probe != nullptr, s,
-                            false);
+                           pdl);
     }
     if (llk_dev) k_llk_reduce<<<1, 1024, 0, s>>>(a, a.N / a.C2, llk_dev);
     e = cudaGetLastError();
@@ -1341,12 +1349,13 @@ ptx_status enqueue_grad(ptx_handle* h, ProbHost& ph, float2* g_obj, float2* g_pr
     if (e == cudaSuccess && g_probe) e = cudaMemsetAsync(g_probe, 0, sizeof(float2) * (size_t)a.K * a.N * a.N, s);
     if (e != cudaSuccess) return cuda_fail(e, "gradient memset");
     set_batch(ph, h->spec_bytes, 1, h->batch_cap, h->bwd_slots);
+    const bool pdl = pass_pdl(h, ph);
     for (int j0 = 0; j0 < ph.p.J; j0 += ph.B) {
         const int nb = std::min(ph.B, ph.p.J - j0);
-        ph.ks->row_fwd(a, j0, nb, X_PHI, s, false);
-        ph.ks->col(a, j0, nb, COL_GRAD, s, false);
+        ph.ks->row_fwd(a, j0, nb, X_PHI, s, pdl && j0 > 0);
+        ph.ks->col(a, j0, nb, COL_GRAD, s, pdl);
         if (g_obj || g_probe)
-            ph.ks->row_bwd(a, j0, nb, std::min(ph.G3, nb), BWD_GRAD, g_obj != nullptr, g_probe != nullptr, s, false);
+            ph.ks->row_bwd(a, j0, nb, std::min(ph.G3, nb), BWD_GRAD, g_obj != nullptr, g_probe != nullptr, s, pdl);
     }
     if (llk_out) k_llk_reduce<<<1, 1024, 0, s>>>(a, a.N / a.C2, llk_out);
     e = cudaGetLastError();
