@@ -245,7 +245,8 @@ ptx_status ptx_accumulators(ptx_handle* h, int32_t p, void** obj_acc, size_t* ob
  * cycle is in that form); "pdl" (1, default: the forward row, column and
  * backward row passes of far-field, one-mode problems without a background in
  * FP32 (in the AP / DM cycle within each lane, in ptx_llk, ptx_ml_grad and the
- * ML cycles' gradients) are launched as programmatic dependents of the pass
+ * ML cycles' gradients and line searches) are launched as programmatic
+ * dependents of the pass
  * before them, so that a pass's first blocks load their inputs while the
  * previous pass's last blocks finish; 0: plain launches, each pass after the
  * whole previous one); "tma" (0, default: the register column pass;

@@ -1327,10 +1327,11 @@ ptx_status enqueue_line_coeffs(ptx_handle* h, ProbHost& ph, const float2* d_obj,
     if (B < 1) B = 1;
     if (B > (size_t)ph.p.J) B = ph.p.J;
     if (B > 32768) B = 32768;
+    const bool pdl = pass_pdl(h, ph);
     for (int j0 = 0; j0 < ph.p.J; j0 += (int)B) {
         const int nb = std::min((int)B, ph.p.J - j0);
-        ph.ks->row_fwd_ls(a, j0, nb, 0, s);
-        ph.ks->col_ls(a, j0, nb, 0, s);
+        ph.ks->row_fwd_ls(a, j0, nb, pdl && j0 > 0, s);
+        ph.ks->col_ls(a, j0, nb, pdl, s);
     }
     // partial pairs per frame: one per column block of the line-search column pass
     k_ls_reduce<<<1, 1024, 0, s>>>(a.ls_part, (size_t)ph.p.J * (ph.p.N / ls_cols(ph.ks, ph.p.K)), out);

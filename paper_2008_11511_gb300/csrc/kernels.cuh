@@ -738,8 +738,9 @@ struct KernelSet {
     void (*row_bwd)(const ProbArgs&, int j0, int nb, int G, int mode, int upd_obj, int upd_probe, cudaStream_t,
                     bool pdl);
     void (*fft2)(float2* data, int nframes, int dir, cudaStream_t);
-    void (*row_fwd_ls)(const ProbArgs&, int j0, int nb, int unused, cudaStream_t);
-    void (*col_ls)(const ProbArgs&, int j0, int nb, int unused, cudaStream_t);
+    // line search; pdl as for the passes above (one-mode register kernels)
+    void (*row_fwd_ls)(const ProbArgs&, int j0, int nb, int pdl, cudaStream_t);
+    void (*col_ls)(const ProbArgs&, int j0, int nb, int pdl, cudaStream_t);
     int max_lines;  // lines per block of the shared-memory kernels
     int ls_lines;   // rows / columns per block of the line-search kernels
     int reg_lines;  // lines per block of the register kernels (0: none for this N)
@@ -862,11 +863,11 @@ constexpr int ls_lines() {
     return L;
 }
 template <int N>
-void launch_row_fwd_ls(const ProbArgs& a, int j0, int nb, int, cudaStream_t s) {
+void launch_row_fwd_ls(const ProbArgs& a, int j0, int nb, int pdl, cudaStream_t s) {
     if constexpr (has_reg<N>()) {
         if (a.K == 1) {
             dim3 grid(N / RegShape<N>::L, nb, (a.dir_obj && a.dir_probe) ? 3 : 2);
-            k_row_fwd_ls_r<N><<<grid, kThreads, smem_row_fwd_r<N>(), s>>>(a, j0);
+            launch_dep(k_row_fwd_ls_r<N>, grid, smem_row_fwd_r<N>(), s, pdl != 0, a, j0);
             return;
         }
     }
@@ -875,11 +876,11 @@ void launch_row_fwd_ls(const ProbArgs& a, int j0, int nb, int, cudaStream_t s) {
     k_row_fwd_ls<N><<<grid, kThreads, sizeof(float2) * (N + (size_t)3 * L * line_pitch<N>()), s>>>(a, j0, L);
 }
 template <int N>
-void launch_col_ls(const ProbArgs& a, int j0, int nb, int, cudaStream_t s) {
+void launch_col_ls(const ProbArgs& a, int j0, int nb, int pdl, cudaStream_t s) {
     if constexpr (has_reg<N>()) {
         if (a.K == 1) {
             dim3 grid(N / RegShape<N>::C, nb);
-            k_col_ls_r<N><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, (a.dir_obj && a.dir_probe) ? 3 : 2);
+            launch_dep(k_col_ls_r<N>, grid, smem_col_r<N>(), s, pdl != 0, a, j0, (a.dir_obj && a.dir_probe) ? 3 : 2);
             return;
         }
     }

@@ -321,6 +321,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_ls
     extern __shared__ __align__(16) float2 sm[];
     float2* tw = sm;
     float2* buf = sm + N;
+    pdl_launch_dependents();
     load_twiddles<N>(tw);
     const int y0 = blockIdx.x * L;
     const int b = blockIdx.y;
@@ -359,6 +360,9 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::MinBlocks) k_row_fwd_ls
         }
     }
     __syncthreads();
+    // launched as a programmatic dependent of the previous batch's column pass,
+    // which reads the work stack: wait before writing it
+    pdl_wait();
 #pragma unroll
     for (int i = 0; i < S::I2; ++i) {
         const int w = threadIdx.x + i * kThreads;
@@ -400,6 +404,7 @@ __global__ void __launch_bounds__(kThreads, ls_min_blocks<N>()) k_col_ls_r(ProbA
     __shared__ double red_s[kThreads / 32];
     float2* tw = sm;
     float2* buf = sm + N;
+    pdl_launch_dependents();
     load_twiddles<N>(tw);
     const int x0 = blockIdx.x * C;
     const int b = blockIdx.y;
@@ -409,6 +414,8 @@ __global__ void __launch_bounds__(kThreads, ls_min_blocks<N>()) k_col_ls_r(ProbA
     float d2[S::CI2][M];
     KahanF l1, l2;  // per-pixel terms in single precision (FP64 throughput is low), compensated sums
     __syncthreads();
+    // launched as a programmatic dependent of the row pass that writes the work stack
+    pdl_wait();
     for (int s = 0; s < nwaves; ++s) {
         const int wave = s == 0 ? 0 : (s == nwaves - 1 ? 1 : 2);
         const float2* spec = a.spec + ((size_t)b * nwaves + wave) * N * N + x0;
