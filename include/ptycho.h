@@ -242,14 +242,15 @@ ptx_status ptx_accumulators(ptx_handle* h, int32_t p, void** obj_acc, size_t* ob
  * default; 1: with a tensor-core form, the forward and backward row passes of
  * problems with N = 256 and one mode, or N = 512 and any number of modes, run
  * their DFT stages on the tensor cores too, so that every DFT stage of the
- * cycle is in that form); "pdl" (1, default: the forward row, column and
- * backward row passes of far-field, one-mode problems without a background in
- * FP32 (in the AP / DM cycle within each lane, in ptx_llk, ptx_ml_grad and the
- * ML cycles' gradients and line searches) are launched as programmatic
- * dependents of the pass
- * before them, so that a pass's first blocks load their inputs while the
- * previous pass's last blocks finish; 0: plain launches, each pass after the
- * whole previous one); "tma" (0, default: the register column pass;
+ * cycle is in that form); "pdl" (1, default: the FP32 register passes of
+ * far-field problems without a background (forward row, column and backward
+ * row passes of the one-mode AP / DM cycle within each lane, of ptx_llk,
+ * ptx_ml_grad and the ML cycles' gradients; the one-mode line-search passes)
+ * are launched as
+ * programmatic dependents of the pass before them, so that a pass's first
+ * blocks load their inputs while the previous pass's last blocks finish; 0:
+ * plain launches, each pass after the whole previous one); "tma" (0, default:
+ * the register column pass;
  * 1: the AP / DM column pass of one-mode problems with N = 256 takes its inputs
  * by 2D tensor copies (cp.async.bulk.tensor) in a persistent grid of two CTAs
  * per SM).  "tma_gather" (1, default: the object numerator / denominator of

@@ -822,9 +822,9 @@ void launch_col(const ProbArgs& a, int j0, int nb, int mode, cudaStream_t s, boo
         dim3 grid(N / RegShape<N>::C, nb);
         if (a.K > 1) {
             if (mode == COL_PROJECT && !a.bg)
-                k_col_modes_r<N, true><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, mode);
+                launch_dep(k_col_modes_r<N, true>, grid, smem_col_r<N>(), s, pdl, a, j0, mode);
             else
-                k_col_modes_r<N, false><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, mode);
+                launch_dep(k_col_modes_r<N, false>, grid, smem_col_r<N>(), s, pdl, a, j0, mode);
         } else if (a.bg && mode == COL_PROJECT)
             k_col_r<N, true, true><<<grid, kThreads, smem_col_r<N>(), s>>>(a, j0, mode);
         else if (a.bg)

@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_mod
     __shared__ double red_s[kThreads / 32];
     float2* tw = sm;
     float2* buf = sm + N;
+    pdl_launch_dependents();
     load_twiddles<N>(tw);
     const int K = a.K;
     const int x0 = blockIdx.x * C;
@@ -135,6 +136,8 @@ __global__ void __launch_bounds__(kThreads, RegShape<N>::ColMinBlocks) k_col_mod
 #pragma unroll
         for (int k1 = 0; k1 < M; ++k1) ic_r[i][k1] = 0.f;
     __syncthreads();
+    // launched as a programmatic dependent of the row pass that writes the work stack
+    pdl_wait();
     // sweep 1: forward transforms
     for (int k = 0; k < K; ++k) {
         float2* spec = spec_b + (size_t)k * N * N;
