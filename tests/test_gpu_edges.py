@@ -178,3 +178,39 @@ def test_set_param_refuses_bad_names_and_values_and_keeps_the_handle():
     o, p, _ = oracle.ap_cycle(o0, p0, data)
     _check(s, pb, o, p, TOL1)
     pb.close()
+
+
+def test_dependent_launches_match_plain_launches():
+    """The batch passes launched as programmatic dependents (the default) and
+    plainly ("pdl" 0), in batches of 24 frames over two lanes: both give the
+    oracle's LLK and two DM cycles; the LLK (no atomics on its path) is
+    bit-identical, the gradient and the cycles agree to FP32 rounding (the
+    probe sums and the gradient scatter are atomic additions in arbitrary
+    order).  The gradient is not compared with the oracle here: one AP cycle
+    from the start leaves pixels of small I_c whose weight 2(1 - I_o/I_c)
+    amplifies float32 rounding (the full-size gradient test covers the
+    dependent chain of eight batches against the oracle)."""
+    s = make_config("dm256", J=150, Ho=640, Wo=640)
+    data, o0, p0 = _warm(s)
+    l_ref = oracle.llk(o0, p0, data)
+    o, p, psi, lr = oracle.cycles("DM", o0, p0, data, 2)
+    out = {}
+    for pdl in (1, 0):
+        pb = _problem(s, o0, p0)
+        pb.set_param("pdl", pdl)
+        pb.set_param("batch_frames", 24)
+        l0 = float(pb.llk())
+        assert abs(l0 - l_ref) < TOL1 * abs(l_ref)
+        _, go, gp = pb.ml_grad()
+        llk = pb.dm(2, init_psi=True).cpu().numpy()
+        _check(s, pb, o, p, TOL1 * 2, psi)
+        np.testing.assert_allclose(llk, lr, rtol=TOL1 * 2)
+        out[pdl] = dict(l0=l0, go=go.cpu().numpy(), gp=gp.cpu().numpy(), llk=llk, obj=pb.obj.cpu().numpy(),
+                        probe=pb.probe.cpu().numpy(), psi=pb.psi.cpu().numpy())
+        pb.close()
+    a, b = out[1], out[0]
+    assert a["l0"] == b["l0"]
+    for k in ("go", "gp", "obj", "probe"):
+        assert rel(a[k], b[k]) < 1e-6, k
+    assert rel(a["psi"], b["psi"]) < 1e-5
+    np.testing.assert_allclose(a["llk"], b["llk"], rtol=1e-6)
