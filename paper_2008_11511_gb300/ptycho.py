@@ -268,7 +268,7 @@ class Ptycho:
         """A handle parameter, by the names and ranges of ptx_set_param: the
         inertia factors ``alpha_obj`` / ``alpha_probe``, the schedule
         (``lanes``, ``batch_frames``, ``bwd_slots``, ``tma``, ``tma_gather``,
-        ``persistent``), the number format of the DFT stages (``tc``,
+        ``persistent``, ``pdl``), the number format of the DFT stages (``tc``,
         ``tc_rows``) and the self-test switches; PtychoError for an unknown name
         or a value out of range."""
         _lib.call("ptx_set_param", self._handle(), name.encode(), float(value))
