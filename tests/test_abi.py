@@ -176,6 +176,15 @@ def test_product_package_does_not_import_the_oracle():
                 assert "import oracle" not in src and "from oracle" not in src, f
 
 
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """Without the compiled library the binding raises; there is no fallback
+    path that computes anything on the host."""
+    import paper_2008_11511_gb300._lib as L
+    monkeypatch.setattr(L, "_lib", None)
+    with pytest.raises(RuntimeError, match="libptycho.so not found"):
+        L.load(str(tmp_path / "libptycho.so"))
+
+
 def test_python_api_imports_without_a_gpu():
     from paper_2008_11511_gb300 import Ptycho, PtychoError, PtychoLLK, fft2  # noqa: F401
     import paper_2008_11511_gb300.ptycho as m
